@@ -1,0 +1,106 @@
+"""Exact rational evaluation of the plain definition p(x) = sum c_e x^e.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Doubles are dyadic
+rationals, so every value here is exact: a double m * 2^k is carried as the
+integer pair (m, k) and sums align exponents with shifts.  Pure Python, meant
+for a few points at a time.
+"""
+from fractions import Fraction
+import math
+
+P_MODP = 0xFFFFFFFF00000001
+
+
+def _split(x):
+    """x = m * 2^k exactly, m an int."""
+    x = float(x)
+    if x == 0.0:
+        return 0, 0
+    m, e = math.frexp(x)          # x = m * 2^e, 0.5 <= |m| < 1
+    mi = int(m * (1 << 53))       # exact: m has at most 53 significant bits
+    return mi, e - 53
+
+
+def _mul(a, b):
+    return a[0] * b[0], a[1] + b[1]
+
+
+def _pow(a, d):
+    return a[0] ** d, a[1] * d
+
+
+def _sum(items):
+    items = [t for t in items if t[0] != 0]
+    if not items:
+        return 0, 0
+    k = min(t[1] for t in items)
+    return sum(m << (e - k) for m, e in items), k
+
+
+def to_fraction(v):
+    m, k = v
+    return Fraction(m) * (Fraction(2) ** k)
+
+
+def exact_value(exps, coeffs, point):
+    """Exact p(point) and exact sum |c_e||point^e| as Fractions.  exps: list of
+    exponent tuples, coeffs: doubles, point: one double per variable."""
+    nv = len(point)
+    xs = [_split(v) for v in point]
+    cache = [dict() for _ in range(nv)]
+
+    def pw(v, d):
+        if d not in cache[v]:
+            cache[v][d] = _pow(xs[v], d)
+        return cache[v][d]
+
+    terms, aterms = [], []
+    for e, c in zip(exps, coeffs):
+        t = _split(c)
+        for v in range(nv):
+            if e[v]:
+                t = _mul(t, pw(v, int(e[v])))
+        terms.append(t)
+        aterms.append((abs(t[0]), t[1]))
+    return to_fraction(_sum(terms)), to_fraction(_sum(aterms))
+
+
+def exact_horner_univariate(coeffs_by_degree, x):
+    """Exact value of sum_i c_i x^i for a dense univariate polynomial given as
+    coefficients indexed by degree; Horner over (int, exponent) pairs, which
+    keeps large degrees affordable.  Returns (value, sum |c_i||x|^i)."""
+    xm, xk = _split(x)
+    axm = abs(xm)
+    r = (0, 0)
+    ar = (0, 0)
+    for c in reversed(list(coeffs_by_degree)):
+        cm, ck = _split(c)
+        r = _sum([_mul(r, (xm, xk)), (cm, ck)])
+        ar = _sum([_mul(ar, (axm, xk)), (abs(cm), ck)])
+    return to_fraction(r), to_fraction(ar)
+
+
+def modp_value(exps, coeffs, point):
+    """p(point) mod 2^64 - 2^32 + 1 with Python integers."""
+    s = 0
+    for e, c in zip(exps, coeffs):
+        t = int(c)
+        for v, xv in enumerate(point):
+            t = t * pow(int(xv), int(e[v]), P_MODP) % P_MODP
+        s = (s + t) % P_MODP
+    return s
+
+
+def round_down(q):
+    """Largest double <= the Fraction q (q within the finite double range)."""
+    f = float(q)  # round to nearest
+    while Fraction(f) > q:
+        f = math.nextafter(f, -math.inf)
+    while Fraction(math.nextafter(f, math.inf)) <= q:
+        f = math.nextafter(f, math.inf)
+    return f
+
+
+def round_up(q):
+    """Smallest double >= the Fraction q."""
+    return -round_down(-q)

@@ -1,0 +1,259 @@
+"""Pins of the oracle's tree construction (Def. 1.1-1.3, Table 1) against
+what the paper and the mathematics fix: the worked example, Table 1's power
+sets, the logarithmic lazy-height bound, scheme invariance and brute force."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_example.txt")
+
+
+def _golden():
+    g = {"powers": {}}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *rest = line.split()
+            if key == "coeffs":
+                g["coeffs"] = [float(v) for v in rest]
+            elif key.startswith("lazy_height"):
+                g[key] = {rest[i]: int(rest[i + 1]) for i in range(0, len(rest), 2)}
+            elif key == "horner_classical_height":
+                g[key] = int(rest[0])
+            elif key == "powers":
+                g["powers"][rest[0]] = {int(v) for v in rest[1:]}
+    return g
+
+
+def _example():
+    g = _golden()
+    k = len(g["coeffs"])
+    return g, W.dense_univariate_exps(k), np.array(g["coeffs"])
+
+
+def _depth_sum_ok(t):
+    """Monomial degree = sum of partial degrees on the path to the root (Sec. 1)."""
+    nv = t.nvars
+    for i in range(t.n):
+        acc = np.zeros(nv, dtype=np.int64)
+        j = i
+        while j >= 0:
+            acc[t.pd_var[j]] += t.pd[j]
+            j = t.parent[j]
+        if not np.array_equal(acc, t.node_e[i]):
+            return False
+    return True
+
+
+# ---------------------------------------------------------------- worked example
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B"])
+def test_worked_example_lazy_height(scheme):
+    g, e, _ = _example()
+    t = O.build_tree(e, scheme)
+    assert int(t.lh.max()) == g["lazy_height_pinned"][scheme]
+    if scheme != "E":  # the paper's Estrin value is the documented exception
+        assert int(t.lh.max()) == g["lazy_height_printed"][scheme]
+
+
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B"])
+def test_worked_example_powers(scheme):
+    g, e, _ = _example()
+    t = O.build_tree(e, scheme)
+    assert {d for _, d in t.partial_degrees()} == g["powers"][scheme]
+
+
+def test_worked_example_horner_shape():
+    g, e, _ = _example()
+    t = O.build_tree(e, "H")
+    # Horner is a chain: node i's parent is i+1; its classical height is n
+    assert t.parent[:-1].tolist() == list(range(1, t.n))
+    height = 0
+    for i in range(t.n):
+        d, j = 0, i
+        while t.parent[j] >= 0:
+            j = t.parent[j]
+            d += 1
+        height = max(height, d)
+    assert height == g["horner_classical_height"]
+
+
+def test_worked_example_balanced_lower_degrees():
+    """Sec. 1.2: the balanced tree holds lower partial degrees than Estrin's."""
+    _, e, _ = _example()
+    tb, te = O.build_tree(e, "B"), O.build_tree(e, "E")
+    assert max(d for _, d in tb.partial_degrees()) < max(d for _, d in te.partial_degrees())
+
+
+# ---------------------------------------------------------------- Table 1
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 100, 255, 256, 1000, 1023, 2999, 10006])
+def test_table1_power_sets(n):
+    e = W.dense_univariate_exps(n + 1)
+    logn = int(math.floor(math.log2(n))) if n >= 1 else 0
+    pD = {d for _, d in O.build_tree(e, "D").partial_degrees()}
+    pH = {d for _, d in O.build_tree(e, "H").partial_degrees()}
+    pE = {d for _, d in O.build_tree(e, "E").partial_degrees()}
+    pB = {d for _, d in O.build_tree(e, "B").partial_degrees()}
+    assert pD == set(range(1, n + 1))
+    assert pH == {1}
+    assert pE <= {2 ** k for k in range(logn + 1)}
+    allowed_b = {n // 2 ** k for k in range(logn + 1)} | {n // 2 ** k + 1 for k in range(logn + 1)}
+    assert pB <= allowed_b
+    assert len(pE) <= logn + 1 and len(pB) <= 2 * (logn + 1)
+
+
+# ---------------------------------------------------------------- structure
+def _random_ftab(nmax, seed):
+    r = W.rng(seed)
+    ft = np.zeros(nmax + 1, dtype=np.int32)
+    for n in range(1, nmax + 1):
+        ft[n] = r.integers(1, n + 1)
+    return ft
+
+
+def _hybrid_ftab(nmax, k0=10):
+    """Remark of Sec. 1.1: Estrin above k0, Horner below."""
+    ft = np.zeros(nmax + 1, dtype=np.int32)
+    for n in range(1, nmax + 1):
+        ft[n] = 2 ** int(math.floor(math.log2(n))) if n > k0 else 1
+    return ft
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 16, 17, 100, 1000])
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B", "random", "hybrid"])
+def test_tree_is_topological_and_degrees_add_up(k, scheme):
+    e = W.dense_univariate_exps(k)
+    ft = None
+    if scheme == "random":
+        ft, scheme = _random_ftab(k, 7), "CUSTOM"
+    elif scheme == "hybrid":
+        ft, scheme = _hybrid_ftab(k), "CUSTOM"
+    t = O.build_tree(e, scheme, ft)
+    assert t.n == k
+    assert t.parent[-1] == -1
+    assert np.all(t.parent[:-1] > np.arange(k - 1))      # children before parents
+    assert np.all(t.pd[:-1] > 0)
+    assert _depth_sum_ok(t)
+    # Sec. 1.3: the maximal lazy height is at most logarithmic
+    assert t.lh.max() <= max(0, math.ceil(math.log2(k)))
+
+
+def test_balanced_equals_estrin_at_powers_of_two():
+    for k in (2, 4, 64, 1024):
+        e = W.dense_univariate_exps(k)
+        a, b = O.build_tree(e, "E"), O.build_tree(e, "B")
+        assert np.array_equal(a.parent, b.parent) and np.array_equal(a.pd, b.pd)
+
+
+def test_estrin_lazy_height_closed_form():
+    """For 2^m terms the corrected rule gives lh = floor(m/2) (recurrence
+    lh(E_m) = max(lh(E_{m-1}), 1 + lh(E_{m-2})))."""
+    for m in range(1, 15):
+        t = O.build_tree(W.dense_univariate_exps(2 ** m), "E")
+        assert int(t.lh.max()) == m // 2
+
+
+def test_scheme_f_values():
+    assert O.scheme_f("E", 1) == 1 and O.scheme_f("E", 7) == 4 and O.scheme_f("E", 8) == 8
+    assert O.scheme_f("B", 1) == 1 and O.scheme_f("B", 8) == 4 and O.scheme_f("B", 9) == 5
+    assert O.scheme_f("D", 9) == 9 and O.scheme_f("H", 9) == 1
+
+
+# ---------------------------------------------------------------- walk vs plain sum
+def _sparse_univariate(seed, k, maxdeg):
+    r = W.rng(seed)
+    e = np.sort(r.choice(maxdeg + 1, size=k, replace=False))[::-1].astype(np.int32).reshape(-1, 1)
+    c = r.integers(1, O.P_MODP, size=k, dtype=np.uint64)
+    return e, c
+
+
+def test_printed_lazy_height_breaks_walk_corrected_does_not():
+    """Reading of Def. 1.3: the printed rule ignores the first child's height
+    and loses terms on some trees; the corrected rule never does."""
+    broken_printed = 0
+    for seed in range(300):
+        r = W.rng(1000 + seed)
+        k = int(r.integers(2, 40))
+        e, c = _sparse_univariate(seed, k, 60)
+        ft = _random_ftab(k, seed)
+        x = W.residues(3, seed + 5).reshape(1, 3)
+        want = O.eval_modp(e, c, x)
+        t = O.build_tree(e, "CUSTOM", ft)
+        assert np.array_equal(O.walk_modp(t, t.node_coeffs(c, np.uint64), x), want)
+        t1 = O.build_tree(e, "CUSTOM", ft, lh_rule=1)
+        if not np.array_equal(O.walk_modp(t1, t1.node_coeffs(c, np.uint64), x), want):
+            broken_printed += 1
+    assert broken_printed > 0
+
+
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B", "random", "hybrid"])
+def test_scheme_invariance_modp_bit_identical(scheme):
+    """Def. 1.2: every f with 0 < f(n) <= n gives the same polynomial; over
+    Z/pZ the walk must agree bit for bit with the plain sum."""
+    k = 300
+    e, c, x = W.univariate_case(k, 64, 3, "modp")
+    ft = None
+    if scheme == "random":
+        ft, scheme = _random_ftab(k, 11), "CUSTOM"
+    elif scheme == "hybrid":
+        ft, scheme = _hybrid_ftab(k), "CUSTOM"
+    want = O.eval_modp(e, c, x)
+    assert np.array_equal(O.eval_walk_modp(e, c, x, scheme, ft), want)
+
+
+def _random_multivariate(seed, nvars, k, maxe, downward_closed):
+    r = W.rng(seed)
+    if downward_closed:
+        e = W.graded_prefix_exps(k, nvars)
+    else:
+        seen = set()
+        while len(seen) < k:
+            seen.add(tuple(int(v) for v in r.integers(0, maxe + 1, size=nvars)))
+        e = np.array(sorted(seen), dtype=np.int32)
+    c = r.integers(1, O.P_MODP, size=len(e), dtype=np.uint64)
+    return W.shuffled(e, c, seed + 1)
+
+
+@pytest.mark.parametrize("nvars", [2, 3, 4])
+@pytest.mark.parametrize("closed", [True, False])
+def test_multivariate_walk_equals_plain_sum(nvars, closed):
+    for seed in range(25):
+        e, c = _random_multivariate(seed, nvars, 30, 5, closed)
+        x = W.residues(nvars * 4, seed).reshape(nvars, 4)
+        want = O.eval_modp(e, c, x)
+        for scheme in "DHEB":
+            t = O.build_tree(e, scheme)
+            assert _depth_sum_ok(t)
+            assert all(t.pd[i] > 0 for i in range(t.n - 1))
+            got = O.walk_modp(t, t.node_coeffs(c, np.uint64), x)
+            assert np.array_equal(got, want), (seed, scheme)
+
+
+def test_multivariate_virtual_nodes_only_where_missing():
+    e = W.total_degree_exps(3, 6)
+    t = O.build_tree(e, "E")
+    assert t.n == len(e) and np.all(t.term_of_node >= 0)  # downward closed: none virtual
+    e2 = np.array([[2, 1, 1], [0, 3, 0]], dtype=np.int32)
+    t2 = O.build_tree(e2, "E")
+    virt = {tuple(v) for v, tn in zip(t2.node_e.tolist(), t2.term_of_node) if tn < 0}
+    assert virt == {(2, 0, 0), (2, 1, 0), (0, 0, 0)}
+
+
+def test_trivariate_degree40_term_count():
+    assert len(W.total_degree_exps(3, 40)) == 12341
+
+
+def test_errors():
+    with pytest.raises(O.OracleError):
+        O.build_tree(np.array([[1], [1]]), "E")  # duplicate term
+    with pytest.raises(O.OracleError):
+        O.build_tree(np.array([[1], [-1]]), "E")  # negative exponent
+    bad = np.zeros(5, dtype=np.int32)  # f(n) = 0 violates 0 < f(n)
+    with pytest.raises(O.OracleError):
+        O.build_tree(W.dense_univariate_exps(4), "CUSTOM", bad)
