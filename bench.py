@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark: dense univariate evaluation at 2^24 points.
+
+Workload (one step): polynomials with k = 1000, 3000 and 10007 terms
+(coefficients uniform[-1,1]), each compiled under the Horner, Estrin and
+Balanced function schemes, each evaluated in FP64 and in compensated FP32 at
+2^24 points uniform[-1,1]: 18 evaluations, 1.41e12 term evaluations.
+
+Metric: term evaluations per second (k x points per evaluation), whole job.
+Also reported: the roofline of the dominant kernel (the FP64 evaluation,
+bound by the FP64 multiply-add issue rate), the plain one-thread-per-point
+FP64 Horner kernel on the same FP64 evaluations, an end-to-end figure
+through the host-buffer entry point, and the CPU oracle on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (weak scaling, no collective on the data path): launched by
+torch.distributed.run, each rank evaluates its own points.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G term-evals/s and roofline fraction vs plain FP64 kernel; p50/p99 serve latency"
+UNIT = "G term-evals/s"
+KS = (1000, 3000, 10007)
+SCHEMES = ("H", "E", "B")
+DTYPES = ("f64", "f32c")
+NPTS = 1 << 24
+SEED = 1000  # configuration index x 1000
+
+# FP64 issue peak: 2 DFMA per clock per SM (GB300) x 152 SMs x 2070 MHz x 2 FLOP
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6 * 2 / 1e12
+
+CPU_SAMPLE_POINTS = 1 << 15  # points per evaluation in the CPU-oracle sample
+
+
+def workload_config():
+    return {
+        "workload": "univariate dense, k in {1000, 3000, 10007} terms x schemes {H, E, B} x {f64, f32c}, "
+                    "2^24 points uniform[-1,1], coefficients uniform[-1,1]",
+        "terms": list(KS),
+        "schemes": list(SCHEMES),
+        "value_types": list(DTYPES),
+        "points": NPTS,
+        "term_evals_per_step": sum(KS) * len(SCHEMES) * len(DTYPES) * NPTS,
+        "l2": "no flush: each step reads 192 MiB of points and writes 256 MiB of results (> 129 MB L2)",
+    }
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_chunk(args):
+    k, lo, hi, seed = args
+    import workloads as W
+    import oracle as O
+    e, c, x = W.univariate_case(k, NPTS if hi > NPTS else hi, seed)
+    xs = x[:, lo:hi]
+    t0 = time.perf_counter()
+    O.eval_f64(e, c, xs)                                  # FP64
+    O.eval_f64(e, W.to_f32(c).astype(np.float64), W.to_f32(xs).astype(np.float64))  # FP32C reference
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(npoints=CPU_SAMPLE_POINTS):
+    """Oracle (plain sum, as it stands) on all host cores: term-evals per second
+    over a sample of npoints points of every (k, value type); the plain sum does
+    not depend on the scheme, so one sample per k stands for all three schemes."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    chunks = []
+    per = max(1, npoints // cores)
+    for k in KS:
+        for j in range(0, npoints, per):
+            chunks.append((k, j, min(npoints, j + per), SEED + k))
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(KS[0], 0, 64, SEED + KS[0])] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_chunk, chunks)
+        wall = time.perf_counter() - t0
+    evals = sum(KS) * npoints * len(DTYPES)  # term-evals actually computed
+    return evals / wall, cores, wall
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(1 << 12)
+    rate = None
+    for _ in range(args.steps):
+        rate, cores, wall = cpu_oracle_rate(1 << 13)
+        times.append(wall)
+    value = rate / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32c", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "2^13 points per (k, value type), schemes share the plain-sum oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, device_index):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9 or f[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM; each rank evaluates its own points (weak scaling)
+    x64 = W.points_f64(1, NPTS, SEED + 1 + 7919 * rank)
+    d64 = torch.from_numpy(x64).to(dev)
+    d32 = torch.from_numpy(W.to_f32(x64)).to(dev)
+    out64 = torch.empty(NPTS, dtype=torch.float64, device=dev)
+    out32 = torch.empty((2, NPTS), dtype=torch.float32, device=dev)
+    trees = []
+    for k in KS:
+        e, c, _ = W.univariate_case(k, 1, SEED + k)
+        for s in SCHEMES:
+            trees.append((k, s, fpl.fp_compile(e, c, s)))
+    plain_coeffs = {k: torch.from_numpy(W.univariate_case(k, 1, SEED + k)[1][::-1].copy()).to(dev) for k in KS}
+
+    launches = []  # (kind, k, start_event, end_event)
+
+    def step(record):
+        for k, s, t in trees:
+            for dt in DTYPES:
+                if record:
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                if dt == "f64":
+                    fpl.fp_eval(t, "f64", d64, out=out64, stream=stream)
+                else:
+                    fpl.fp_eval(t, "f32c", d32, out=out32, stream=stream)
+                if record:
+                    b.record(stream)
+                    launches.append((dt, k, a, b))
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop(torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # dominant kernel: FP64 evaluation
+    f64_ms = sum(a.elapsed_time(b) for dt, k, a, b in launches if dt == "f64")
+    f32_ms = sum(a.elapsed_time(b) for dt, k, a, b in launches if dt == "f32c")
+    f64_flops = sum(2.0 * k * NPTS for dt, k, a, b in launches if dt == "f64")
+    f64_launches = sum(1 for dt, *_ in launches if dt == "f64")
+    achieved = f64_flops / (f64_ms * 1e-3) / 1e12
+
+    # plain FP64 kernel (one thread per point, Horner) on the same FP64 evaluations
+    for k in KS:
+        fpl.fp_eval_plain_f64(plain_coeffs[k], d64, out=out64, stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(len(SCHEMES)):
+        for k in KS:
+            fpl.fp_eval_plain_f64(plain_coeffs[k], d64, out=out64, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b)
+    plain_rate = len(SCHEMES) * sum(KS) * NPTS / (plain_ms * 1e-3) / 1e9
+    ours_f64_rate = f64_flops / 2 / (f64_ms * 1e-3) / 1e9 / args.steps * args.steps
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h64 = torch.from_numpy(x64).pin_memory()
+    h32 = torch.from_numpy(W.to_f32(x64)).pin_memory()
+    ho64 = torch.empty(NPTS, dtype=torch.float64).pin_memory()
+    ho32 = torch.empty((2, NPTS), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        for k, s, t in trees:
+            fpl._check(fpl._lib.fp_eval_host(t.handle, 0, fpl._ptr(h64), NPTS, fpl._ptr(ho64),
+                                             fpl._stream_handle(stream)), "fp_eval_host")
+            fpl._check(fpl._lib.fp_eval_host(t.handle, 1, fpl._ptr(h32), NPTS, fpl._ptr(ho32),
+                                             fpl._stream_handle(stream)), "fp_eval_host")
+    e2e_step()
+    e2e_steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = len(trees) * NPTS * (8 + 4)
+    d2h = len(trees) * NPTS * (8 + 8)
+
+    units = workload_config()["term_evals_per_step"] * args.steps * world
+    value = units / (ms * 1e-3) / 1e9
+    e2e_value = workload_config()["term_evals_per_step"] * world / e2e_s / 1e9
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            rate, cores, wall = cpu_oracle_rate()
+            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "2^15 points per (k, value type) of the same workload; the plain-sum oracle does not "
+                             "depend on the scheme (%.1f s wall)" % wall}
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "eval_f64_traffic.txt")
+        if os.path.exists(tf):
+            for line in open(tf):
+                if line.startswith("bytes_per_launch_k10007_2^24:"):
+                    traffic = float(line.split(":")[1])
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/f32c", "data": "synthetic", "config": workload_config(),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "kernel": "eval_kernel<F64,1,true> (FP64 walk)",
+                         "peak_basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 FLOP (recipe unit counts "
+                                       "and max clock); 1 term-eval = 1 multiply + 1 add",
+                         "launches": f64_launches, "avg_launch_ms": f64_ms / max(1, f64_launches)},
+            "kernel_time_share": {"f64": f64_ms / (f64_ms + f32_ms), "f32c": f32_ms / (f64_ms + f32_ms)},
+            "plain_f64_kernel": {"value": plain_rate, "unit": UNIT,
+                                 "ours_f64_same_work": ours_f64_rate,
+                                 "speedup": ours_f64_rate / plain_rate},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": len(trees) * len(DTYPES) * args.steps,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

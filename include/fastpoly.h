@@ -1,0 +1,163 @@
+/*
+ * fastpoly -- GB300 (sm_103a) library for fast polynomial evaluation and
+ * composition through evaluation trees, after G. Moroz, "Fast polynomial
+ * evaluation and composition" (arXiv:1307.5655).
+ *
+ * C ABI.  Plain pointers and sizes only.  Unless stated otherwise:
+ *   - every function returns FP_OK (0) or a negative fp_status code and
+ *     leaves its outputs untouched on error;
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     global memory of the current device, owned by the caller;
+ *   - device work is enqueued asynchronously on `stream` (a cudaStream_t,
+ *     NULL = the legacy default stream); the call returns once the work is
+ *     enqueued, and inputs must stay valid until the stream reaches it;
+ *   - a tree is owned by the library from fp_compile until fp_free; it is
+ *     immutable, so one tree may serve concurrent calls on several streams.
+ */
+#ifndef FASTPOLY_H
+#define FASTPOLY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  FP_OK = 0,
+  FP_E_BAD_VALUE = -1,   /* null pointer, negative size or exponent, coefficient not < p */
+  FP_E_DUP_TERM = -2,    /* two terms with the same exponent vector */
+  FP_E_BAD_SCHEME = -3,  /* unknown scheme, or a custom f with f(n) outside (0, n] */
+  FP_E_DTYPE = -4,       /* value type not available for this tree */
+  FP_E_NOMEM = -5,       /* host or device allocation failed */
+  FP_E_TOO_LARGE = -6,   /* a size beyond the documented limits */
+  FP_E_CUDA = -7,        /* a CUDA call or kernel launch failed */
+  FP_E_TIMEOUT = -8      /* a bounded device-side wait gave up */
+} fp_status;
+
+/* Function schemes f (Sec. 1.1, Def. 1.2, and the balanced scheme of Sec. 1.2).
+ * With n = #terms - 1 of the (sub)polynomial, p = a(x) x^(e) + b(x) where b
+ * holds the f(n) lowest terms:
+ *   FP_SCHEME_D  Direct   f(n) = n
+ *   FP_SCHEME_H  Horner   f(n) = 1
+ *   FP_SCHEME_E  Estrin   f(n) = 2^floor(log2 n)
+ *   FP_SCHEME_B  Balanced f(n) = floor((n+1)/2), i.e. floor(#terms/2) low terms
+ *   FP_SCHEME_CUSTOM  f(n) = f_table[n] for 1 <= n < f_table_len (the paper's
+ *                user-defined schemes, e.g. Estrin above a threshold and Horner
+ *                below, Remark of Sec. 1.1). */
+typedef enum {
+  FP_SCHEME_D = 0,
+  FP_SCHEME_H = 1,
+  FP_SCHEME_E = 2,
+  FP_SCHEME_B = 3,
+  FP_SCHEME_CUSTOM = 4
+} fp_scheme;
+
+/* Value types (the paper evaluates over any ring-like type, Sec. 2.3):
+ *   FP_F64   IEEE double, round to nearest; fused multiply-adds.
+ *   FP_F32C  float with compensation (error-free transformations); the result
+ *            is an unevaluated pair hi + lo.
+ *   FP_IV64  closed intervals of doubles [lo, hi] with directed rounding.
+ *   FP_MODP  integers modulo p = 2^64 - 2^32 + 1, canonical in [0, p). */
+typedef enum { FP_F64 = 0, FP_F32C = 1, FP_IV64 = 2, FP_MODP = 3 } fp_dtype;
+
+typedef struct fp_tree fp_tree;
+
+/* Limits. */
+#define FP_MAX_VARS 8
+#define FP_MAX_TERMS (1 << 24)
+#define FP_MAX_LAZY_HEIGHT 63
+
+/*
+ * fp_compile -- build the evaluation tree of a polynomial (Def. 1.1, 1.2,
+ * the multivariate Remark of Sec. 1.1, lazy heights Def. 1.3, powers Sec. 2.2)
+ * and upload its evaluation schedule to the current device.
+ *
+ *   nvars        number of variables, 1..FP_MAX_VARS.
+ *   nterms       number of terms, 0..FP_MAX_TERMS (0, or all coefficients
+ *                zero, gives the zero polynomial).
+ *   exps         host, int32 [nterms][nvars], non-negative; any term order
+ *                (terms are sorted into decreasing lex order, x1 > x2 > ...).
+ *   coeffs       host; double [nterms] when coeff_type is FP_F64, uint64
+ *                [nterms] (each < p) when coeff_type is FP_MODP.  Terms with a
+ *                zero coefficient are dropped.
+ *   coeff_type   FP_F64 (the tree then serves FP_F64, FP_F32C and FP_IV64;
+ *                FP_F32C rounds the coefficients to float, FP_IV64 uses the
+ *                degenerate intervals [c, c]) or FP_MODP (serves FP_MODP).
+ *   scheme       see fp_scheme; f_table/f_table_len only for FP_SCHEME_CUSTOM.
+ *   out          receives the new tree.
+ * Errors: FP_E_BAD_VALUE, FP_E_DUP_TERM, FP_E_BAD_SCHEME, FP_E_TOO_LARGE
+ * (nvars, nterms, or lazy height above the limits), FP_E_NOMEM, FP_E_CUDA.
+ * Synchronous: returns after the schedule is resident on the device.
+ */
+int fp_compile(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
+               fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
+               int64_t f_table_len, fp_tree** out);
+
+/* fp_compile_host -- the same tree construction as fp_compile, on the host
+ * only: nothing is uploaded and no CUDA call is made.  The tree can be
+ * inspected with fp_tree_info / fp_tree_export; fp_eval on it returns
+ * FP_E_DTYPE.  Same arguments and errors as fp_compile (no FP_E_CUDA). */
+int fp_compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
+                    fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
+                    int64_t f_table_len, fp_tree** out);
+
+/* fp_free -- release a tree and its device memory (NULL is a no-op). The
+ * caller must make sure no enqueued work still uses it. */
+void fp_free(fp_tree* t);
+
+/*
+ * fp_eval -- evaluate a compiled tree at npts points (the coefficient walk of
+ * Sec. 2.1 with the powers of Sec. 2.2), one point per GPU lane group.
+ *
+ * Layouts (all device memory, structure of arrays, v = variable index):
+ *   FP_F64   points double [nvars][npts];       out double [npts]
+ *   FP_F32C  points float  [nvars][npts];       out float [2][npts] (hi, then lo)
+ *   FP_IV64  points double [nvars][2][npts]     (per variable: npts lower
+ *            bounds, then npts upper bounds);   out double [2][npts] (lo, hi)
+ *   FP_MODP  points uint64 [nvars][npts];       out uint64 [npts], in [0, p)
+ *            (points >= p are taken modulo p).
+ * The IV64 result is bit-identical to the walk run with directed rounding on
+ * the CPU in the tree's operation order; FP_MODP is exact; FP_F64 satisfies
+ * |r - p(x)| <= 4 n u sum_e |c_e x^e| (n = #terms - 1, u = 2^-53).
+ * Errors: FP_E_BAD_VALUE, FP_E_DTYPE, FP_E_CUDA.  npts = 0 does nothing.
+ */
+int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out,
+            void* stream);
+
+/* fp_eval_host -- the same as fp_eval with host buffers: copies the points to
+ * the device, evaluates, copies the result back and synchronises `stream`.
+ * Device buffers are allocated per call (stream-ordered). */
+int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts,
+                 void* out_host, void* stream);
+
+/* Tree introspection (host).  fp_tree_info fills, when non-NULL: node count
+ * (terms plus virtual group roots), variables, maximal lazy height, number of
+ * distinct powers in the power table, coefficient type. */
+int fp_tree_info(const fp_tree* t, int64_t* nnodes, int* nvars, int* max_lazy_height,
+                 int* npowers, int* coeff_type);
+
+/* fp_tree_export -- copy the tree (node index order <_t of Sec. 1): per node
+ * its exponent vector int32 [nnodes][nvars], the index of the input term it
+ * came from (-1 for a virtual node), parent index (-1 for the root), the
+ * variable and degree of its partial degree, and its lazy height.  Any
+ * pointer may be NULL. */
+int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, int64_t* parent,
+                   int32_t* pd_var, int64_t* pd, int32_t* lazy_height);
+
+/* fp_eval_plain_f64 -- the comparison baseline: one launch per polynomial,
+ * one thread per point, Horner's rule over the dense coefficient vector
+ * coeffs[0..ncoeffs-1] (index = degree), FP64, no tree.  Device pointers. */
+int fp_eval_plain_f64(const double* coeffs, int64_t ncoeffs, const double* points, int64_t npts,
+                      double* out, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* fp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTPOLY_H */

@@ -1,0 +1,185 @@
+"""Python binding of libfastpoly (GB300 / sm_103a): fast polynomial evaluation
+and composition through evaluation trees (Moroz, arXiv:1307.5655).
+
+Argument marshalling only: every step of evaluation runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device
+memory and streams); the library never falls back to the CPU and importing
+fails loudly when the compiled library is missing.
+
+Names mirror the C ABI of ``include/fastpoly.h``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfastpoly.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libfastpoly.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(or python paper_1307_5655_gb300/build.py)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P, _I, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+
+for _name, _args in {
+    "fp_compile": [_I, _I64, _P, _P, _I, _I, _P, _I64, ctypes.POINTER(_P)],
+    "fp_compile_host": [_I, _I64, _P, _P, _I, _I, _P, _I64, ctypes.POINTER(_P)],
+    "fp_eval": [_P, _I, _P, _I64, _P, _P],
+    "fp_eval_host": [_P, _I, _P, _I64, _P, _P],
+    "fp_tree_info": [_P, _P, _P, _P, _P, _P],
+    "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
+    "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
+}.items():
+    getattr(_lib, _name).restype = _I
+    getattr(_lib, _name).argtypes = _args
+_lib.fp_free.restype = None
+_lib.fp_free.argtypes = [_P]
+_lib.fp_strerror.restype = ctypes.c_char_p
+_lib.fp_strerror.argtypes = [_I]
+
+P_MODP = 0xFFFFFFFF00000001
+SCHEMES = {"D": 0, "H": 1, "E": 2, "B": 3, "CUSTOM": 4}
+DTYPES = {"f64": 0, "f32c": 1, "iv64": 2, "modp": 3}
+
+
+class FastPolyError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, _lib.fp_strerror(code).decode(), code))
+        self.code = code
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise FastPolyError(rc, what)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Tree:
+    """A compiled evaluation tree (owned by the library until freed)."""
+
+    def __init__(self, handle, nvars, coeff_type):
+        self._h = handle
+        self.nvars = nvars
+        self.coeff_type = coeff_type
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.fp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n = ctypes.c_int64()
+        nv, lh, npw, ct = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fp_tree_info(self._h, ctypes.byref(n), ctypes.byref(nv), ctypes.byref(lh), ctypes.byref(npw),
+                                 ctypes.byref(ct)), "fp_tree_info")
+        return {"nnodes": n.value, "nvars": nv.value, "max_lazy_height": lh.value, "npowers": npw.value,
+                "coeff_type": ct.value}
+
+    def export(self):
+        n = self.info()["nnodes"]
+        e = np.zeros((n, self.nvars), dtype=np.int32)
+        tn = np.zeros(n, dtype=np.int64)
+        par = np.zeros(n, dtype=np.int64)
+        pv = np.zeros(n, dtype=np.int32)
+        pd = np.zeros(n, dtype=np.int64)
+        lh = np.zeros(n, dtype=np.int32)
+        _check(_lib.fp_tree_export(self._h, _ptr(e), _ptr(tn), _ptr(par), _ptr(pv), _ptr(pd), _ptr(lh)),
+               "fp_tree_export")
+        return {"node_e": e, "term_of_node": tn, "parent": par, "pd_var": pv, "pd": pd, "lh": lh}
+
+
+def _compile(fn, exps, coeffs, scheme, ftab, modp):
+    e = np.ascontiguousarray(exps, dtype=np.int32)
+    if e.ndim == 1:
+        e = e.reshape(-1, 1)
+    nterms, nvars = e.shape
+    c = np.ascontiguousarray(coeffs, dtype=np.uint64 if modp else np.float64)
+    if len(c) != nterms:
+        raise ValueError("coeffs and exps disagree on the number of terms")
+    ft = None if ftab is None else np.ascontiguousarray(ftab, dtype=np.int32)
+    h = ctypes.c_void_p()
+    rc = fn(nvars, nterms, _ptr(e), _ptr(c), DTYPES["modp"] if modp else DTYPES["f64"],
+            SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+            None if ft is None else _ptr(ft), 0 if ft is None else len(ft), ctypes.byref(h))
+    _check(rc, fn.__name__)
+    return Tree(h.value, nvars, "modp" if modp else "f64")
+
+
+def fp_compile(exps, coeffs, scheme="E", ftab=None, modp=False):
+    """Compile terms (exps [nterms, nvars], coeffs [nterms]) under a function
+    scheme ('D', 'H', 'E', 'B' or 'CUSTOM' with ftab[n] = f(n)) and upload the
+    schedule to the current CUDA device.  modp=True: uint64 coefficients mod p."""
+    return _compile(_lib.fp_compile, exps, coeffs, scheme, ftab, modp)
+
+
+def fp_compile_host(exps, coeffs, scheme="E", ftab=None, modp=False):
+    """Host-only compile (no CUDA call): for inspecting the tree."""
+    return _compile(_lib.fp_compile_host, exps, coeffs, scheme, ftab, modp)
+
+
+def out_shape(dtype, npts):
+    return (npts,) if dtype in ("f64", "modp") else (2, npts)
+
+
+def _torch_dtype(dtype):
+    import torch
+    # residues travel as int64 bit patterns (uint64 tensors have few ops in torch)
+    return {"f64": torch.float64, "f32c": torch.float32, "iv64": torch.float64, "modp": torch.int64}[dtype]
+
+
+def fp_eval(tree, dtype, points, npts=None, out=None, stream=None):
+    """Evaluate on the GPU.  points: CUDA tensor in the layout of fp_eval
+    (f64 [nvars, npts] float64; f32c [nvars, npts] float32; iv64
+    [nvars, 2, npts] float64; modp [nvars, npts] uint64).  Returns out."""
+    import torch
+    if not points.is_cuda or not points.is_contiguous():
+        raise ValueError("points must be a contiguous CUDA tensor")
+    if npts is None:
+        npts = points.shape[-1]
+    if out is None:
+        out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    _check(_lib.fp_eval(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream)), "fp_eval")
+    return out
+
+
+def fp_eval_host(tree, dtype, points, stream=None):
+    """End-to-end: numpy points in host memory -> numpy result (copies inside)."""
+    pts = np.ascontiguousarray(points)
+    npts = pts.shape[-1]
+    npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dtype]
+    out = np.empty(out_shape(dtype, npts), dtype=npdt)
+    _check(_lib.fp_eval_host(tree.handle, DTYPES[dtype], _ptr(pts), npts, _ptr(out), _stream_handle(stream)),
+           "fp_eval_host")
+    return out
+
+
+def fp_eval_plain_f64(coeffs_by_degree, points, out=None, stream=None):
+    """Baseline: one thread per point, Horner over dense FP64 coefficients."""
+    import torch
+    npts = points.shape[-1]
+    if out is None:
+        out = torch.empty(npts, dtype=torch.float64, device=points.device)
+    _check(_lib.fp_eval_plain_f64(_ptr(coeffs_by_degree), coeffs_by_degree.numel(), _ptr(points), npts, _ptr(out),
+                                  _stream_handle(stream)), "fp_eval_plain_f64")
+    return out

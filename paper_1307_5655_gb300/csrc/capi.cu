@@ -1,0 +1,322 @@
+// C ABI of the library (declarations and contracts in include/fastpoly.h).
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "eval_kernel.cuh"
+#include "tree.hpp"
+
+namespace fp {
+namespace {
+
+template <class T>
+int upload(const std::vector<T>& h, T** d) {
+  const size_t n = h.empty() ? 1 : h.size();
+  if (cudaMalloc((void**)d, n * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return FP_E_NOMEM; }
+  if (!h.empty() && cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return FP_E_CUDA;
+  return FP_OK;
+}
+
+void release(fp_tree* t) {
+  DeviceSchedule& d = t->dev;
+  void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d = DeviceSchedule{};
+}
+
+int upload_schedule(fp_tree* t) {
+  DeviceSchedule& d = t->dev;
+  if (cudaGetDevice(&d.device) != cudaSuccess) { cudaGetLastError(); return FP_E_CUDA; }
+  if (t->nnodes == 0) return FP_OK;
+  const int64_t N = t->nnodes, S = N - 1;
+  int rc = upload(t->ctrl, &d.ctrl);
+  if (rc == FP_OK) rc = upload(t->pow_prog, &d.pow_prog);
+  if (rc != FP_OK) return rc;
+  std::vector<uint2> dv(t->pow_prog.size());
+  for (size_t k = 0; k < dv.size(); ++k) dv[k] = make_uint2((unsigned)t->pow_var[k], (unsigned)t->pow_deg[k]);
+  rc = upload(dv, &d.pow_dv);
+  if (rc != FP_OK) return rc;
+  if (t->coeff_type == FP_MODP) {
+    std::vector<uint64_t> a(S), b(S);
+    for (int64_t i = 0; i < S; ++i) {
+      a[i] = t->c_u64[i];
+      b[i] = ((t->ctrl[i] >> kCtrlFirst) & 1u) ? t->c_u64[t->parent[i]] : 0;
+    }
+    rc = upload(a, &d.ca_u64);
+    if (rc == FP_OK) rc = upload(b, &d.cb_u64);
+  } else {
+    std::vector<double> a(S), b(S);
+    std::vector<float> af(S), bf(S);
+    for (int64_t i = 0; i < S; ++i) {
+      a[i] = t->c_f64[i];
+      b[i] = ((t->ctrl[i] >> kCtrlFirst) & 1u) ? t->c_f64[t->parent[i]] : 0.0;
+      af[i] = (float)a[i];
+      bf[i] = (float)b[i];
+    }
+    rc = upload(a, &d.ca_f64);
+    if (rc == FP_OK) rc = upload(b, &d.cb_f64);
+    if (rc == FP_OK) rc = upload(af, &d.ca_f32);
+    if (rc == FP_OK) rc = upload(bf, &d.cb_f32);
+  }
+  return rc;
+}
+
+__global__ void fill_zero_kernel(uint64_t* out, int64_t nwords) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 0;
+}
+
+__global__ void fill_zero32_kernel(uint32_t* out, int64_t nwords) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 0;
+}
+
+size_t value_bytes_out(fp_dtype dt) {  // bytes of output per point
+  switch (dt) {
+    case FP_F64: return 8;
+    case FP_F32C: return 8;
+    case FP_IV64: return 16;
+    case FP_MODP: return 8;
+  }
+  return 0;
+}
+
+size_t point_bytes(fp_dtype dt) {  // bytes of input per point and variable
+  switch (dt) {
+    case FP_F64: return 8;
+    case FP_F32C: return 4;
+    case FP_IV64: return 16;
+    case FP_MODP: return 8;
+  }
+  return 0;
+}
+
+bool dtype_ok(const fp_tree* t, fp_dtype dt) {
+  if (t->dev.device < 0) return false;  // host-only tree
+  if (dt == FP_MODP) return t->coeff_type == FP_MODP;
+  if (dt == FP_F64 || dt == FP_F32C || dt == FP_IV64) return t->coeff_type == FP_F64;
+  return false;
+}
+
+__global__ void plain_horner_kernel(const double* __restrict__ c, int64_t nc, const double* __restrict__ x,
+                                    int64_t npts, double* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= npts) return;
+  const double xv = x[j];
+  double r = c[nc - 1];
+  for (int64_t i = nc - 2; i >= 0; --i) r = fma(r, xv, c[i]);
+  out[j] = r;
+}
+
+}  // namespace
+
+int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st) {
+  if (!t) return FP_E_BAD_VALUE;
+  if ((int)dt < FP_F64 || (int)dt > FP_MODP) return FP_E_DTYPE;
+  if (!dtype_ok(t, dt)) return FP_E_DTYPE;
+  if (npts < 0) return FP_E_BAD_VALUE;
+  if (npts == 0) return FP_OK;
+  if (!points || !out) return FP_E_BAD_VALUE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->dev.device) { cudaGetLastError(); return FP_E_BAD_VALUE; }
+  if (t->nnodes == 0) {  // zero polynomial
+    const int64_t bytes = npts * (int64_t)value_bytes_out(dt);
+    const int blocks = (int)((bytes / 8 + 255) / 256 < 4096 ? (bytes / 8 + 255) / 256 + 1 : 4096);
+    if (bytes % 8 == 0) fill_zero_kernel<<<blocks, 256, 0, st>>>((uint64_t*)out, bytes / 8);
+    else fill_zero32_kernel<<<blocks, 256, 0, st>>>((uint32_t*)out, bytes / 4);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
+  }
+  EvalArgs a{};
+  a.ctrl = t->dev.ctrl;
+  a.pow_prog = t->dev.pow_prog;
+  a.pow_dv = t->dev.pow_dv;
+  a.nsteps = t->nnodes - 1;
+  a.npow = (int)t->pow_prog.size();
+  a.nslot = t->max_lh + 1;
+  a.nvars = t->nvars;
+  a.root_leaf = t->root_leaf;
+  a.root_lh = t->root_lh;
+  a.root_pid = t->root_pid;
+  a.points = points;
+  a.npts = npts;
+  a.out = out;
+  const int64_t root = t->nnodes - 1;
+  size_t vbytes = 8, pbytes = 8;
+  int ppt = 1;
+  switch (dt) {
+    case FP_F64: {
+      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
+      std::memcpy(&a.root_c, &t->c_f64[root], 8);
+      break;
+    }
+    case FP_IV64: {
+      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
+      std::memcpy(&a.root_c, &t->c_f64[root], 8);
+      vbytes = pbytes = 16;
+      break;
+    }
+    case FP_F32C: {
+      a.ca = t->dev.ca_f32; a.cb = t->dev.cb_f32;
+      const float c = (float)t->c_f64[root];
+      uint32_t bits;
+      std::memcpy(&bits, &c, 4);
+      a.root_c = bits;
+      ppt = 2;
+      break;
+    }
+    case FP_MODP: {
+      a.ca = t->dev.ca_u64; a.cb = t->dev.cb_u64;
+      a.root_c = t->c_u64[root];
+      ppt = 2;
+      break;
+    }
+  }
+  const size_t smem = (vbytes * (size_t)a.nslot + pbytes * (size_t)a.nvars) * ppt * kTPB;
+  if (smem > kSmemMax) return FP_E_TOO_LARGE;
+  cudaError_t e = cudaSuccess;
+  switch (dt) {
+    case FP_F64: e = launch_eval_f64(a, st); break;
+    case FP_F32C: e = launch_eval_f32c(a, st); break;
+    case FP_IV64: e = launch_eval_iv64(a, st); break;
+    case FP_MODP: e = launch_eval_modp(a, st); break;
+  }
+  return e == cudaSuccess ? FP_OK : FP_E_CUDA;
+}
+
+}  // namespace fp
+
+using namespace fp;
+
+extern "C" {
+
+int fp_compile(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs, fp_dtype coeff_type,
+               fp_scheme scheme, const int32_t* f_table, int64_t f_table_len, fp_tree** out) {
+  if (!out) return FP_E_BAD_VALUE;
+  fp_tree* t = new (std::nothrow) fp_tree();
+  if (!t) return FP_E_NOMEM;
+  int rc;
+  try {
+    rc = compile_host(nvars, nterms, exps, coeffs, coeff_type, scheme, f_table, f_table_len, t);
+  } catch (const std::bad_alloc&) {
+    rc = FP_E_NOMEM;
+  }
+  if (rc == FP_OK) rc = upload_schedule(t);
+  if (rc != FP_OK) {
+    release(t);
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return FP_OK;
+}
+
+int fp_compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs, fp_dtype coeff_type,
+                    fp_scheme scheme, const int32_t* f_table, int64_t f_table_len, fp_tree** out) {
+  if (!out) return FP_E_BAD_VALUE;
+  fp_tree* t = new (std::nothrow) fp_tree();
+  if (!t) return FP_E_NOMEM;
+  int rc;
+  try {
+    rc = compile_host(nvars, nterms, exps, coeffs, coeff_type, scheme, f_table, f_table_len, t);
+  } catch (const std::bad_alloc&) {
+    rc = FP_E_NOMEM;
+  }
+  if (rc != FP_OK) {
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return FP_OK;
+}
+
+void fp_free(fp_tree* t) {
+  if (!t) return;
+  release(t);
+  delete t;
+}
+
+int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream) {
+  return eval_device(t, dtype, points, npts, out, (cudaStream_t)stream);
+}
+
+int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts, void* out_host,
+                 void* stream) {
+  if (!t) return FP_E_BAD_VALUE;
+  if (!dtype_ok(t, dtype)) return FP_E_DTYPE;
+  if (npts < 0) return FP_E_BAD_VALUE;
+  if (npts == 0) return FP_OK;
+  if (!points_host || !out_host) return FP_E_BAD_VALUE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t in_bytes = point_bytes(dtype) * (size_t)t->nvars * (size_t)npts;
+  const size_t out_bytes = value_bytes_out(dtype) * (size_t)npts;
+  void *din = nullptr, *dout = nullptr;
+  if (cudaMallocAsync(&din, in_bytes, st) != cudaSuccess || cudaMallocAsync(&dout, out_bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (din) cudaFreeAsync(din, st);
+    return FP_E_NOMEM;
+  }
+  int rc = FP_OK;
+  if (cudaMemcpyAsync(din, points_host, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = FP_E_CUDA;
+  if (rc == FP_OK) rc = eval_device(t, dtype, din, npts, dout, st);
+  if (rc == FP_OK && cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = FP_E_CUDA;
+  cudaFreeAsync(din, st);
+  cudaFreeAsync(dout, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == FP_OK) rc = FP_E_CUDA;
+  return rc;
+}
+
+int fp_tree_info(const fp_tree* t, int64_t* nnodes, int* nvars, int* max_lazy_height, int* npowers,
+                 int* coeff_type) {
+  if (!t) return FP_E_BAD_VALUE;
+  if (nnodes) *nnodes = t->nnodes;
+  if (nvars) *nvars = t->nvars;
+  if (max_lazy_height) *max_lazy_height = t->max_lh;
+  if (npowers) *npowers = (int)t->pow_prog.size();
+  if (coeff_type) *coeff_type = t->coeff_type;
+  return FP_OK;
+}
+
+int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, int64_t* parent, int32_t* pd_var,
+                   int64_t* pd, int32_t* lazy_height) {
+  if (!t) return FP_E_BAD_VALUE;
+  const size_t N = (size_t)t->nnodes;
+  if (N == 0) return FP_OK;
+  if (node_exps) std::memcpy(node_exps, t->node_e.data(), N * t->nvars * sizeof(int32_t));
+  if (term_of_node) std::memcpy(term_of_node, t->term_of_node.data(), N * sizeof(int64_t));
+  if (parent) std::memcpy(parent, t->parent.data(), N * sizeof(int64_t));
+  if (pd_var) std::memcpy(pd_var, t->pd_var.data(), N * sizeof(int32_t));
+  if (pd) std::memcpy(pd, t->pd.data(), N * sizeof(int64_t));
+  if (lazy_height) std::memcpy(lazy_height, t->lh.data(), N * sizeof(int32_t));
+  return FP_OK;
+}
+
+int fp_eval_plain_f64(const double* coeffs, int64_t ncoeffs, const double* points, int64_t npts, double* out,
+                      void* stream) {
+  if (ncoeffs < 1 || npts < 0 || !coeffs) return FP_E_BAD_VALUE;
+  if (npts == 0) return FP_OK;
+  if (!points || !out) return FP_E_BAD_VALUE;
+  const int64_t blocks = (npts + 255) / 256;
+  if (blocks > 0x7FFFFFFFLL) return FP_E_TOO_LARGE;
+  plain_horner_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(coeffs, ncoeffs, points, npts, out);
+  return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
+}
+
+const char* fp_strerror(int status) {
+  switch (status) {
+    case FP_OK: return "ok";
+    case FP_E_BAD_VALUE: return "bad value";
+    case FP_E_DUP_TERM: return "duplicate term";
+    case FP_E_BAD_SCHEME: return "bad scheme";
+    case FP_E_DTYPE: return "value type not available for this tree";
+    case FP_E_NOMEM: return "out of memory";
+    case FP_E_TOO_LARGE: return "size beyond the supported limits";
+    case FP_E_CUDA: return "CUDA error";
+    case FP_E_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// Host compiler: terms -> evaluation tree -> flattened per-point schedule.
+//
+// Follows Moroz, "Fast polynomial evaluation and composition":
+//   Sec. 1 (decreasing lex order <_t, root = last node), Def. 1.1 (partial
+//   degrees), Def. 1.2 (function scheme split p = a x^f(n) + b with b the
+//   f(n) lowest terms, n = #terms - 1), the Remark on multivariate polynomials
+//   (the scheme applied per variable: terms grouped by the first variable's
+//   exponent, each group compiled over the next variable and represented by
+//   its lowest term; a group missing that term gets a zero-coefficient root),
+//   Def. 1.3 (lazy height, with the first-walked child counted:
+//   lh(N) = max(lh(C1), 1 + max_{i>=2} lh(Ci))), Sec. 2.2 (distinct powers,
+//   computed once per point by squarings and multiplications by x).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "tree.hpp"
+
+namespace fp {
+namespace {
+
+// f(n) of a scheme; n = #terms - 1 >= 1.  Returns 0 when undefined.
+int64_t split_count(fp_scheme s, const int32_t* ft, int64_t ftlen, int64_t n) {
+  switch (s) {
+    case FP_SCHEME_D: return n;
+    case FP_SCHEME_H: return 1;
+    case FP_SCHEME_E: {
+      int64_t f = 1;
+      while ((f << 1) <= n) f <<= 1;
+      return f;
+    }
+    case FP_SCHEME_B: return (n + 1) >> 1;
+    case FP_SCHEME_CUSTOM: return (ft && n < ftlen) ? ft[n] : 0;
+  }
+  return 0;
+}
+
+struct Builder {
+  int nv;
+  const std::vector<int32_t>& e;  // [N][nv]
+  std::vector<int64_t>& parent;
+  std::vector<int32_t>& pd_var;
+  std::vector<int64_t>& pd;
+  fp_scheme scheme;
+  const int32_t* ft;
+  int64_t ftlen;
+  int status = FP_OK;
+
+  int32_t ex(int64_t node, int v) const { return e[node * nv + v]; }
+
+  // Attach the units (groups) of one level by the function scheme.
+  void attach_units(const std::vector<int64_t>& root, int var) {
+    std::vector<std::pair<int64_t, int64_t>> work;
+    work.emplace_back(0, (int64_t)root.size() - 1);
+    while (!work.empty() && status == FP_OK) {
+      auto [a, b] = work.back();
+      work.pop_back();
+      if (a >= b) continue;
+      const int64_t n = b - a;
+      const int64_t f = split_count(scheme, ft, ftlen, n);
+      if (f < 1 || f > n) { status = FP_E_BAD_SCHEME; return; }
+      const int64_t top = root[b - f], base = root[b];  // roots of T_a and T_b
+      parent[top] = base;
+      pd_var[top] = var;
+      pd[top] = (int64_t)ex(top, var) - ex(base, var);
+      work.emplace_back(b - f + 1, b);  // b: the f lowest units
+      work.emplace_back(a, b - f);      // a: the rest
+    }
+  }
+
+  // Nodes [lo, hi] agree on the variables before `var`.
+  void level(int64_t lo, int64_t hi, int var) {
+    std::vector<int64_t> roots;
+    int64_t start = lo;
+    for (int64_t i = lo; i <= hi && status == FP_OK; ++i) {
+      if (i == hi || ex(i, var) != ex(i + 1, var)) {
+        if (var + 1 < nv) level(start, i, var + 1);
+        roots.push_back(i);
+        start = i + 1;
+      }
+    }
+    if (status == FP_OK) attach_units(roots, var);
+  }
+};
+
+// Emit the sorted terms of `run` (sharing their first `var` exponents) into
+// `out`, appending a virtual node (prefix, 0, ..., 0) when the run lacks it.
+void emit_with_roots(const std::vector<int64_t>& order, int64_t lo, int64_t hi, int var, int nv,
+                     const int32_t* exps, std::vector<int32_t>& out_e, std::vector<int64_t>& out_t) {
+  if (var == nv) {  // a single term
+    out_e.insert(out_e.end(), exps + order[lo] * nv, exps + order[lo] * nv + nv);
+    out_t.push_back(order[lo]);
+    return;
+  }
+  int64_t start = lo;
+  int32_t last_val = -1;
+  for (int64_t i = lo; i <= hi; ++i) {
+    const int32_t v = exps[order[i] * nv + var];
+    if (i == hi || exps[order[i + 1] * nv + var] != v) {
+      emit_with_roots(order, start, i, var + 1, nv, exps, out_e, out_t);
+      last_val = v;
+      start = i + 1;
+    }
+  }
+  if (var > 0 && last_val != 0) {
+    // the run's root (prefix, 0, ..., 0) is missing
+    const int32_t* pre = exps + order[lo] * nv;
+    for (int v = 0; v < nv; ++v) out_e.push_back(v < var ? pre[v] : 0);
+    out_t.push_back(-1);
+  }
+}
+
+}  // namespace
+
+int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
+                 fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
+                 int64_t f_table_len, fp_tree* t) {
+  if (nvars < 1 || nvars > FP_MAX_VARS || nterms < 0) return nvars > FP_MAX_VARS ? FP_E_TOO_LARGE : FP_E_BAD_VALUE;
+  if (nterms > FP_MAX_TERMS) return FP_E_TOO_LARGE;
+  if (nterms > 0 && (!exps || !coeffs)) return FP_E_BAD_VALUE;
+  if (coeff_type != FP_F64 && coeff_type != FP_MODP) return FP_E_DTYPE;
+  if ((int)scheme < FP_SCHEME_D || (int)scheme > FP_SCHEME_CUSTOM) return FP_E_BAD_SCHEME;
+  if (scheme == FP_SCHEME_CUSTOM && (!f_table || f_table_len < 1)) return FP_E_BAD_SCHEME;
+  const uint64_t P = 0xFFFFFFFF00000001ull;
+
+  // a1: keep the non-zero terms, sort them into decreasing lex order
+  std::vector<int64_t> order;
+  order.reserve(nterms);
+  for (int64_t i = 0; i < nterms; ++i) {
+    for (int v = 0; v < nvars; ++v)
+      if (exps[i * nvars + v] < 0) return FP_E_BAD_VALUE;
+    if (coeff_type == FP_MODP) {
+      const uint64_t c = ((const uint64_t*)coeffs)[i];
+      if (c >= P) return FP_E_BAD_VALUE;
+      if (c == 0) continue;
+    } else {
+      const double c = ((const double*)coeffs)[i];
+      if (!(c == c) || c == 0.0) {
+        if (c == 0.0) continue;
+        return FP_E_BAD_VALUE;  // NaN coefficient
+      }
+    }
+    order.push_back(i);
+  }
+  auto greater = [&](int64_t a, int64_t b) {
+    for (int v = 0; v < nvars; ++v) {
+      const int32_t x = exps[a * nvars + v], y = exps[b * nvars + v];
+      if (x != y) return x > y;
+    }
+    return false;
+  };
+  std::stable_sort(order.begin(), order.end(), greater);
+  for (size_t i = 1; i < order.size(); ++i)
+    if (!greater(order[i - 1], order[i])) return FP_E_DUP_TERM;
+
+  t->nvars = nvars;
+  t->coeff_type = coeff_type;
+  t->node_e.clear();
+  t->term_of_node.clear();
+  if (order.empty()) {  // the zero polynomial
+    t->nnodes = 0;
+    return FP_OK;
+  }
+  emit_with_roots(order, 0, (int64_t)order.size() - 1, 0, nvars, exps, t->node_e, t->term_of_node);
+  const int64_t N = (int64_t)t->term_of_node.size();
+  t->nnodes = N;
+  t->parent.assign(N, -1);
+  t->pd_var.assign(N, 0);
+  t->pd.assign(N, 0);
+
+  // a2: the tree, Def. 1.2 per level
+  Builder bld{nvars, t->node_e, t->parent, t->pd_var, t->pd, scheme, f_table, f_table_len};
+  bld.level(0, N - 1, 0);
+  if (bld.status != FP_OK) return bld.status;
+  t->pd_var[N - 1] = 0;
+  t->pd[N - 1] = t->node_e[(N - 1) * nvars];  // root: (e_1, 0, ..., 0)
+
+  // node coefficients
+  if (coeff_type == FP_MODP) {
+    t->c_u64.assign(N, 0);
+    for (int64_t i = 0; i < N; ++i)
+      if (t->term_of_node[i] >= 0) t->c_u64[i] = ((const uint64_t*)coeffs)[t->term_of_node[i]];
+  } else {
+    t->c_f64.assign(N, 0.0);
+    for (int64_t i = 0; i < N; ++i)
+      if (t->term_of_node[i] >= 0) t->c_f64[i] = ((const double*)coeffs)[t->term_of_node[i]];
+  }
+
+  // a3: lazy heights (children precede parents in index order)
+  t->lh.assign(N, 0);
+  std::vector<int32_t> lh_first(N, 0), lh_rest(N, -1);
+  std::vector<uint8_t> has_child(N, 0), is_first(N, 0);
+  int32_t L = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const int32_t h = has_child[i] ? std::max(lh_first[i], lh_rest[i] + 1) : 0;
+    t->lh[i] = h;
+    L = std::max(L, h);
+    const int64_t q = t->parent[i];
+    if (q < 0) continue;
+    if (!has_child[q]) {
+      has_child[q] = 1;
+      is_first[i] = 1;
+      lh_first[q] = h;
+    } else {
+      lh_rest[q] = std::max(lh_rest[q], h);
+    }
+  }
+  if (L > FP_MAX_LAZY_HEIGHT) return FP_E_TOO_LARGE;
+  t->max_lh = L;
+
+  // a4: distinct powers x_v^d and the program computing them:
+  // x^1 = x, x^(2k) = (x^k)^2, x^(2k+1) = x^(2k) x
+  std::map<std::pair<int32_t, int64_t>, int32_t> pid;
+  std::vector<std::pair<int32_t, int64_t>> need;
+  auto want = [&](int32_t v, int64_t d) { need.emplace_back(v, d); };
+  for (int64_t i = 0; i + 1 < N; ++i) want(t->pd_var[i], t->pd[i]);
+  if (t->pd[N - 1] > 0) want(0, t->pd[N - 1]);
+  for (size_t k = 0; k < need.size(); ++k) {  // closure under the rule above
+    const auto [v, d] = need[k];
+    if (d == 1) continue;
+    need.emplace_back(v, (d % 2 == 0) ? d / 2 : d - 1);
+  }
+  std::sort(need.begin(), need.end());
+  need.erase(std::unique(need.begin(), need.end()), need.end());
+  if (need.size() >= kMaxPowers) return FP_E_TOO_LARGE;
+  t->pow_prog.clear();
+  t->pow_var.clear();
+  t->pow_deg.clear();
+  for (const auto& [v, d] : need) {
+    const int32_t id = (int32_t)t->pow_prog.size();
+    uint32_t w;
+    if (d == 1) w = kPowLoad | (uint32_t)v << 2;
+    else if (d % 2 == 0) w = kPowSq | (uint32_t)pid.at({v, d / 2}) << 2;
+    else w = kPowMulX | (uint32_t)pid.at({v, d - 1}) << 2 | (uint32_t)pid.at({v, 1}) << 17;
+    pid[{v, d}] = id;
+    t->pow_prog.push_back(w);
+    t->pow_var.push_back(v);
+    t->pow_deg.push_back(d);
+  }
+
+  // a5: the schedule, one control word per non-root node
+  t->ctrl.assign(N - 1, 0);
+  for (int64_t i = 0; i + 1 < N; ++i) {
+    const int64_t q = t->parent[i];
+    const uint32_t leaf = has_child[i] ? 0u : 1u;
+    const uint32_t S = leaf ? 0u : (uint32_t)t->lh[i];
+    t->ctrl[i] = S << kCtrlS | (uint32_t)t->lh[q] << kCtrlD | leaf << kCtrlLeaf |
+                 (uint32_t)is_first[i] << kCtrlFirst |
+                 (uint32_t)pid.at({t->pd_var[i], t->pd[i]}) << kCtrlPid;
+  }
+  t->root_leaf = has_child[N - 1] ? 0 : 1;
+  t->root_lh = t->lh[N - 1];
+  t->root_pid = t->pd[N - 1] > 0 ? pid.at({0, t->pd[N - 1]}) : -1;
+  return FP_OK;
+}
+
+}  // namespace fp

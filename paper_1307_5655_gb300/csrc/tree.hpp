@@ -1,0 +1,75 @@
+// Internal representation of a compiled evaluation tree and of the flattened
+// per-point schedule the kernels replay.  Not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "../../include/fastpoly.h"
+
+namespace fp {
+
+// Schedule control word of one non-root node, in node index order (Sec. 1):
+//   bits  0..5   S     lazy height of the node (its accumulator slot)
+//   bits  6..11  D     lazy height of its parent (the slot it feeds)
+//   bit  12      LEAF  the node has no children
+//   bit  13      FIRST the node is the lowest-index child of its parent
+//   bits 14..31  PID   index of x_v^d in the per-point power table
+constexpr uint32_t kCtrlS = 0, kCtrlD = 6, kCtrlLeaf = 12, kCtrlFirst = 13, kCtrlPid = 14;
+constexpr uint32_t kMaxPowers = 1u << 15;
+
+// Power program entry, one per power-table slot, in dependency order:
+//   bits  0..1   op   0: load x_v (A1 = v)   1: square of slot A1
+//                     2: slot A1 times slot A2 (A2 holds x_v)
+//   bits  2..16  A1
+//   bits 17..31  A2
+constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
+
+struct DeviceSchedule {
+  int device = -1;
+  uint32_t* ctrl = nullptr;   // [nsteps]
+  uint32_t* pow_prog = nullptr;  // [npow]
+  uint2* pow_dv = nullptr;       // [npow] (variable, degree)
+  double* ca_f64 = nullptr;   // [nsteps] coefficient of the node
+  double* cb_f64 = nullptr;   // [nsteps] coefficient of the parent when FIRST, else 0
+  float* ca_f32 = nullptr;
+  float* cb_f32 = nullptr;
+  uint64_t* ca_u64 = nullptr;
+  uint64_t* cb_u64 = nullptr;
+};
+
+}  // namespace fp
+
+struct fp_tree {
+  int nvars = 1;
+  int coeff_type = FP_F64;  // FP_F64 or FP_MODP
+  int64_t nnodes = 0;       // 0: the zero polynomial
+  std::vector<int32_t> node_e;       // [nnodes][nvars]
+  std::vector<int64_t> term_of_node;  // -1: virtual group root
+  std::vector<int64_t> parent;       // -1: root
+  std::vector<int32_t> pd_var;
+  std::vector<int64_t> pd;
+  std::vector<int32_t> lh;
+  std::vector<double> c_f64;    // node coefficients (coeff_type FP_F64)
+  std::vector<uint64_t> c_u64;  // node coefficients (coeff_type FP_MODP)
+  int max_lh = 0;
+
+  // flattened schedule
+  std::vector<uint32_t> ctrl;      // [nnodes-1]
+  std::vector<uint32_t> pow_prog;  // [npow]
+  std::vector<int32_t> pow_var;
+  std::vector<int64_t> pow_deg;
+  int root_leaf = 1;
+  int root_lh = 0;
+  int root_pid = -1;
+
+  fp::DeviceSchedule dev;
+};
+
+namespace fp {
+// Build the tree and its schedule on the host (no CUDA calls).
+int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
+                 fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
+                 int64_t f_table_len, fp_tree* t);
+}  // namespace fp

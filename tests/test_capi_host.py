@@ -1,0 +1,125 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports every
+symbol the header declares, and the host compiler builds exactly the tree
+the oracle builds (index work is compared bit for bit)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+import paper_1307_5655_gb300 as fpl
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fastpoly.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared()
+    assert "fp_compile" in names and "fp_eval" in names
+    lib = ctypes.CDLL(fpl.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _compare(exps, coeffs, scheme, ftab=None):
+    t = fpl.fp_compile_host(exps, coeffs, scheme, ftab)
+    got = t.export()
+    ref = O.build_tree(exps, scheme, ftab)
+    assert np.array_equal(got["node_e"], ref.node_e)
+    assert np.array_equal(got["term_of_node"], ref.term_of_node)
+    assert np.array_equal(got["parent"], ref.parent)
+    assert np.array_equal(got["pd_var"], ref.pd_var)
+    assert np.array_equal(got["pd"], ref.pd)
+    assert np.array_equal(got["lh"], ref.lh)
+    info = t.info()
+    assert info["nnodes"] == ref.n and info["max_lazy_height"] == int(ref.lh.max())
+    t.free()
+
+
+def _ftab(kind, nmax, seed=0):
+    ft = np.zeros(nmax + 1, dtype=np.int32)
+    r = W.rng(seed)
+    for n in range(1, nmax + 1):
+        if kind == "random":
+            ft[n] = r.integers(1, n + 1)
+        else:  # Estrin above 10 terms, Horner below (Remark of Sec. 1.1)
+            ft[n] = 2 ** int(math.floor(math.log2(n))) if n > 10 else 1
+    return ft
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 9, 100, 1000, 1024, 3000, 10007])
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B", "random", "hybrid"])
+def test_univariate_tree_matches_oracle(k, scheme):
+    if scheme == "D" and k > 3000:
+        pytest.skip("direct scheme oracle recursion is linear in depth")
+    e = W.dense_univariate_exps(k)
+    c = W.uniform_f64(k, k)
+    ft = None
+    if scheme in ("random", "hybrid"):
+        ft, scheme = _ftab(scheme, k, k), "CUSTOM"
+    e, c = W.shuffled(e, c, 3)
+    _compare(e, c, scheme, ft)
+
+
+@pytest.mark.parametrize("nvars", [2, 3, 4])
+@pytest.mark.parametrize("scheme", ["D", "H", "E", "B"])
+def test_multivariate_tree_matches_oracle(nvars, scheme):
+    for seed in range(6):
+        r = W.rng(seed)
+        if seed % 2 == 0:
+            e = W.graded_prefix_exps(int(r.integers(1, 60)), nvars)
+        else:
+            pts = {tuple(int(v) for v in r.integers(0, 6, size=nvars)) for _ in range(40)}
+            e = np.array(sorted(pts), dtype=np.int32)
+        c = W.uniform_f64(len(e), seed) + 2.0  # non-zero
+        e, c = W.shuffled(e, c, seed)
+        _compare(e, c, scheme)
+
+
+def test_trivariate_degree40_tree_matches_oracle():
+    e = W.total_degree_exps(3, 40)
+    c = W.uniform_f64(len(e), 1)
+    for s in "EB":
+        _compare(e, c, s)
+
+
+def test_sparse_univariate_root_degree():
+    e = np.array([[40], [17], [5]], dtype=np.int32)
+    _compare(e, np.array([1.0, -2.0, 3.0]), "E")
+
+
+def test_zero_coefficients_dropped_and_zero_polynomial():
+    t = fpl.fp_compile_host(np.array([[3], [2], [1]]), np.array([1.0, 0.0, 2.0]), "H")
+    assert t.info()["nnodes"] == 2
+    z = fpl.fp_compile_host(np.array([[3], [1]]), np.array([0.0, 0.0]), "E")
+    assert z.info()["nnodes"] == 0
+    z0 = fpl.fp_compile_host(np.zeros((0, 1), dtype=np.int32), np.zeros(0), "E")
+    assert z0.info()["nnodes"] == 0
+
+
+@pytest.mark.parametrize("bad,code", [
+    ((np.array([[1], [1]]), np.array([1.0, 2.0]), "E", None, False), -2),      # duplicate
+    ((np.array([[1], [-1]]), np.array([1.0, 2.0]), "E", None, False), -1),     # negative exponent
+    ((np.array([[2], [1], [0]]), np.array([1.0, 2.0, 3.0]), "CUSTOM", np.array([0, 0, 1]), False), -3),
+    ((np.array([[1], [0]]), np.array([O.P_MODP, 1], dtype=np.uint64), "E", None, True), -1),
+    ((np.zeros((1, 9), dtype=np.int32), np.array([1.0]), "E", None, False), -6),  # too many variables
+])
+def test_compile_errors(bad, code):
+    with pytest.raises(fpl.FastPolyError) as ei:
+        fpl.fp_compile_host(*bad)
+    assert ei.value.code == code
+
+
+def test_eval_on_host_only_tree_is_rejected():
+    t = fpl.fp_compile_host(np.array([[1], [0]]), np.array([1.0, 2.0]), "E")
+    rc = fpl._lib.fp_eval(t.handle, 0, None, 0, None, None)
+    assert rc == -4

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA evaluation path against the CPU oracle, element by
+element on seeded inputs, for every value type, scheme and edge case.
+
+Bars (derived in the design doc):
+  MODP   bit-exact against the plain sum mod p.
+  IV64   bit-exact (both bounds) against the oracle's directed-rounding walk
+         on the oracle's own tree.
+  FP64   |gpu - oracle| <= (4k + g) u S, S = sum |c_e x^e|, u = 2^-53,
+         4k u S the stated bound of the GPU path, g u S the oracle's own
+         bound (g = max total degree + nvars + k).
+  FP32C  inputs rounded to float; |hi + lo - oracle| <= 2 gamma_{2k+64}(2^-24)^2 S
+         + g u S, and the median error below k 2^-48 S.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+import paper_1307_5655_gb300 as fpl
+from gpu_util import run
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def g32(k):
+    return k * U32 / (1 - k * U32)
+
+
+def check_f64(e, c, x, got):
+    want, S = O.eval_f64(e, c, x)
+    k = len(e)
+    g = int(np.asarray(e).sum(axis=1).max()) + np.asarray(e).shape[1] + k
+    tol = (4 * k + g) * U * S
+    bad = np.abs(got - want) > tol
+    assert not bad.any(), (np.nonzero(bad)[0][:5], got[bad][:5], want[bad][:5])
+
+
+def check_f32c(e, c, x, got):
+    c32 = W.to_f32(c).astype(np.float64)
+    x32 = W.to_f32(x).astype(np.float64)
+    want, S = O.eval_f64(e, c32, x32)
+    k = len(e)
+    g = int(np.asarray(e).sum(axis=1).max()) + np.asarray(e).shape[1] + k
+    val = got[0].astype(np.float64) + got[1].astype(np.float64)
+    err = np.abs(val - want)
+    tol = 2 * g32(2 * k + 64) ** 2 * S + g * U * S + 1e-300
+    assert np.all(err <= tol), (err / S).max()
+    assert np.median(err / S) <= k * 2.0 ** -48
+    return err / S
+
+
+def check_modp(e, c, x, got):
+    assert np.array_equal(got, O.eval_modp(e, c, x))
+
+
+def check_iv64(e, c, lo, hi, scheme, got, ftab=None):
+    t = O.build_tree(e, scheme, ftab)
+    rlo, rhi = O.walk_iv64(t, t.node_coeffs(c, np.float64), lo, hi)
+    assert np.array_equal(got[0], rlo), np.nonzero(got[0] != rlo)[0][:5]
+    assert np.array_equal(got[1], rhi), np.nonzero(got[1] != rhi)[0][:5]
+
+
+# ----------------------------------------------------------------- univariate
+KS = [1, 2, 3, 17, 100, 1000, 1024]
+SCHEMES = ["D", "H", "E", "B"]
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_f64_univariate(k, scheme):
+    e, c, x = W.univariate_case(k, 3000 + 17, 10 + k)
+    t = fpl.fp_compile(e, c, scheme)
+    check_f64(e, c, x, run(t, "f64", x))
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_f32c_univariate(k, scheme):
+    e, c, x = W.univariate_case(k, 3000 + 17, 20 + k)
+    t = fpl.fp_compile(e, c, scheme)
+    check_f32c(e, c, x, run(t, "f32c", x))
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_modp_univariate(k, scheme):
+    e, c, x = W.univariate_case(k, 3000 + 17, 30 + k, "modp")
+    t = fpl.fp_compile(e, c, scheme, modp=True)
+    check_modp(e, c, x, run(t, "modp", x))
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_iv64_univariate(k, scheme):
+    e, c, (lo, hi) = W.univariate_case(k, 1000 + 17, 40 + k, "iv64")
+    t = fpl.fp_compile(e, c, scheme)
+    check_iv64(e, c, lo, hi, scheme, run(t, "iv64", (lo, hi)))
+
+
+# ----------------------------------------------------------------- multivariate
+MULTI = [(2, "graded", 60), (3, "total", 10), (3, "sparse", 80), (4, "graded", 50)]
+
+
+def _multi(nvars, kind, size, seed):
+    if kind == "graded":
+        e = W.graded_prefix_exps(size, nvars)
+    elif kind == "total":
+        e = W.total_degree_exps(nvars, size)
+    else:
+        r = W.rng(seed)
+        e = np.array(sorted({tuple(int(v) for v in r.integers(0, 7, size=nvars)) for _ in range(size)}),
+                     dtype=np.int32)
+    return e
+
+
+@pytest.mark.parametrize("nvars,kind,size", MULTI)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_multivariate_all_types(nvars, kind, size, scheme):
+    e = _multi(nvars, kind, size, 5)
+    c = W.uniform_f64(len(e), 6)
+    e, c = W.shuffled(e, c, 7)
+    npts = 2000 + 3
+    x = W.points_f64(nvars, npts, 8)
+    t = fpl.fp_compile(e, c, scheme)
+    check_f64(e, c, x, run(t, "f64", x))
+    check_f32c(e, c, x, run(t, "f32c", x))
+    lo, hi = W.boxes(nvars, 500 + 3, 9)
+    check_iv64(e, c, lo, hi, scheme, run(t, "iv64", (lo, hi)))
+    cm = W.residues(len(e), 10)
+    xm = W.points_modp(nvars, npts, 11)
+    tm = fpl.fp_compile(e, cm, scheme, modp=True)
+    check_modp(e, cm, xm, run(tm, "modp", xm))
+
+
+# ----------------------------------------------------------------- edge cases
+def test_zero_points_is_noop():
+    t = fpl.fp_compile(W.dense_univariate_exps(5), W.uniform_f64(5, 1), "E")
+    import torch
+    x = torch.zeros((1, 0), dtype=torch.float64, device="cuda")
+    out = fpl.fp_eval(t, "f64", x)
+    assert out.numel() == 0
+
+
+def test_single_point_and_single_term():
+    e = np.array([[7]], dtype=np.int32)
+    c = np.array([0.75])
+    x = np.array([[0.5]])
+    t = fpl.fp_compile(e, c, "E")
+    assert run(t, "f64", x)[0] == 0.75 * 0.5 ** 7
+    lo, hi = W.boxes(1, 1, 3)
+    check_iv64(e, c, lo, hi, "E", run(t, "iv64", (lo, hi)))
+
+
+def test_zero_polynomial_all_types():
+    e = np.array([[3], [1]], dtype=np.int32)
+    t = fpl.fp_compile(e, np.zeros(2), "E")
+    x = W.points_f64(1, 257, 1)
+    assert np.all(run(t, "f64", x) == 0)
+    assert np.all(run(t, "f32c", x) == 0)
+    assert np.all(run(t, "iv64", (x, x)) == 0)
+    tm = fpl.fp_compile(e, np.zeros(2, dtype=np.uint64), "E", modp=True)
+    assert np.all(run(tm, "modp", W.points_modp(1, 257, 2)) == 0)
+
+
+def test_sparse_root_degree_and_gaps():
+    e = np.array([[900], [512], [77], [40], [13]], dtype=np.int32)
+    c = W.uniform_f64(5, 4)
+    x = W.points_f64(1, 999, 5)
+    for s in SCHEMES:
+        t = fpl.fp_compile(e, c, s)
+        check_f64(e, c, x, run(t, "f64", x))
+        lo, hi = W.boxes(1, 999, 6)
+        check_iv64(e, c, lo, hi, s, run(t, "iv64", (lo, hi)))
+
+
+def test_deep_lazy_height_custom_scheme():
+    """Random function schemes give lazy heights well above E/B's."""
+    k = 3000
+    r = W.rng(3)
+    ft = np.zeros(k + 1, dtype=np.int32)
+    for n in range(1, k + 1):
+        ft[n] = max(1, min(n, int(r.integers(1, 4)) if n % 3 else n // 2 + 1))
+    e, c, x = W.univariate_case(k, 1000 + 1, 12)
+    t = fpl.fp_compile(e, c, "CUSTOM", ft)
+    assert t.info()["max_lazy_height"] >= 2
+    check_f64(e, c, x, run(t, "f64", x))
+    cm = W.residues(k, 4)
+    tm = fpl.fp_compile(e, cm, "CUSTOM", ft, modp=True)
+    xm = W.points_modp(1, 1001, 5)
+    check_modp(e, cm, xm, run(tm, "modp", xm))
+
+
+def test_modp_noncanonical_points_are_reduced():
+    e, c, x = W.univariate_case(50, 300, 7, "modp")
+    t = fpl.fp_compile(e, c, "E", modp=True)
+    xr = x.copy()
+    big = np.array([O.P_MODP + 5, 2 ** 64 - 1], dtype=np.uint64)
+    xr[0, :2] = big
+    want = O.eval_modp(e, c, np.array([[5, (2 ** 64 - 1) - O.P_MODP]], dtype=np.uint64))
+    got = run(t, "modp", xr)
+    assert np.array_equal(got[:2], want)
+
+
+def test_dtype_mismatch_rejected():
+    t = fpl.fp_compile(W.dense_univariate_exps(3), W.residues(3, 1), "E", modp=True)
+    with pytest.raises(fpl.FastPolyError):
+        run(t, "f64", W.points_f64(1, 10, 1))
+
+
+def test_host_entry_point_matches_device():
+    e, c, x = W.univariate_case(300, 4097, 13)
+    t = fpl.fp_compile(e, c, "B")
+    assert np.array_equal(fpl.fp_eval_host(t, "f64", x), run(t, "f64", x))
+
+
+def test_plain_baseline_kernel():
+    import torch
+    e, c, x = W.univariate_case(1024, 5000, 14)
+    by_degree = torch.from_numpy(c[::-1].copy()).cuda()
+    got = fpl.fp_eval_plain_f64(by_degree, torch.from_numpy(x).cuda()).cpu().numpy()
+    check_f64(e, c, x, got)
+
+
+# ----------------------------------------------------------------- full sizes, sampled
+def _sample(npts, m, seed):
+    return np.sort(W.rng(seed).choice(npts, size=m, replace=False))
+
+
+def test_config1_full():
+    """1024 terms, Estrin, 65536 points: every point checked."""
+    e, c, x = W.univariate_case(1024, 65536, 101)
+    t = fpl.fp_compile(e, c, "E")
+    check_f64(e, c, x, run(t, "f64", x))
+
+
+@pytest.mark.parametrize("k", [1000, 3000, 10007])
+def test_config2_full_size_sampled(k):
+    """2^24 points per (k, scheme); 512 sampled outputs checked per launch."""
+    npts = 1 << 24
+    e, c, x = W.univariate_case(k, npts, 200 + k)
+    idx = _sample(npts, 512, k)
+    for s in ("H", "E", "B"):
+        t = fpl.fp_compile(e, c, s)
+        got = run(t, "f64", x)
+        check_f64(e, c, x[:, idx], got[idx])
+        got32 = run(t, "f32c", x)
+        check_f32c(e, c, x[:, idx], got32[:, idx])
+
+
+def test_config2_exact_rational_bound():
+    """North-star FP64 bound against exact rationals: |r - p| <= 4 n u cond."""
+    from fractions import Fraction
+    from oracle import exact as X
+    k = 10007
+    e, c, x = W.univariate_case(k, 1 << 16, 777)
+    t = fpl.fp_compile(e, c, "B")
+    got = run(t, "f64", x)
+    coeffs_by_degree = c[::-1]
+    for j in (0, 1, 2):
+        v, s = X.exact_horner_univariate(coeffs_by_degree, x[0, j])
+        assert abs(Fraction(got[j]) - v) <= 4 * (k - 1) * Fraction(U) * s
+
+
+def test_config3_full_size_sampled():
+    """Trivariate total degree 40 (12341 terms), 2^22 boxes and residues."""
+    npts = 1 << 22
+    e, c, (lo, hi) = W.trivariate_case(40, npts, 300, "iv64")
+    idx = _sample(npts, 48, 3)
+    t = fpl.fp_compile(e, c, "E")
+    got = run(t, "iv64", (lo, hi))
+    check_iv64(e, c, lo[:, idx], hi[:, idx], "E", got[:, idx])
+    em, cm, xm = W.trivariate_case(40, npts, 301, "modp")
+    tm = fpl.fp_compile(em, cm, "E", modp=True)
+    gm = run(tm, "modp", xm)
+    idx = _sample(npts, 256, 4)
+    check_modp(em, cm, xm[:, idx], gm[idx])
