@@ -41,7 +41,7 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6 * 2 / 1e12
 
-CPU_SAMPLE_POINTS = 1 << 15  # points per evaluation in the CPU-oracle sample
+CPU_SAMPLE_POINTS = 1 << 18  # points per evaluation in the CPU-oracle sample
 
 
 def workload_config():
@@ -287,7 +287,7 @@ def run_ours(args):
         if world == 1 and not args.no_cpu:
             rate, cores, wall = cpu_oracle_rate()
             cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "2^15 points per (k, value type) of the same workload; the plain-sum oracle does not "
+                   "sample": "2^18 points per (k, value type) of the same workload; the plain-sum oracle does not "
                              "depend on the scheme (%.1f s wall)" % wall}
         traffic = None
         tf = os.path.join(ROOT, "profiles", "eval_f64_traffic.txt")
@@ -319,15 +319,52 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One FP64 (or other type) evaluation of a dense polynomial at 2^24 points,
+    after one warm-up launch: the small case the ncu captures use."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    k, scheme, dt = args.profile_k, args.profile_scheme, args.profile_dtype
+    torch.cuda.set_device(0)
+    x = W.points_f64(1, NPTS, SEED + 1)
+    e, c, _ = W.univariate_case(k, 1, SEED + k)
+    if dt == "modp":
+        e, c, _ = W.univariate_case(k, 1, SEED + k, "modp")
+        pts = torch.from_numpy(W.points_modp(1, NPTS, SEED + 2).view(np.int64)).cuda()
+        t = fpl.fp_compile(e, c, scheme, modp=True)
+    elif dt == "f32c":
+        pts = torch.from_numpy(W.to_f32(x)).cuda()
+        t = fpl.fp_compile(e, c, scheme)
+    elif dt == "iv64":
+        lo, hi = W.boxes(1, NPTS, SEED + 3)
+        pts = torch.from_numpy(np.ascontiguousarray(np.stack([lo, hi], axis=1))).cuda()
+        t = fpl.fp_compile(e, c, scheme)
+    else:
+        pts = torch.from_numpy(x).cuda()
+        t = fpl.fp_compile(e, c, scheme)
+    for _ in range(2):
+        fpl.fp_eval(t, dt, pts)
+    torch.cuda.synchronize()
+    print("profile case done: k=%d scheme=%s dtype=%s points=%d" % (k, scheme, dt, NPTS))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run two launches of one evaluation (for ncu) and exit")
+    ap.add_argument("--profile-k", type=int, default=3000)
+    ap.add_argument("--profile-scheme", default="E")
+    ap.add_argument("--profile-dtype", default="f64")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
