@@ -207,7 +207,7 @@ def run_ours(args):
                     fpl.fp_eval(t, "f32c", d32, out=out32, stream=stream)
                 if record:
                     b.record(stream)
-                    launches.append((dt, k, a, b))
+                    launches.append((dt, k, a, b, s))
 
     for _ in range(args.warmup):
         step(False)
@@ -235,10 +235,16 @@ def run_ours(args):
         ms = float(tt.item())
 
     # dominant kernel: FP64 evaluation
-    f64_ms = sum(a.elapsed_time(b) for dt, k, a, b in launches if dt == "f64")
-    f32_ms = sum(a.elapsed_time(b) for dt, k, a, b in launches if dt == "f32c")
-    f64_flops = sum(2.0 * k * NPTS for dt, k, a, b in launches if dt == "f64")
+    f64_ms = sum(a.elapsed_time(b) for dt, k, a, b, _ in launches if dt == "f64")
+    f32_ms = sum(a.elapsed_time(b) for dt, k, a, b, _ in launches if dt == "f32c")
+    f64_flops = sum(2.0 * k * NPTS for dt, k, a, b, _ in launches if dt == "f64")
     f64_launches = sum(1 for dt, *_ in launches if dt == "f64")
+    per_eval = {}
+    for dt, k, a, b, s in launches:
+        key = "%s/%s/%d" % (dt, s, k)
+        per_eval.setdefault(key, []).append(a.elapsed_time(b))
+    per_eval = {key: {"ms": float(np.mean(v)), "G_term_evals_per_s": int(key.split("/")[2]) * NPTS / (np.mean(v) * 1e6)}
+                for key, v in per_eval.items()}
     achieved = f64_flops / (f64_ms * 1e-3) / 1e12
 
     # plain FP64 kernel (one thread per point, Horner) on the same FP64 evaluations
@@ -301,11 +307,12 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64/f32c", "data": "synthetic", "config": workload_config(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": "eval_kernel<F64,1,true> (FP64 walk)",
+                         "kernel": "eval_ops_kernel<F64,1,scheme> (FP64 grouped-op walk)",
                          "peak_basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 FLOP (recipe unit counts "
                                        "and max clock); 1 term-eval = 1 multiply + 1 add",
                          "launches": f64_launches, "avg_launch_ms": f64_ms / max(1, f64_launches)},
             "kernel_time_share": {"f64": f64_ms / (f64_ms + f32_ms), "f32c": f32_ms / (f64_ms + f32_ms)},
+            "per_evaluation": per_eval,
             "plain_f64_kernel": {"value": plain_rate, "unit": UNIT,
                                  "ours_f64_same_work": ours_f64_rate,
                                  "speedup": ours_f64_rate / plain_rate},
@@ -344,9 +351,9 @@ def run_profile_case(args):
         pts = torch.from_numpy(x).cuda()
         t = fpl.fp_compile(e, c, scheme)
     for _ in range(2):
-        fpl.fp_eval(t, dt, pts)
+        fpl.fp_eval_ex(t, dt, pts, kernel=args.profile_kernel)
     torch.cuda.synchronize()
-    print("profile case done: k=%d scheme=%s dtype=%s points=%d" % (k, scheme, dt, NPTS))
+    print("profile case done: k=%d scheme=%s dtype=%s kernel=%s points=%d" % (k, scheme, dt, args.profile_kernel, NPTS))
 
 
 def main():
@@ -356,6 +363,7 @@ def main():
     ap.add_argument("--profile-k", type=int, default=3000)
     ap.add_argument("--profile-scheme", default="E")
     ap.add_argument("--profile-dtype", default="f64")
+    ap.add_argument("--profile-kernel", default="auto", choices=["auto", "ops", "node"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

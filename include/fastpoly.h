@@ -127,6 +127,27 @@ void fp_free(fp_tree* t);
 int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out,
             void* stream);
 
+/* Launch configuration for fp_eval_ex.
+ *   kernel  0: automatic;
+ *           1: grouped ops -- chains of single-child nodes run as a register
+ *              loop and dense subtrees of <= 16 terms (univariate, schemes E
+ *              and B) by a compiled template of the scheme's split; FP64,
+ *              FP32C and MODP only, power table in shared memory (else
+ *              FP_E_TOO_LARGE);
+ *           2: node by node (any tree and value type).
+ * MODP results are identical for every configuration; FP64 and FP32C results
+ * of configuration 1 may differ in the last bits (another summation order
+ * inside blocks) and satisfy the same error bounds. */
+typedef struct {
+  int kernel;
+  int reserved[3];
+} fp_launch_cfg;
+
+/* fp_eval_ex -- fp_eval with an explicit launch configuration (cfg may be
+ * NULL: automatic). */
+int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out,
+               void* stream, const fp_launch_cfg* cfg);
+
 /* fp_eval_host -- the same as fp_eval with host buffers: copies the points to
  * the device, evaluates, copies the result back and synchronises `stream`.
  * Device buffers are allocated per call (stream-ordered). */

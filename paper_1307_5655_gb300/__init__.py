@@ -28,6 +28,7 @@ for _name, _args in {
     "fp_compile_host": [_I, _I64, _P, _P, _I, _I, _P, _I64, ctypes.POINTER(_P)],
     "fp_eval": [_P, _I, _P, _I64, _P, _P],
     "fp_eval_host": [_P, _I, _P, _I64, _P, _P],
+    "fp_eval_ex": [_P, _I, _P, _I64, _P, _P, _P],
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
@@ -160,6 +161,28 @@ def fp_eval(tree, dtype, points, npts=None, out=None, stream=None):
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
     _check(_lib.fp_eval(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream)), "fp_eval")
+    return out
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+KERNELS = {"auto": 0, "ops": 1, "node": 2}
+
+
+def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=None):
+    """fp_eval with an explicit kernel choice ('auto', 'ops', 'node')."""
+    import torch
+    if not points.is_cuda or not points.is_contiguous():
+        raise ValueError("points must be a contiguous CUDA tensor")
+    if npts is None:
+        npts = points.shape[-1]
+    if out is None:
+        out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    cfg = LaunchCfg(KERNELS[kernel])
+    _check(_lib.fp_eval_ex(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
+                           ctypes.byref(cfg)), "fp_eval_ex")
     return out
 
 

@@ -21,10 +21,27 @@ int upload(const std::vector<T>& h, T** d) {
 
 void release(fp_tree* t) {
   DeviceSchedule& d = t->dev;
-  void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64};
+  void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64,
+                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceSchedule{};
+}
+
+// op records and the coefficient stream in the coefficient type C
+template <class C, class H>
+void build_ops(const fp_tree* t, const std::vector<H>& c, std::vector<OpRec<C>>& recs, std::vector<C>& st) {
+  recs.resize(t->ops.size());
+  for (size_t i = 0; i < t->ops.size(); ++i) {
+    OpRec<C> r{};
+    r.x = t->ops[i].x; r.y = t->ops[i].y; r.z = t->ops[i].z; r.w = t->ops[i].w;
+    r.a = t->op_a_node[i] >= 0 ? (C)c[t->op_a_node[i]] : C(0);
+    r.b = t->op_b_node[i] >= 0 ? (C)c[t->op_b_node[i]] : C(0);
+    recs[i] = r;
+  }
+  st.assign(t->stream.size() + kStreamAlign, C(0));  // padded so 4-wide loads stay in bounds
+  for (size_t k = 0; k < t->stream.size(); ++k)
+    if (t->stream[k] >= 0) st[k] = (C)c[t->stream[k]];
 }
 
 int upload_schedule(fp_tree* t) {
@@ -47,6 +64,11 @@ int upload_schedule(fp_tree* t) {
     }
     rc = upload(a, &d.ca_u64);
     if (rc == FP_OK) rc = upload(b, &d.cb_u64);
+    std::vector<OpRec<uint64_t>> recs;
+    std::vector<uint64_t> st;
+    build_ops(t, t->c_u64, recs, st);
+    if (rc == FP_OK) rc = upload(recs, &d.ops_u64);
+    if (rc == FP_OK) rc = upload(st, &d.st_u64);
   } else {
     std::vector<double> a(S), b(S);
     std::vector<float> af(S), bf(S);
@@ -60,6 +82,17 @@ int upload_schedule(fp_tree* t) {
     if (rc == FP_OK) rc = upload(b, &d.cb_f64);
     if (rc == FP_OK) rc = upload(af, &d.ca_f32);
     if (rc == FP_OK) rc = upload(bf, &d.cb_f32);
+    std::vector<OpRec<double>> recs;
+    std::vector<double> st;
+    build_ops(t, t->c_f64, recs, st);
+    if (rc == FP_OK) rc = upload(recs, &d.ops_f64);
+    if (rc == FP_OK) rc = upload(st, &d.st_f64);
+    std::vector<float> cf(t->c_f64.begin(), t->c_f64.end());
+    std::vector<OpRec<float>> recs32;
+    std::vector<float> st32;
+    build_ops(t, cf, recs32, st32);
+    if (rc == FP_OK) rc = upload(recs32, &d.ops_f32);
+    if (rc == FP_OK) rc = upload(st32, &d.st_f32);
   }
   return rc;
 }
@@ -113,7 +146,9 @@ __global__ void plain_horner_kernel(const double* __restrict__ c, int64_t nc, co
 
 }  // namespace
 
-int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st) {
+int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st,
+                int variant = 0) {
+  if (variant < 0 || variant > 2) return FP_E_BAD_VALUE;
   if (!t) return FP_E_BAD_VALUE;
   if ((int)dt < FP_F64 || (int)dt > FP_MODP) return FP_E_DTYPE;
   if (!dtype_ok(t, dt)) return FP_E_DTYPE;
@@ -143,12 +178,17 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
   a.points = points;
   a.npts = npts;
   a.out = out;
+  OpArgs o{};
+  o.nops = (int64_t)t->ops.size();
+  o.pid_x1 = t->pid_x1;
+  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->pid_pow[d];
   const int64_t root = t->nnodes - 1;
   size_t vbytes = 8, pbytes = 8;
   int ppt = 1;
   switch (dt) {
     case FP_F64: {
       a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
+      o.recs = t->dev.ops_f64; o.stream = t->dev.st_f64;
       std::memcpy(&a.root_c, &t->c_f64[root], 8);
       break;
     }
@@ -160,6 +200,7 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
     }
     case FP_F32C: {
       a.ca = t->dev.ca_f32; a.cb = t->dev.cb_f32;
+      o.recs = t->dev.ops_f32; o.stream = t->dev.st_f32;
       const float c = (float)t->c_f64[root];
       uint32_t bits;
       std::memcpy(&bits, &c, 4);
@@ -169,6 +210,7 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
     }
     case FP_MODP: {
       a.ca = t->dev.ca_u64; a.cb = t->dev.cb_u64;
+      o.recs = t->dev.ops_u64; o.stream = t->dev.st_u64;
       a.root_c = t->c_u64[root];
       ppt = 2;
       break;
@@ -178,11 +220,12 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
   if (smem > kSmemMax) return FP_E_TOO_LARGE;
   cudaError_t e = cudaSuccess;
   switch (dt) {
-    case FP_F64: e = launch_eval_f64(a, st); break;
-    case FP_F32C: e = launch_eval_f32c(a, st); break;
-    case FP_IV64: e = launch_eval_iv64(a, st); break;
-    case FP_MODP: e = launch_eval_modp(a, st); break;
+    case FP_F64: e = launch_eval_f64(a, o, t->block_scheme, st, variant); break;
+    case FP_F32C: e = launch_eval_f32c(a, o, t->block_scheme, st, variant); break;
+    case FP_IV64: e = launch_eval_iv64(a, o, t->block_scheme, st, variant); break;
+    case FP_MODP: e = launch_eval_modp(a, o, t->block_scheme, st, variant); break;
   }
+  if (e == cudaErrorInvalidValue && variant == 1) { cudaGetLastError(); return FP_E_TOO_LARGE; }
   return e == cudaSuccess ? FP_OK : FP_E_CUDA;
 }
 
@@ -240,6 +283,11 @@ void fp_free(fp_tree* t) {
 
 int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream) {
   return eval_device(t, dtype, points, npts, out, (cudaStream_t)stream);
+}
+
+int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
+               const fp_launch_cfg* cfg) {
+  return eval_device(t, dtype, points, npts, out, (cudaStream_t)stream, cfg ? cfg->kernel : 0);
 }
 
 int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts, void* out_host,

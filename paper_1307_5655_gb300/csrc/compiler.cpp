@@ -249,6 +249,79 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
                  (uint32_t)is_first[i] << kCtrlFirst |
                  (uint32_t)pid.at({t->pd_var[i], t->pd[i]}) << kCtrlPid;
   }
+  // a5': group the walk into ops (fused value types).  A block is a maximal
+  // subtree of at most kMaxBlock nodes over consecutive exponents of a
+  // univariate polynomial under E or B: its shape is the scheme's own split
+  // applied to a dense run, so a compile-time template evaluates it.  A chain
+  // is a run j0..j1 where each node is the only child of the next.
+  {
+    std::vector<int64_t> size(N, 1), nchild(N, 0);
+    for (int64_t i = 0; i + 1 < N; ++i) {
+      size[t->parent[i]] += size[i];
+      nchild[t->parent[i]]++;
+    }
+    const bool blocks = nvars == 1 && (scheme == FP_SCHEME_E || scheme == FP_SCHEME_B);
+    t->block_scheme = blocks ? (int)scheme : 0;
+    std::vector<int64_t> block_len(N, 0);  // at the block's first node
+    if (blocks) {
+      for (int64_t r = 0; r + 1 < N; ++r) {
+        const int64_t s = size[r], q = t->parent[r];
+        if (s < 2 || s > kMaxBlock) continue;
+        if (q != N - 1 && size[q] <= kMaxBlock) continue;  // not maximal
+        const int64_t j0 = r - s + 1;
+        if (t->node_e[j0] - t->node_e[r] != s - 1) continue;  // not a dense run
+        if (j0 >= (1ll << 32)) continue;
+        block_len[j0] = s;
+      }
+    }
+    auto pid_of = [&](int64_t i) { return (uint32_t)pid.at({t->pd_var[i], t->pd[i]}); };
+    auto emit = [&](uint32_t kind, int64_t j0, int64_t j1) {
+      const int64_t q = t->parent[j1];
+      const uint32_t leaf = has_child[j0] ? 0u : 1u;
+      uint32_t x = kind | (leaf ? 0u : (uint32_t)t->lh[j0]) << kOpS | (uint32_t)t->lh[q] << kOpD |
+                   leaf << kOpLeaf | (uint32_t)is_first[j1] << kOpFirst | pid_of(j1) << kOpPid;
+      if (kind == kOpChain) {
+        bool uni = true;
+        for (int64_t j = j0; j < j1; ++j) uni = uni && pid_of(j) == pid_of(j0);
+        x |= (uni ? 1u : 0u) << kOpUniform;
+      }
+      uint32_t off = 0;
+      if (kind != kOpNode) {
+        while (t->stream.size() % kStreamAlign) t->stream.push_back(-1);
+        off = (uint32_t)t->stream.size();
+        for (int64_t j = j0; j <= j1; ++j) t->stream.push_back(j);
+      }
+      uint4 w;
+      w.x = x;
+      w.y = (uint32_t)(j1 - j0);
+      w.z = (uint32_t)j0;
+      w.w = off;
+      t->ops.push_back(w);
+      t->op_a_node.push_back(kind == kOpNode && leaf ? j0 : -1);
+      t->op_b_node.push_back(is_first[j1] ? q : -1);
+    };
+    t->ops.clear();
+    t->op_a_node.clear();
+    t->op_b_node.clear();
+    t->stream.clear();
+    for (int64_t i = 0; i + 1 < N;) {
+      if (block_len[i] > 0) {
+        emit(kOpBlock, i, i + block_len[i] - 1);
+        i += block_len[i];
+        continue;
+      }
+      int64_t j = i;
+      while (j + 1 < N - 1 && j - i + 1 < kMaxChain && t->parent[j] == j + 1 && nchild[j + 1] == 1 &&
+             block_len[j + 1] == 0)
+        ++j;
+      emit(j > i ? kOpChain : kOpNode, i, j);
+      i = j + 1;
+    }
+    t->pid_x1 = pid.count({0, 1}) ? pid.at({0, 1}) : -1;
+    for (int d = 0; d <= kMaxBlock; ++d) t->pid_pow[d] = pid.count({0, d}) ? pid.at({0, d}) : -1;
+    if (t->pid_x1 < 0) t->block_scheme = 0;
+  }
+
   t->root_leaf = has_child[N - 1] ? 0 : 1;
   t->root_lh = t->lh[N - 1];
   t->root_pid = t->pd[N - 1] > 0 ? pid.at({0, t->pd[N - 1]}) : -1;

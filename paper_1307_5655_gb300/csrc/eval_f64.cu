@@ -1,6 +1,8 @@
-// Instantiation of the evaluation kernel for the F64 value type.
+// Instantiation of the evaluation kernels for the F64 value type.
 #include "eval_kernel.cuh"
 
 namespace fp {
-cudaError_t launch_eval_f64(const EvalArgs& a, cudaStream_t s) { return launch_eval<F64, 1>(a, s); }
+cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant) {
+  return launch_eval_fused<F64, 1, 1>(a, o, scheme, s, variant);
+}
 }  // namespace fp

@@ -1,6 +1,10 @@
-// Instantiation of the evaluation kernel for the IV64 value type.
+// Instantiation of the evaluation kernel for the IV64 value type (node by
+// node, in the paper's operation order).
 #include "eval_kernel.cuh"
 
 namespace fp {
-cudaError_t launch_eval_iv64(const EvalArgs& a, cudaStream_t s) { return launch_eval<IV64, 1>(a, s); }
+cudaError_t launch_eval_iv64(const EvalArgs& a, const OpArgs&, int, cudaStream_t s, int variant) {
+  if (variant == 1) return cudaErrorInvalidValue;
+  return launch_eval_smem<IV64, 1>(a, s);
+}
 }  // namespace fp

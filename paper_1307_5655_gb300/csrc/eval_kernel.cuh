@@ -22,6 +22,8 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cstring>
+#include <type_traits>
 
 #include "tree.hpp"
 
@@ -73,6 +75,8 @@ struct F64 {
     const double init = first ? cb : *dst;
     *dst = fma(s, xd, init);
   }
+  static __device__ __forceinline__ val from_coef(coef c) { return c; }
+  static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return __dmul_rn(r, xd); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((double*)out)[idx] = r; }
@@ -111,9 +115,10 @@ struct F32C {
     const float e = __fmaf_rn(a.x, x.x, -p);
     return renorm(p, __fmaf_rn(a.y, x.x, e));
   }
-  static __device__ __forceinline__ void node(bool leaf, bool first, coef ca, coef cb, const val* src, val* dst, pw xd) {
-    const float2 s = leaf ? make_float2(ca, 0.0f) : *src;
-    const float2 init = first ? make_float2(cb, 0.0f) : *dst;
+  // s * x^d + init with the rounding errors of the product and the sum
+  // (exact by TwoProduct / TwoSum) and the first-order terms of the
+  // operands' own corrections gathered in lo
+  static __device__ __forceinline__ val mad(val s, pw xd, val init) {
     const float p = __fmul_rn(s.x, xd.x);
     const float pe = __fmaf_rn(s.x, xd.x, -p);
     float h, se;
@@ -121,7 +126,13 @@ struct F32C {
     float lo = __fadd_rn(init.y, __fadd_rn(pe, se));
     lo = __fmaf_rn(s.y, xd.x, lo);
     lo = __fmaf_rn(s.x, xd.y, lo);
-    *dst = make_float2(h, lo);
+    return make_float2(h, lo);
+  }
+  static __device__ __forceinline__ val from_coef(coef c) { return make_float2(c, 0.0f); }
+  static __device__ __forceinline__ void node(bool leaf, bool first, coef ca, coef cb, const val* src, val* dst, pw xd) {
+    const float2 s = leaf ? make_float2(ca, 0.0f) : *src;
+    const float2 init = first ? make_float2(cb, 0.0f) : *dst;
+    *dst = mad(s, xd, init);
   }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? make_float2(c, 0.0f) : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) {
@@ -176,6 +187,8 @@ struct MODP {
     const uint64_t init = first ? cb : *dst;
     *dst = mul_add(s, xd, init);
   }
+  static __device__ __forceinline__ val from_coef(coef c) { return c; }
+  static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return mul_add(r, xd, 0); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((uint64_t*)out)[idx] = r; }
@@ -373,13 +386,249 @@ __global__ void __launch_bounds__(kTPB) eval_kernel(const EvalArgs g) {
   }
 }
 
-// Launch helpers (defined per type in eval_<type>.cu).
-size_t eval_smem_bytes(fp_dtype dt, int nslot, int npow, int ppt);
-int eval_ppt(fp_dtype dt);
-cudaError_t launch_eval_f64(const EvalArgs& a, cudaStream_t s);
-cudaError_t launch_eval_f32c(const EvalArgs& a, cudaStream_t s);
-cudaError_t launch_eval_iv64(const EvalArgs& a, cudaStream_t s);
-cudaError_t launch_eval_modp(const EvalArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- grouped-op kernel
+// The walk grouped into ops (see kOpNode / kOpChain / kOpBlock): the fused
+// value types evaluate chains as a register loop and dense subtree blocks with
+// a compile-time template of the scheme's split, and dispatch once per op.
+
+template <class T>
+__device__ __forceinline__ T shfl_any(T v, int src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+  if constexpr (sizeof(T) == 4) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u = __shfl_sync(0xffffffffu, u, src);
+    memcpy(&v, &u, 4);
+  } else {
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    u = __shfl_sync(0xffffffffu, u, src);
+    memcpy(&v, &u, 8);
+  }
+  return v;
+}
+
+struct OpArgs {
+  const void* recs;    // OpRec<coef> [nops]
+  const void* stream;  // coefficients of chains and blocks
+  int64_t nops;
+  int pid_x1;       // power slot of x
+  int pid_pow[kMaxBlock + 1];  // power slot of x^d for the block templates (-1: absent)
+};
+
+template <int SCHEME>
+__host__ __device__ constexpr int scheme_split(int n) {
+  if (SCHEME == FP_SCHEME_E) {
+    int f = 1;
+    while (2 * f <= n) f *= 2;
+    return f;
+  }
+  return (n + 1) / 2;  // FP_SCHEME_B
+}
+
+// which powers x^d (d <= kMaxBlock) a block template of the scheme can use
+template <int SCHEME>
+__host__ __device__ constexpr bool block_uses_power(int d) {
+  for (int m = 2; m <= kMaxBlock; ++m)  // sizes of dense runs inside a block
+    for (int n = 1; n < m; ++n)
+      if (scheme_split<SCHEME>(n) == d) return true;
+  return false;
+}
+
+// value of the tree T_f over the dense run c[LO..HI] (index order: c[LO] is
+// the highest term), relative to the exponent of c[HI]:
+//   T(run) = T(b) + T(a) x^f(n),  b = the f(n) lowest terms (Def. 1.2)
+template <class A, int SCHEME, int LO, int HI>
+__device__ __forceinline__ typename A::val block_eval(const typename A::coef (&c)[kMaxBlock],
+                                                      const typename A::pw (&xp)[kMaxBlock + 1]) {
+  if constexpr (LO == HI) {
+    return A::from_coef(c[HI]);
+  } else {
+    constexpr int n = HI - LO;
+    constexpr int f = scheme_split<SCHEME>(n);
+    const typename A::val b = block_eval<A, SCHEME, HI - f + 1, HI>(c, xp);
+    const typename A::val a = block_eval<A, SCHEME, LO, HI - f>(c, xp);
+    return A::mad(a, xp[f], b);
+  }
+}
+
+// powers a block template reads, closed under the power rule
+// (x^2k needs x^k; x^(2k+1) needs x^2k and x)
+template <int SCHEME>
+__host__ __device__ constexpr bool block_needs_power(int d) {
+  if (block_uses_power<SCHEME>(d)) return true;
+  for (int e = d + 1; e <= kMaxBlock; ++e) {
+    const bool dep = (e % 2 == 0) ? (e / 2 == d) : (e - 1 == d || d == 1);
+    if (dep && block_needs_power<SCHEME>(e)) return true;
+  }
+  return false;
+}
+
+template <class A, int SCHEME, int PPT>
+__device__ __forceinline__ void block_dispatch(int len, const typename A::coef (&c)[kMaxBlock],
+                                               const typename A::pw (&xp)[PPT][kMaxBlock + 1],
+                                               typename A::val (&v)[PPT]) {
+#define FP_BLOCK_CASE(L)                                                          \
+  case L:                                                                         \
+    _Pragma("unroll") for (int p = 0; p < PPT; ++p) v[p] = block_eval<A, SCHEME, 0, L - 1>(c, xp[p]); \
+    break;
+  switch (len) {
+    FP_BLOCK_CASE(2) FP_BLOCK_CASE(3) FP_BLOCK_CASE(4) FP_BLOCK_CASE(5) FP_BLOCK_CASE(6)
+    FP_BLOCK_CASE(7) FP_BLOCK_CASE(8) FP_BLOCK_CASE(9) FP_BLOCK_CASE(10) FP_BLOCK_CASE(11)
+    FP_BLOCK_CASE(12) FP_BLOCK_CASE(13) FP_BLOCK_CASE(14) FP_BLOCK_CASE(15) FP_BLOCK_CASE(16)
+    default: break;
+  }
+#undef FP_BLOCK_CASE
+}
+
+// 128-bit loads of an op record and of coefficient runs (read-only path)
+template <class C>
+__device__ __forceinline__ void load_rec(const OpRec<C>* r, uint4& h, C& a, C& b) {
+  h = __ldg(reinterpret_cast<const uint4*>(r));
+  if constexpr (sizeof(C) == 8) {
+    const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2*>(r) + 1);
+    memcpy(&a, &q.x, 8);
+    memcpy(&b, &q.y, 8);
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(r) + 2);
+    memcpy(&a, &q.x, 4);
+    memcpy(&b, &q.y, 4);
+  }
+}
+
+// coefficients st[off + 4q .. off + 4q + 3] (off is a multiple of 4)
+template <class C>
+__device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]) {
+  if constexpr (sizeof(C) == 8) {
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(st + off) + 2 * q;
+    const ulonglong2 u0 = __ldg(v), u1 = __ldg(v + 1);
+    memcpy(&c[0], &u0.x, 8); memcpy(&c[1], &u0.y, 8); memcpy(&c[2], &u1.x, 8); memcpy(&c[3], &u1.y, 8);
+  } else {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(st + off) + q);
+    memcpy(&c[0], &u.x, 4); memcpy(&c[1], &u.y, 4); memcpy(&c[2], &u.z, 4); memcpy(&c[3], &u.w, 4);
+  }
+}
+
+template <class A, int PPT, int SCHEME>
+__global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using V = typename A::val;
+  using W = typename A::pw;
+  using C = typename A::coef;
+  V* acc = reinterpret_cast<V*>(smem_raw);  // [nslot][PPT][TPB]
+  W* pw = reinterpret_cast<W*>(smem_raw + sizeof(V) * (size_t)g.nslot * PPT * kTPB);  // [npow][PPT][TPB]
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * (kTPB * PPT);
+
+  for (int k = 0; k < g.npow; ++k) {
+    const uint32_t w = __ldg(g.pow_prog + k);
+    const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int64_t idx = base + p * kTPB + tid;
+      W r;
+      if (op == kPowLoad) r = idx < g.npts ? A::load_point(g.points, (int)a1, idx, g.npts) : A::dummy_point();
+      else if (op == kPowSq) r = A::square(pw[(a1 * PPT + p) * kTPB + tid]);
+      else r = A::mulx(pw[(a1 * PPT + p) * kTPB + tid], pw[(a2 * PPT + p) * kTPB + tid]);
+      pw[(k * PPT + p) * kTPB + tid] = r;
+    }
+  }
+
+  // powers x^d of the block templates: every one is a partial degree of the
+  // tree, so it is read from the power table (recomputing them per block
+  // would cost FP64 multiplies)
+  W xp[PPT][kMaxBlock + 1];
+  if constexpr (SCHEME != 0) {
+#pragma unroll
+    for (int d = 1; d <= kMaxBlock; ++d) {
+      if (block_uses_power<SCHEME>(d)) {
+        const int q = o.pid_pow[d] < 0 ? 0 : o.pid_pow[d];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) xp[p][d] = pw[(q * PPT + p) * kTPB + tid];
+      }
+    }
+  }
+
+  const OpRec<C>* recs = reinterpret_cast<const OpRec<C>*>(o.recs);
+  const C* st = reinterpret_cast<const C*>(o.stream);
+  for (int64_t i = 0; i < o.nops; ++i) {
+    uint4 h;
+    C a, b;
+    load_rec(recs + i, h, a, b);
+    const uint32_t kind = h.x & 3u;
+    const int S = (int)((h.x >> kOpS) & 63u), D = (int)((h.x >> kOpD) & 63u);
+    const bool leaf = (h.x >> kOpLeaf) & 1u, first = (h.x >> kOpFirst) & 1u;
+    const int pid = (int)(h.x >> kOpPid);
+    const int len = (int)h.y + 1;
+    const int64_t off = (int64_t)h.w;
+    V v[PPT];
+    if (kind == kOpNode) {
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(a) : acc[(S * PPT + p) * kTPB + tid];
+    } else if (kind == kOpChain) {
+      const int64_t j0 = (int64_t)h.z;
+      const C* cs = st + off;  // node j0 + t uses cs[t]
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(__ldg(cs)) : acc[(S * PPT + p) * kTPB + tid];
+      if ((h.x >> kOpUniform) & 1u) {
+        const int pc = (int)(__ldg(g.ctrl + j0) >> kCtrlPid);
+        W xu[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) xu[p] = pw[(pc * PPT + p) * kTPB + tid];
+        for (int t = 1; t < len; ++t) {
+          const V cj = A::from_coef(__ldg(cs + t));
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xu[p], cj);
+        }
+      } else {
+        for (int t = 1; t < len; ++t) {
+          const int pc = (int)(__ldg(g.ctrl + j0 + t - 1) >> kCtrlPid);
+          const V cj = A::from_coef(__ldg(cs + t));
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
+        }
+      }
+    } else {
+      if constexpr (SCHEME != 0) {
+        C c[kMaxBlock];
+#pragma unroll
+        for (int q = 0; q < kMaxBlock / 4; ++q) {
+          C c4[4];
+          if (4 * q < len) load4(st, off, q, c4);
+          else c4[0] = c4[1] = c4[2] = c4[3] = C(0);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];
+        }
+        block_dispatch<A, SCHEME, PPT>(len, c, xp, v);
+      }
+    }
+    // the outgoing edge of the op's last node
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      V* dst = &acc[(D * PPT + p) * kTPB + tid];
+      const V init = first ? A::from_coef(b) : *dst;
+      *dst = A::mad(v[p], pw[(pid * PPT + p) * kTPB + tid], init);
+    }
+  }
+
+  const C rc = A::coef_from_bits(g.root_c);
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const int64_t idx = base + p * kTPB + tid;
+    V r = A::root(g.root_leaf, rc, &acc[(g.root_lh * PPT + p) * kTPB + tid]);
+    if (g.root_pid >= 0) r = A::apply_root_power(r, pw[(g.root_pid * PPT + p) * kTPB + tid]);
+    if (idx < g.npts) A::store(g.out, idx, g.npts, r);
+  }
+}
+
+// Launch helpers (defined per type in eval_<type>.cu).  variant: 0 = choose,
+// 1 = register kernel, 2 = shared-memory kernel.
+// variant 1 = grouped-op kernel (fused types only), 2 = node-by-node kernel.
+cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
+cudaError_t launch_eval_f32c(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
+cudaError_t launch_eval_iv64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
+cudaError_t launch_eval_modp(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
 
 // Shared memory of one block; the power table is used while it leaves room
 // for at least two resident blocks per SM.
@@ -392,8 +641,9 @@ size_t eval_smem(const EvalArgs& a, bool table) {
           sizeof(typename A::pw) * (size_t)(table ? a.npow : a.nvars)) * PPT * kTPB;
 }
 
+// Shared-memory kernel (any lazy height; power table or on-the-fly powers).
 template <class A, int PPT>
-cudaError_t launch_eval(const EvalArgs& a, cudaStream_t s) {
+cudaError_t launch_eval_smem(const EvalArgs& a, cudaStream_t s) {
   const bool table = eval_smem<A, PPT>(a, true) <= kTableSmemCap;
   const size_t smem = eval_smem<A, PPT>(a, table);
   if (smem > kSmemMax) return cudaErrorInvalidValue;
@@ -414,6 +664,41 @@ cudaError_t launch_eval(const EvalArgs& a, cudaStream_t s) {
   if (table) eval_kernel<A, PPT, true><<<(unsigned)blocks, kTPB, smem, s>>>(a);
   else eval_kernel<A, PPT, false><<<(unsigned)blocks, kTPB, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class A, int PPT, int SCHEME>
+cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
+  const size_t smem = (sizeof(typename A::val) * (size_t)a.nslot + sizeof(typename A::pw) * (size_t)a.npow) * PPT * kTPB;
+  if (smem > kSmemMax) return cudaErrorInvalidValue;
+  static int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, PPT, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  const int64_t per_block = (int64_t)kTPB * PPT;
+  const int64_t blocks = (a.npts + per_block - 1) / per_block;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  eval_ops_kernel<A, PPT, SCHEME><<<(unsigned)blocks, kTPB, smem, s>>>(a, o);
+  return cudaGetLastError();
+}
+
+// Kernel choice for the fused types: the grouped-op kernel whenever the power
+// table fits in shared memory, else the node-by-node kernel (on-the-fly powers).
+template <class A, int PPT_OPS, int PPT_NODE>
+cudaError_t launch_eval_fused(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant) {
+  const size_t table = (sizeof(typename A::val) * (size_t)a.nslot + sizeof(typename A::pw) * (size_t)a.npow) * PPT_OPS * kTPB;
+  const bool ops_ok = table <= kTableSmemCap && o.recs != nullptr;
+  if (variant == 1 && !ops_ok) return cudaErrorInvalidValue;
+  if (variant != 2 && ops_ok) {
+    if (scheme == FP_SCHEME_E) return launch_eval_ops<A, PPT_OPS, FP_SCHEME_E>(a, o, s);
+    if (scheme == FP_SCHEME_B) return launch_eval_ops<A, PPT_OPS, FP_SCHEME_B>(a, o, s);
+    return launch_eval_ops<A, PPT_OPS, 0>(a, o, s);
+  }
+  return launch_eval_smem<A, PPT_NODE>(a, s);
 }
 
 }  // namespace fp

@@ -1,6 +1,8 @@
-// Instantiation of the evaluation kernel for the MODP value type.
+// Instantiation of the evaluation kernels for the MODP value type.
 #include "eval_kernel.cuh"
 
 namespace fp {
-cudaError_t launch_eval_modp(const EvalArgs& a, cudaStream_t s) { return launch_eval<MODP, 2>(a, s); }
+cudaError_t launch_eval_modp(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant) {
+  return launch_eval_fused<MODP, 2, 2>(a, o, scheme, s, variant);
+}
 }  // namespace fp

@@ -26,6 +26,29 @@ constexpr uint32_t kMaxPowers = 1u << 15;
 //   bits 17..31  A2
 constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 
+// Ops for the fused value types (FP64, FP32C, MODP): the walk grouped into
+// ops, each ending with the outgoing multiply-add of its last node.  One op
+// record (32 bytes, read with two 128-bit loads) per op:
+//   x: bits 0..1 kind  (0: one node; 1: chain j0..j0+len-1, each node the only
+//                       child of the next; 2: dense subtree block of len nodes
+//                       evaluated by the scheme's own splits in registers)
+//      bits 2..7 S, 8..13 D, 14 LEAF (first node of the op is a leaf),
+//      15 FIRST (last node is its parent's first child), 16 UNIFORM (all
+//      powers inside a chain are the same), 17..31 PID of the outgoing edge
+//   y: len - 1      z: first node j0      w: offset of the op's coefficients
+//   a: leaf coefficient of a single-node op   b: parent coefficient if FIRST
+// The coefficients of chains and blocks are stored per op in a stream, each
+// op's run starting at a multiple of 4 elements (aligned vector loads).
+constexpr uint32_t kOpNode = 0, kOpChain = 1, kOpBlock = 2;
+constexpr uint32_t kOpS = 2, kOpD = 8, kOpLeaf = 14, kOpFirst = 15, kOpUniform = 16, kOpPid = 17;
+constexpr int kMaxChain = 64, kMaxBlock = 16, kStreamAlign = 4;
+
+template <class C>
+struct alignas(16) OpRec {
+  uint32_t x, y, z, w;
+  C a, b;
+};
+
 struct DeviceSchedule {
   int device = -1;
   uint32_t* ctrl = nullptr;   // [nsteps]
@@ -37,6 +60,12 @@ struct DeviceSchedule {
   float* cb_f32 = nullptr;
   uint64_t* ca_u64 = nullptr;
   uint64_t* cb_u64 = nullptr;
+  OpRec<double>* ops_f64 = nullptr;  // [nops]
+  OpRec<float>* ops_f32 = nullptr;
+  OpRec<uint64_t>* ops_u64 = nullptr;
+  double* st_f64 = nullptr;          // coefficient stream of chains and blocks
+  float* st_f32 = nullptr;
+  uint64_t* st_u64 = nullptr;
 };
 
 }  // namespace fp
@@ -63,6 +92,15 @@ struct fp_tree {
   int root_leaf = 1;
   int root_lh = 0;
   int root_pid = -1;
+
+  // grouped ops for the fused value types
+  std::vector<uint4> ops;          // x, y, z, w of each op record
+  std::vector<int64_t> op_a_node;  // node whose coefficient is the op's leaf value, or -1
+  std::vector<int64_t> op_b_node;  // parent whose coefficient initialises the slot, or -1
+  std::vector<int64_t> stream;     // node whose coefficient sits at each stream slot, or -1 (padding)
+  int block_scheme = 0;            // FP_SCHEME_E or FP_SCHEME_B when blocks are used, else 0
+  int pid_x1 = -1;                 // power slot of x_1
+  int pid_pow[fp::kMaxBlock + 1] = {};  // power slot of x_1^d, d <= kMaxBlock (-1: absent)
 
   fp::DeviceSchedule dev;
 };

@@ -20,9 +20,12 @@ def device_points(dtype, pts):
     return torch.from_numpy(a).cuda()
 
 
-def run(tree, dtype, pts, stream=None):
+def run(tree, dtype, pts, stream=None, kernel=None):
     d = device_points(dtype, pts)
-    out = fpl.fp_eval(tree, dtype, d, stream=stream).cpu().numpy()
+    if kernel is None:
+        out = fpl.fp_eval(tree, dtype, d, stream=stream).cpu().numpy()
+    else:
+        out = fpl.fp_eval_ex(tree, dtype, d, kernel=kernel, stream=stream).cpu().numpy()
     if dtype == "modp":
         out = out.view(np.uint64)
     return out

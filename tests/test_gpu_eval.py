@@ -224,6 +224,82 @@ def test_plain_baseline_kernel():
     check_f64(e, c, x, got)
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("k", [5, 17, 300, 1024])
+def test_grouped_and_node_kernels(scheme, k):
+    """Both kernels on every fused type: MODP identical bit for bit; FP64 and
+    FP32C identical where no block template reorders sums (H, D), and within
+    the bound everywhere."""
+    e, c, x = W.univariate_case(k, 2000 + 11, 50 + k)
+    t = fpl.fp_compile(e, c, scheme)
+    em, cm, xm = W.univariate_case(k, 2000 + 11, 52 + k, "modp")
+    tm = fpl.fp_compile(em, cm, scheme, modp=True)
+    for dt, tree, pts in (("f64", t, x), ("f32c", t, x), ("modp", tm, xm)):
+        try:
+            a = run(tree, dt, pts, kernel="ops")
+        except fpl.FastPolyError as err:
+            # the Direct scheme's power table (one power per node) does not fit
+            assert scheme == "D" and k > 17 and err.code == -6
+            continue
+        b = run(tree, dt, pts, kernel="node")
+        if dt == "modp" or scheme in ("H", "D"):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), dt
+        if dt == "f64":
+            check_f64(e, c, x, a)
+            check_f64(e, c, x, b)
+        elif dt == "f32c":
+            check_f32c(e, c, x, a)
+            check_f32c(e, c, x, b)
+        else:
+            check_modp(em, cm, xm, a)
+    lo, hi = W.boxes(1, 500, 53 + k)
+    with pytest.raises(fpl.FastPolyError):
+        run(t, "iv64", (lo, hi), kernel="ops")  # intervals keep the paper's node order
+
+
+def deep_ftab(kmax):
+    """A function scheme maximising the lazy height (dynamic programming over
+    the split f at every size): lh grows linearly, about (k - 1) / 2."""
+    neg = -10 ** 9
+    best = {1: (0, neg, None)}
+    for m in range(2, kmax + 1):
+        cand = None
+        for f in range(1, m):
+            la, ma, _ = best[m - f]
+            lb, mb, _ = best[f]
+            key = (max(la, 1 + mb) if mb > neg else la, max(la, mb))
+            if cand is None or key > cand[0]:
+                cand = (key, f)
+        best[m] = (cand[0][0], cand[0][1], cand[1])
+    ft = np.ones(kmax + 1, dtype=np.int32)
+    for m in range(2, kmax + 1):
+        ft[m - 1] = best[m][2]
+    return ft
+
+
+def test_deep_trees():
+    """Lazy heights 16..63 run on both kernels; above 63 fp_compile refuses
+    the tree."""
+    k = 61
+    ft = deep_ftab(k)
+    e, c, x = W.univariate_case(k, 1300, 61)
+    t = fpl.fp_compile(e, c, "CUSTOM", ft)
+    assert t.info()["max_lazy_height"] == O.build_tree(e, "CUSTOM", ft).lh.max() >= 16
+    check_f64(e, c, x, run(t, "f64", x, kernel="ops"))
+    check_f64(e, c, x, run(t, "f64", x, kernel="node"))
+    lo, hi = W.boxes(1, 500, 62)
+    check_iv64(e, c, lo, hi, "CUSTOM", run(t, "iv64", (lo, hi)), ftab=ft)
+    cm = W.residues(k, 63)
+    tm = fpl.fp_compile(e, cm, "CUSTOM", ft, modp=True)
+    xm = W.points_modp(1, 1300, 64)
+    check_modp(e, cm, xm, run(tm, "modp", xm))
+    check_f32c(e, c, x, run(t, "f32c", x))
+    kb = 200
+    fb = deep_ftab(kb)
+    with pytest.raises(fpl.FastPolyError):
+        fpl.fp_compile(W.dense_univariate_exps(kb), W.uniform_f64(kb, 1), "CUSTOM", fb)
+
+
 # ----------------------------------------------------------------- full sizes, sampled
 def _sample(npts, m, seed):
     return np.sort(W.rng(seed).choice(npts, size=m, replace=False))

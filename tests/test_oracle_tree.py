@@ -140,8 +140,38 @@ def test_tree_is_topological_and_degrees_add_up(k, scheme):
     assert np.all(t.parent[:-1] > np.arange(k - 1))      # children before parents
     assert np.all(t.pd[:-1] > 0)
     assert _depth_sum_ok(t)
-    # Sec. 1.3: the maximal lazy height is at most logarithmic
-    assert t.lh.max() <= max(0, math.ceil(math.log2(k)))
+    # Sec. 1.3: the maximal lazy height is at most logarithmic -- for the
+    # classical schemes; an adversarial f reaches about k/2 (next test)
+    if scheme != "CUSTOM":
+        assert t.lh.max() <= max(0, math.ceil(math.log2(k)))
+
+
+def test_lazy_height_is_not_logarithmic_for_every_scheme():
+    """Reading of Sec. 1.3: with a node whose first child is a leaf and whose
+    second child has lazy height h, lh = h + 1 costs two nodes, so some f give
+    lh = (k - 1) // 2; the logarithmic claim holds for D, H, E, B only."""
+    k = 41
+    # the best f at every size, by dynamic programming on (lh, max child lh)
+    neg = -10 ** 9
+    dp = {1: (0, neg)}
+    choice = {}
+    for m in range(2, k + 1):
+        cands = []
+        for f in range(1, m):
+            la, ma = dp[m - f]
+            lb, mb = dp[f]
+            cands.append(((max(la, 1 + mb) if mb > neg else la, max(la, mb)), f))
+        dp[m], choice[m] = max(cands)
+    fdp = np.ones(k + 1, dtype=np.int32)
+    for m in range(2, k + 1):
+        fdp[m - 1] = choice[m]
+    t = O.build_tree(W.dense_univariate_exps(k), "CUSTOM", fdp)
+    assert int(t.lh.max()) == dp[k][0] == (k - 1) // 2
+    assert t.lh.max() > math.ceil(math.log2(k))
+    x = W.residues(5, 1).reshape(1, 5)
+    c = W.residues(k, 2)
+    assert np.array_equal(O.walk_modp(t, t.node_coeffs(c, np.uint64), x),
+                          O.eval_modp(W.dense_univariate_exps(k), c, x))
 
 
 def test_balanced_equals_estrin_at_powers_of_two():
