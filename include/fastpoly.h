@@ -168,6 +168,33 @@ int fp_tree_info(const fp_tree* t, int64_t* nnodes, int* nvars, int* max_lazy_he
 int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, int64_t* parent,
                    int32_t* pd_var, int64_t* pd, int32_t* lazy_height);
 
+/*
+ * fp_compose -- batched composition r_j(y) = p_j(q_j(y)) for j < npairs: the
+ * coefficient walk (Sec. 2.1) of p's tree run over polynomial values, the
+ * "composition" of the paper's title, where values grow with each product
+ * (Sec. 1.2).  Every pair shares the tree of p (its terms and scheme); the
+ * coefficients may differ per pair.  Univariate trees only.
+ *
+ *   p        tree from fp_compile (nvars = 1).  FP_MODP needs a FP_MODP tree,
+ *            FP_F64 a FP_F64 tree.
+ *   dtype    FP_MODP (exact; products by number-theoretic transforms) or
+ *            FP_F64 (products by direct convolution: componentwise error
+ *            bounded by the same walk run on |p|, |q|).
+ *   pcoeffs  device, [npairs][nterms] in the term order given to fp_compile,
+ *            or NULL to use the tree's own coefficients for every pair.  Terms
+ *            whose compile-time coefficient was zero are not in the tree and
+ *            are ignored (compile with non-zero placeholders).
+ *   q        device, [npairs][degq + 1], coefficient of y^i at index i.
+ *   out      device, [npairs][deg(p) * degq + 1].
+ * Work space (about (lazy height + 6) x npairs x deg(p) x degq x 8 bytes) is
+ * allocated on `stream` with cudaMallocAsync and released before returning;
+ * the call synchronises `stream` while it uploads its tables.
+ * Errors: FP_E_BAD_VALUE, FP_E_DTYPE, FP_E_TOO_LARGE (output longer than
+ * 2^26), FP_E_NOMEM, FP_E_CUDA.
+ */
+int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
+               int64_t npairs, void* out, void* stream);
+
 /* fp_eval_plain_f64 -- the comparison baseline: one launch per polynomial,
  * one thread per point, Horner's rule over the dense coefficient vector
  * coeffs[0..ncoeffs-1] (index = degree), FP64, no tree.  Device pointers. */

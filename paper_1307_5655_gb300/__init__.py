@@ -32,6 +32,7 @@ for _name, _args in {
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
+    "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
 }.items():
     getattr(_lib, _name).restype = _I
     getattr(_lib, _name).argtypes = _args
@@ -205,4 +206,23 @@ def fp_eval_plain_f64(coeffs_by_degree, points, out=None, stream=None):
         out = torch.empty(npts, dtype=torch.float64, device=points.device)
     _check(_lib.fp_eval_plain_f64(_ptr(coeffs_by_degree), coeffs_by_degree.numel(), _ptr(points), npts, _ptr(out),
                                   _stream_handle(stream)), "fp_eval_plain_f64")
+    return out
+
+
+def fp_compose(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
+    """Batched composition p_j(q_j(y)): q is a CUDA tensor [npairs, degq + 1]
+    (float64, or int64 holding residues for 'modp'); pcoeffs an optional CUDA
+    tensor [npairs, nterms] of per-pair coefficients in the compiled term
+    order.  Returns out [npairs, deg(p) * degq + 1]."""
+    import torch
+    if not q.is_cuda or not q.is_contiguous():
+        raise ValueError("q must be a contiguous CUDA tensor")
+    npairs, nq = q.shape
+    if degp is None:
+        degp = int(tree.export()["node_e"][0, 0]) if tree.info()["nnodes"] else 0
+    if out is None:
+        out = torch.empty((npairs, degp * (nq - 1) + 1), dtype=_torch_dtype(dtype), device=q.device)
+    pc = None if pcoeffs is None else _ptr(pcoeffs)
+    _check(_lib.fp_compose(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
+                           _stream_handle(stream)), "fp_compose")
     return out

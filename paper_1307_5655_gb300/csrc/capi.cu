@@ -229,6 +229,9 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
   return e == cudaSuccess ? FP_OK : FP_E_CUDA;
 }
 
+int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
+                   void* out, cudaStream_t st);
+
 }  // namespace fp
 
 using namespace fp;
@@ -339,6 +342,13 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
   if (pd) std::memcpy(pd, t->pd.data(), N * sizeof(int64_t));
   if (lazy_height) std::memcpy(lazy_height, t->lh.data(), N * sizeof(int32_t));
   return FP_OK;
+}
+
+int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
+               void* out, void* stream) {
+  int dev = -1;
+  if (p && (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev.device)) { cudaGetLastError(); return FP_E_BAD_VALUE; }
+  return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream);
 }
 
 int fp_eval_plain_f64(const double* coeffs, int64_t ncoeffs, const double* points, int64_t npts, double* out,

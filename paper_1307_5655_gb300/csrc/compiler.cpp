@@ -156,6 +156,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
 
   t->nvars = nvars;
   t->coeff_type = coeff_type;
+  t->nterms_in = nterms;
   t->node_e.clear();
   t->term_of_node.clear();
   if (order.empty()) {  // the zero polynomial

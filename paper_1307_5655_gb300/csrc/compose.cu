@@ -1,0 +1,558 @@
+// Batched composition r_j = p_j(q_j(y)) for many pairs (p_j, q_j): the
+// coefficient walk of Moroz, Sec. 2.1, run over polynomial values -- the
+// paper's "polynomial composition", where elements grow with every product
+// (Sec. 1.2, Sec. 3).  All pairs share the tree of p (same terms and scheme),
+// so every node step is one batched operation over the pairs:
+//     acc[lh(P)] = (c_P if N is P's first child else acc[lh(P)]) + s * q^d(N)
+//     s = c_N (leaf) or acc[lh(N)]
+// Products are sized to the degrees they involve (the staircase of the
+// Estrin scheme at 2^m + 1 terms comes from exactly this), computed
+//   MODP: by number-theoretic transforms over p = 2^64 - 2^32 + 1 (roots of
+//         unity of order 2^32 exist): in shared memory for lengths <= 4096,
+//         by a four-step transform (two passes) above;
+//   FP64: by direct convolution (componentwise error bound).
+// Powers q^d follow the tree's power program (squarings and products by q).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "eval_kernel.cuh"
+#include "tree.hpp"
+
+namespace fp {
+namespace {
+
+constexpr uint64_t kP = 0xFFFFFFFF00000001ull;
+constexpr int kNttSmemMax = 4096;  // longest transform done in one block
+
+// ------------------------------------------------------------ mod p (host)
+uint64_t h_mul(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) % kP); }
+uint64_t h_pow(uint64_t a, uint64_t e) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1) r = h_mul(r, a);
+    a = h_mul(a, a);
+    e >>= 1;
+  }
+  return r;
+}
+
+// ------------------------------------------------------------ mod p (device)
+__device__ __forceinline__ uint64_t d_add(uint64_t a, uint64_t b) {
+  const uint64_t s = a + b;
+  // a, b < p: a + b < 2p < 2^65; reduce once (overflow means s + 2^64 >= p)
+  if (s < a) return s + 0xFFFFFFFFull;  // 2^64 = 2^32 - 1 (mod p); s + 2^32 - 1 < p here
+  return s >= kP ? s - kP : s;
+}
+__device__ __forceinline__ uint64_t d_sub(uint64_t a, uint64_t b) { return a >= b ? a - b : a + (kP - b); }
+__device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP::mul_add(a, b, 0); }
+
+// Radix-2 transforms of one vector of length n held in shared memory by the
+// block.  Forward: decimation in frequency, natural order in, bit-reversed
+// order out.  Inverse: decimation in time, bit-reversed in, natural out
+// (unscaled).  tw[j] = w^j for the length-n root w (inverse: w^-j), j < n/2,
+// read with stride `ts` from a table of a longer length.
+__device__ void ntt_dif(uint64_t* a, int n, const uint64_t* tw, int ts) {
+  for (int half = n >> 1; half >= 1; half >>= 1) {
+    __syncthreads();
+    const int step = (n / (2 * half)) * ts;
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int grp = b / half, pos = b - grp * half;
+      const int i = grp * 2 * half + pos, j = i + half;
+      const uint64_t u = a[i], v = a[j];
+      a[i] = d_add(u, v);
+      a[j] = d_mul(d_sub(u, v), __ldg(tw + pos * step));
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void ntt_dit(uint64_t* a, int n, const uint64_t* tw, int ts) {
+  for (int half = 1; half < n; half <<= 1) {
+    __syncthreads();
+    const int step = (n / (2 * half)) * ts;
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int grp = b / half, pos = b - grp * half;
+      const int i = grp * 2 * half + pos, j = i + half;
+      const uint64_t u = a[i], v = d_mul(a[j], __ldg(tw + pos * step));
+      a[i] = d_add(u, v);
+      a[j] = d_sub(u, v);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int bitrev(int x, int logn) { return (int)(__brev((unsigned)x) >> (32 - logn)); }
+
+// ------------------------------------------------------------ MODP kernels
+// Forward transform of length n <= 4096 of src[pair][0..len) zero-padded,
+// into dst[pair][0..n).  One block per pair.
+__global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch,
+                                int n, const uint64_t* tw, int ts) {
+  extern __shared__ uint64_t sh[];
+  const int64_t pr = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = i < len ? src[pr * src_pitch + i] : 0;
+  ntt_dif(sh, n, tw, ts);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[pr * dst_pitch + i] = sh[i];
+}
+
+// Inverse of a product: t = F(A) (in `prod`), multiplied by `fb` (the
+// transform of B), inverse transform, scaled by 1/n, then the first `outlen`
+// coefficients written (mode 0), or added into acc (mode 1), or written with
+// the constant `init[pair]` added at degree 0 (mode 2).
+__global__ void k_ntt_mul_inv_small(const uint64_t* prod, const uint64_t* fb, int64_t pitch, int n,
+                                    const uint64_t* twi, int ts, uint64_t ninv, uint64_t* out, int64_t out_pitch,
+                                    int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
+  extern __shared__ uint64_t sh[];
+  const int64_t pr = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = d_mul(prod[pr * pitch + i], fb[pr * pitch + i]);
+  ntt_dit(sh, n, twi, ts);
+  for (int i = threadIdx.x; i < outlen; i += blockDim.x) {
+    uint64_t v = d_mul(sh[i], ninv);
+    uint64_t* o = out + pr * out_pitch + i;
+    if (mode == 1) v = d_add(*o, v);
+    else if (mode == 2 && i == 0) v = d_add(v, init[pr * init_pitch]);
+    *o = v;
+  }
+}
+
+// Four-step transform of length n = R * C (R, C <= 4096), vector x[C n1 + n2].
+// Column pass: for a tile of TC columns, each column (length R, stride C) is
+// transformed; forward multiplies by w_n^(k1 n2) afterwards, inverse divides
+// before.  Row pass: each row (length C, contiguous) is transformed.
+constexpr int kTileCols = 8;
+
+__global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch, int R,
+                           int C, int logR, const uint64_t* twR, int tsR, const uint64_t* twn, int inverse,
+                           uint64_t scale, int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
+  extern __shared__ uint64_t sh[];  // [kTileCols][R]
+  const int tiles = C / kTileCols;
+  const int64_t pr = blockIdx.x / tiles;
+  const int c0 = (blockIdx.x % tiles) * kTileCols;
+  const int n = R * C;
+  for (int e = threadIdx.x; e < R * kTileCols; e += blockDim.x) {
+    const int r = e / kTileCols, c = e % kTileCols;
+    const int idx = r * C + c0 + c;
+    uint64_t v = idx < len ? src[pr * src_pitch + idx] : 0;
+    if (inverse) {
+      // position r holds k1 = bitrev(r); undo the twiddle w^(k1 n2)
+      const int k1 = bitrev(r, logR);
+      const int64_t ex = ((int64_t)k1 * (c0 + c)) % n;
+      v = d_mul(v, __ldg(twn + ((n - ex) % n)));
+    }
+    sh[c * R + r] = v;
+  }
+  for (int c = 0; c < kTileCols; ++c) {
+    if (inverse) ntt_dit(sh + c * R, R, twR, tsR);
+    else ntt_dif(sh + c * R, R, twR, tsR);
+  }
+  for (int e = threadIdx.x; e < R * kTileCols; e += blockDim.x) {
+    const int r = e / kTileCols, c = e % kTileCols;
+    const int idx = r * C + c0 + c;
+    uint64_t v = sh[c * R + r];
+    if (!inverse) {
+      const int k1 = bitrev(r, logR);
+      const int64_t ex = ((int64_t)k1 * (c0 + c)) % n;
+      v = d_mul(v, __ldg(twn + ex));
+      dst[pr * dst_pitch + idx] = v;
+    } else if (idx < outlen) {
+      v = d_mul(v, scale);
+      uint64_t* o = dst + pr * dst_pitch + idx;
+      if (mode == 1) v = d_add(*o, v);
+      else if (mode == 2 && idx == 0) v = d_add(v, init[pr * init_pitch]);
+      *o = v;
+    }
+  }
+}
+
+__global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, const uint64_t* twC, int tsC, int inverse,
+                           const uint64_t* fb) {
+  extern __shared__ uint64_t sh[];
+  const int64_t pr = blockIdx.x / R;
+  const int r = blockIdx.x % R;
+  uint64_t* row = data + pr * pitch + (int64_t)r * C;
+  const uint64_t* frow = fb ? fb + pr * pitch + (int64_t)r * C : nullptr;
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sh[i] = frow ? d_mul(row[i], frow[i]) : row[i];
+  if (inverse) ntt_dit(sh, C, twC, tsC);
+  else ntt_dif(sh, C, twC, tsC);
+  for (int i = threadIdx.x; i < C; i += blockDim.x) row[i] = sh[i];
+}
+
+// leaf step: dst[0..len) = (init at degree 0 if first) + c[pair] * q^d
+template <class T>
+__global__ void k_leaf(T* dst, int64_t dst_pitch, const T* qd, int64_t q_pitch, int len, const T* c, int64_t c_pitch,
+                       int first, const T* init, int64_t init_pitch, int64_t npairs) {
+  const int64_t total = npairs * (int64_t)len;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / len;
+    const int i = (int)(e - pr * len);
+    const T cv = c[pr * c_pitch];
+    const T qv = qd[pr * q_pitch + i];
+    T* o = dst + pr * dst_pitch + i;
+    const T base = first ? ((i == 0 && init) ? init[pr * init_pitch] : T(0)) : *o;
+    if constexpr (std::is_same<T, uint64_t>::value) *o = MODP::mul_add(cv, qv, base);
+    else *o = fma(cv, qv, base);
+  }
+}
+
+// FP64 product by direct convolution, out[j] = sum_i a[i] b[j-i] for
+// j < outlen, written, accumulated or initialised as k_ntt_mul_inv_small.
+__global__ void k_conv_f64(const double* a, int64_t a_pitch, int alen, const double* b, int64_t b_pitch, int blen,
+                           double* out, int64_t out_pitch, int outlen, int mode, const double* init,
+                           int64_t init_pitch, int tiles) {
+  const int64_t pr = blockIdx.x / tiles;
+  const int j = (blockIdx.x % tiles) * blockDim.x + threadIdx.x;
+  if (j >= outlen) return;
+  const double* ap = a + pr * a_pitch;
+  const double* bp = b + pr * b_pitch;
+  const int lo = j - blen + 1 > 0 ? j - blen + 1 : 0;
+  const int hi = j < alen - 1 ? j : alen - 1;
+  double s = 0.0;
+  for (int i = lo; i <= hi; ++i) s = fma(ap[i], bp[j - i], s);
+  double* o = out + pr * out_pitch + j;
+  if (mode == 1) s += *o;
+  else if (mode == 2 && j == 0) s += init[pr * init_pitch];
+  *o = s;
+}
+
+// per-pair node coefficients: cn[pair][node] = coefficient of that node's term
+template <class T>
+__global__ void k_gather_coeffs(const T* pc, int64_t row_pitch, const int64_t* term_of_node, int64_t nnodes,
+                                T* cn, int64_t npairs, int reduce_modp) {
+  const int64_t total = npairs * nnodes;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / nnodes, i = e - pr * nnodes;
+    const int64_t t = term_of_node[i];
+    T v = t >= 0 ? pc[pr * row_pitch + t] : T(0);
+    if constexpr (std::is_same<T, uint64_t>::value) {
+      if (reduce_modp && v >= kP) v -= kP;
+    }
+    cn[e] = v;
+  }
+}
+
+template <class T>
+__global__ void k_copy_rows(const T* src, int64_t src_pitch, T* dst, int64_t dst_pitch, int len, int64_t npairs,
+                            int reduce_modp) {
+  const int64_t total = npairs * (int64_t)len;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / len;
+    const int i = (int)(e - pr * len);
+    T v = src[pr * src_pitch + i];
+    if constexpr (std::is_same<T, uint64_t>::value) {
+      if (reduce_modp && v >= kP) v -= kP;
+    }
+    dst[pr * dst_pitch + i] = v;
+  }
+}
+
+template <class T>
+__global__ void k_fill_zero(T* dst, int64_t pitch, int from, int len, int64_t npairs) {
+  const int64_t w = len - from;
+  const int64_t total = npairs * w;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / w;
+    dst[pr * pitch + from + (e - pr * w)] = T(0);
+  }
+}
+
+int grid_for(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 65536 ? 65536 : b));
+}
+
+int ilog2(int64_t n) {
+  int l = 0;
+  while ((int64_t)1 << l < n) ++l;
+  return l;
+}
+
+// ------------------------------------------------------------ host plan
+struct Buf {
+  void* ptr = nullptr;
+  int64_t pitch = 0;  // elements per pair
+};
+
+struct Composer {
+  const fp_tree* t;
+  int dtype;  // FP_MODP or FP_F64
+  int degq;
+  int64_t npairs;
+  cudaStream_t st;
+  int status = FP_OK;
+  std::vector<void*> owned;
+  // twiddles (MODP): forward/inverse powers of w_n for every length n used
+  std::map<int, std::pair<uint64_t*, uint64_t*>> tw;
+
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    if (status != FP_OK) return nullptr;
+    if (cudaMallocAsync(&p, bytes < 16 ? 16 : bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      status = FP_E_NOMEM;
+      return nullptr;
+    }
+    owned.push_back(p);
+    return p;
+  }
+  void release() {
+    for (void* p : owned) cudaFreeAsync(p, st);
+    owned.clear();
+  }
+  void check() {
+    if (status == FP_OK && cudaGetLastError() != cudaSuccess) status = FP_E_CUDA;
+  }
+
+  std::pair<uint64_t*, uint64_t*> twiddles(int n) {
+    auto it = tw.find(n);
+    if (it != tw.end()) return it->second;
+    std::vector<uint64_t> f(n), b(n);
+    const uint64_t w = h_pow(7, (kP - 1) / (uint64_t)n);  // 7 generates (Z/pZ)^*
+    const uint64_t wi = h_pow(w, kP - 2);
+    uint64_t x = 1, y = 1;
+    for (int j = 0; j < n; ++j) {
+      f[j] = x;
+      b[j] = y;
+      x = h_mul(x, w);
+      y = h_mul(y, wi);
+    }
+    uint64_t* df = (uint64_t*)alloc(n * 8);
+    uint64_t* db = (uint64_t*)alloc(n * 8);
+    if (status == FP_OK) {
+      cudaMemcpyAsync(df, f.data(), n * 8, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(db, b.data(), n * 8, cudaMemcpyHostToDevice, st);
+      // the host vectors must outlive the copies: wait for them
+      cudaStreamSynchronize(st);
+    }
+    tw[n] = {df, db};
+    return tw[n];
+  }
+
+  // forward transform of length n of src (first len coefficients) into dst
+  void fwd(const Buf& src, int len, const Buf& dst, int n) {
+    if (status != FP_OK) return;
+    if (n <= kNttSmemMax) {
+      auto w = twiddles(n);
+      k_ntt_fwd_small<<<(unsigned)npairs, 256, n * 8, st>>>((const uint64_t*)src.ptr, src.pitch, len,
+                                                            (uint64_t*)dst.ptr, dst.pitch, n, w.first, 1);
+    } else {
+      const int C = kNttSmemMax / 2 >= n / 2 ? n / 2 : 2048;  // row length
+      const int R = n / C;
+      auto wR = twiddles(R);
+      auto wC = twiddles(C);
+      auto wn = twiddles(n);
+      k_ntt_cols<<<(unsigned)(npairs * (C / kTileCols)), 256, (size_t)R * kTileCols * 8, st>>>(
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, ilog2(R), wR.first, 1,
+          wn.first, 0, 1, 0, 0, nullptr, 0);
+      k_ntt_rows<<<(unsigned)(npairs * R), 256, (size_t)C * 8, st>>>((uint64_t*)dst.ptr, dst.pitch, R, C, wC.first,
+                                                                     1, 0, nullptr);
+    }
+    check();
+  }
+
+  // out = first outlen coefficients of inverse(F(A) * F(B)), per mode
+  void mul_inv(const Buf& fa, const Buf& fbuf, int n, const Buf& out, int outlen, int mode, const uint64_t* init,
+               int64_t init_pitch) {
+    if (status != FP_OK) return;
+    const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
+    if (n <= kNttSmemMax) {
+      auto w = twiddles(n);
+      k_ntt_mul_inv_small<<<(unsigned)npairs, 256, n * 8, st>>>((const uint64_t*)fa.ptr, (const uint64_t*)fbuf.ptr,
+                                                                fa.pitch, n, w.second, 1, ninv, (uint64_t*)out.ptr,
+                                                                out.pitch, outlen, mode, init, init_pitch);
+    } else {
+      const int C = 2048;
+      const int R = n / C;
+      auto wR = twiddles(R);
+      auto wC = twiddles(C);
+      auto wn = twiddles(n);
+      k_ntt_rows<<<(unsigned)(npairs * R), 256, (size_t)C * 8, st>>>((uint64_t*)fa.ptr, fa.pitch, R, C, wC.second,
+                                                                     1, 1, (const uint64_t*)fbuf.ptr);
+      k_ntt_cols<<<(unsigned)(npairs * (C / kTileCols)), 256, (size_t)R * kTileCols * 8, st>>>(
+          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, ilog2(R), wR.second, 1,
+          wn.first, 1, ninv, outlen, mode, init, init_pitch);
+    }
+    check();
+  }
+};
+
+int64_t next_pow2(int64_t x) {
+  int64_t n = 1;
+  while (n < x) n <<= 1;
+  return n;
+}
+
+}  // namespace
+
+// Composition entry (declared in capi.cu).
+int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
+                   void* out, cudaStream_t st) {
+  if (!t || !q || !out || degq < 0 || npairs < 0) return FP_E_BAD_VALUE;
+  if (t->nvars != 1) return FP_E_BAD_VALUE;
+  if (dtype == FP_MODP ? t->coeff_type != FP_MODP : (dtype != FP_F64 || t->coeff_type != FP_F64)) return FP_E_DTYPE;
+  if (t->dev.device < 0) return FP_E_DTYPE;
+  if (npairs == 0) return FP_OK;
+  const bool modp = dtype == FP_MODP;
+  const int64_t N = t->nnodes;
+  const int64_t dmax = N > 0 ? t->node_e[0] : 0;  // degree of p (node 0 is the highest term)
+  const int64_t outlen = dmax * (int64_t)degq + 1;
+  const size_t esz = 8;
+  if (outlen > (1 << 26)) return FP_E_TOO_LARGE;
+  Composer cm{t, dtype, degq, npairs, st};
+  Buf outb{out, outlen};
+  if (N == 0) {  // zero polynomial
+    k_fill_zero<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, 0, (int)outlen, npairs);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
+  }
+  // ---- node coefficients per pair: cn[pair][node]
+  Buf cn{cm.alloc(npairs * N * esz), N};
+  {
+    int64_t* d_map = (int64_t*)cm.alloc(N * 8);
+    void* d_pc = nullptr;
+    std::vector<uint64_t> own;
+    if (!pcoeffs) {  // the tree's own coefficients, one row shared by every pair
+      own.assign(t->nterms_in, 0);
+      for (int64_t i = 0; i < N; ++i)
+        if (t->term_of_node[i] >= 0) {
+          if (modp) own[t->term_of_node[i]] = t->c_u64[i];
+          else std::memcpy(&own[t->term_of_node[i]], &t->c_f64[i], 8);
+        }
+      d_pc = cm.alloc(own.size() * 8);
+    }
+    if (cm.status != FP_OK) { cm.release(); return cm.status; }
+    cudaMemcpyAsync(d_map, t->term_of_node.data(), N * 8, cudaMemcpyHostToDevice, st);
+    if (!pcoeffs) cudaMemcpyAsync(d_pc, own.data(), own.size() * 8, cudaMemcpyHostToDevice, st);
+    // term_of_node indexes the caller's input order (rows of nterms_in)
+    const int64_t row = pcoeffs ? t->nterms_in : 0;
+    if (modp)
+      k_gather_coeffs<uint64_t><<<grid_for(npairs * N), 256, 0, st>>>(
+          (const uint64_t*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (uint64_t*)cn.ptr, npairs, 1);
+    else
+      k_gather_coeffs<double><<<grid_for(npairs * N), 256, 0, st>>>(
+          (const double*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (double*)cn.ptr, npairs, 0);
+    cm.check();
+    cudaStreamSynchronize(st);  // the host vectors above must outlive their copies
+  }
+  // ---- degrees of node values: deg(N) = degq * (max exponent in subtree - e(N))
+  std::vector<int64_t> maxe(N);
+  for (int64_t i = 0; i < N; ++i) maxe[i] = t->node_e[i];
+  for (int64_t i = 0; i + 1 < N; ++i) maxe[t->parent[i]] = std::max(maxe[t->parent[i]], maxe[i]);
+  auto degval = [&](int64_t i) { return (maxe[i] - t->node_e[i]) * (int64_t)degq; };
+  std::vector<int64_t> cap(t->max_lh + 1, 1);
+  for (int64_t i = 0; i < N; ++i) cap[t->lh[i]] = std::max(cap[t->lh[i]], degval(i) + 1);
+  std::vector<Buf> acc(cap.size());
+  for (size_t s = 0; s < cap.size(); ++s) acc[s] = Buf{cm.alloc(npairs * cap[s] * esz), cap[s]};
+  // ---- powers q^d (coefficient form) by the tree's power program
+  const int npow = (int)t->pow_prog.size();
+  std::vector<Buf> qp(npow);
+  int64_t maxprod = 1;
+  for (int k = 0; k < npow; ++k) qp[k] = Buf{cm.alloc(npairs * (t->pow_deg[k] * degq + 1) * esz), t->pow_deg[k] * degq + 1};
+  for (int64_t i = 0; i + 1 < N; ++i) maxprod = std::max(maxprod, degval(i) + t->pd[i] * degq + 1);
+  for (int k = 0; k < npow; ++k) maxprod = std::max(maxprod, t->pow_deg[k] * degq + 1);
+  const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
+  Buf ta{cm.alloc(npairs * Lmax * esz), Lmax}, tb{cm.alloc(npairs * Lmax * esz), Lmax};
+  if (cm.status != FP_OK) { cm.release(); return cm.status; }
+  // product helper: dst (per mode) = A[0..alen) * B[0..blen)
+  auto product = [&](const Buf& A, int64_t alen, const Buf& B, int64_t blen, const Buf& dst, int mode,
+                     const void* init, int64_t init_pitch) {
+    const int64_t rl = alen + blen - 1;
+    if (modp) {
+      const int n = (int)next_pow2(rl);
+      cm.fwd(A, (int)alen, ta, n);
+      cm.fwd(B, (int)blen, tb, n);
+      cm.mul_inv(ta, tb, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
+    } else {
+      // the source may be the destination slot: convolve from a copy
+      k_copy_rows<double><<<grid_for(npairs * alen), 256, 0, st>>>((const double*)A.ptr, A.pitch, (double*)ta.ptr,
+                                                                    ta.pitch, (int)alen, npairs, 0);
+      const int tiles = (int)((rl + 255) / 256);
+      k_conv_f64<<<(unsigned)(npairs * tiles), 256, 0, st>>>((const double*)ta.ptr, ta.pitch, (int)alen,
+                                                            (const double*)B.ptr, B.pitch, (int)blen,
+                                                            (double*)dst.ptr, dst.pitch, (int)rl, mode,
+                                                            (const double*)init, init_pitch, tiles);
+      cm.check();
+    }
+  };
+  for (int k = 0; k < npow && cm.status == FP_OK; ++k) {
+    const uint32_t w = t->pow_prog[k];
+    const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+    if (op == kPowLoad) {
+      if (modp) k_copy_rows<uint64_t><<<grid_for(npairs * (degq + 1)), 256, 0, st>>>(
+          (const uint64_t*)q, degq + 1, (uint64_t*)qp[k].ptr, qp[k].pitch, degq + 1, npairs, 1);
+      else k_copy_rows<double><<<grid_for(npairs * (degq + 1)), 256, 0, st>>>(
+          (const double*)q, degq + 1, (double*)qp[k].ptr, qp[k].pitch, degq + 1, npairs, 0);
+      cm.check();
+    } else if (op == kPowSq) {
+      product(qp[a1], qp[a1].pitch, qp[a1], qp[a1].pitch, qp[k], 0, nullptr, 0);
+    } else {
+      product(qp[a1], qp[a1].pitch, qp[a2], qp[a2].pitch, qp[k], 0, nullptr, 0);
+    }
+  }
+  // ---- the walk
+  std::vector<uint8_t> has_child(N, 0), seen(N, 0);
+  for (int64_t i = 0; i + 1 < N; ++i) has_child[t->parent[i]] = 1;
+  std::map<std::pair<int32_t, int64_t>, int> pid;
+  for (int k = 0; k < npow; ++k) pid[{t->pow_var[k], t->pow_deg[k]}] = k;
+  for (int64_t i = 0; i + 1 < N && cm.status == FP_OK; ++i) {
+    const int64_t P = t->parent[i];
+    const bool first = !seen[P];
+    seen[P] = 1;
+    const Buf& dst = acc[t->lh[P]];
+    const Buf& qd = qp[pid.at({0, t->pd[i]})];
+    const int mode = first ? 2 : 1;
+    const void* init = (const char*)cn.ptr + P * esz;
+    if (!has_child[i]) {  // leaf: c_i * q^d
+      const int len = (int)qd.pitch;
+      if (modp)
+        k_leaf<uint64_t><<<grid_for(npairs * len), 256, 0, st>>>(
+            (uint64_t*)dst.ptr, dst.pitch, (const uint64_t*)qd.ptr, qd.pitch, len,
+            (const uint64_t*)cn.ptr + i, N, first, (const uint64_t*)init, N, npairs);
+      else
+        k_leaf<double><<<grid_for(npairs * len), 256, 0, st>>>(
+            (double*)dst.ptr, dst.pitch, (const double*)qd.ptr, qd.pitch, len, (const double*)cn.ptr + i, N, first,
+            (const double*)init, N, npairs);
+      cm.check();
+    } else {
+      product(acc[t->lh[i]], degval(i) + 1, qd, qd.pitch, dst, mode, init, N);
+    }
+  }
+  // ---- root: r = acc (or c) times q^d(root)
+  if (cm.status == FP_OK) {
+    const int64_t R = N - 1;
+    const int64_t d0 = t->pd[R];
+    if (!has_child[R]) {  // a single term c x^d: c * q^d
+      if (d0 == 0) {
+        k_fill_zero<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, 0, (int)outlen, npairs);
+        if (modp) k_copy_rows<uint64_t><<<grid_for(npairs), 256, 0, st>>>((const uint64_t*)cn.ptr + R, N, (uint64_t*)out, outlen, 1, npairs, 0);
+        else k_copy_rows<double><<<grid_for(npairs), 256, 0, st>>>((const double*)cn.ptr + R, N, (double*)out, outlen, 1, npairs, 0);
+      } else {
+        const Buf& qd = qp[pid.at({0, d0})];
+        if (modp)
+          k_leaf<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, (const uint64_t*)qd.ptr,
+                                                                      qd.pitch, (int)outlen, (const uint64_t*)cn.ptr + R,
+                                                                      N, 1, nullptr, 0, npairs);
+        else
+          k_leaf<double><<<grid_for(npairs * outlen), 256, 0, st>>>((double*)out, outlen, (const double*)qd.ptr,
+                                                                    qd.pitch, (int)outlen, (const double*)cn.ptr + R, N,
+                                                                    1, nullptr, 0, npairs);
+      }
+      cm.check();
+    } else if (d0 == 0) {
+      const Buf& src = acc[t->lh[R]];
+      if (modp) k_copy_rows<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((const uint64_t*)src.ptr, src.pitch, (uint64_t*)out, outlen, (int)outlen, npairs, 0);
+      else k_copy_rows<double><<<grid_for(npairs * outlen), 256, 0, st>>>((const double*)src.ptr, src.pitch, (double*)out, outlen, (int)outlen, npairs, 0);
+      cm.check();
+    } else {
+      const Buf& qd = qp[pid.at({0, d0})];
+      product(acc[t->lh[R]], degval(R) + 1, qd, qd.pitch, outb, 0, nullptr, 0);
+    }
+  }
+  const int rc = cm.status;
+  cm.release();
+  return rc;
+}
+
+}  // namespace fp

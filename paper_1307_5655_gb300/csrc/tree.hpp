@@ -74,6 +74,7 @@ struct fp_tree {
   int nvars = 1;
   int coeff_type = FP_F64;  // FP_F64 or FP_MODP
   int64_t nnodes = 0;       // 0: the zero polynomial
+  int64_t nterms_in = 0;    // terms given to fp_compile (term_of_node indexes them)
   std::vector<int32_t> node_e;       // [nnodes][nvars]
   std::vector<int64_t> term_of_node;  // -1: virtual group root
   std::vector<int64_t> parent;       // -1: root
