@@ -356,8 +356,86 @@ def run_profile_case(args):
     print("profile case done: k=%d scheme=%s dtype=%s kernel=%s points=%d" % (k, scheme, dt, args.profile_kernel, NPTS))
 
 
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_compose(args):
+    """Batched composition: 4096 pairs, deg p = 512, deg q = 64 (E and B
+    schemes; MODP exact by NTT, FP64 by direct convolution)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    npairs, degp, degq = args.pairs, 512, 64
+    res = {}
+    for dt in ("modp", "f64"):
+        pc, qc = W.composition_case(npairs, degp, degq, 4000, dt)
+        e = W.dense_univariate_exps(degp + 1)
+        if dt == "modp":
+            dq = torch.from_numpy(qc.view(np.int64)).cuda()
+            dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1]).view(np.int64)).cuda()
+        else:
+            dq = torch.from_numpy(qc).cuda()
+            dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1])).cuda()
+        out = torch.empty((npairs, degp * degq + 1), dtype=torch.int64 if dt == "modp" else torch.float64,
+                          device="cuda")
+        for s in ("E", "B"):
+            t = fpl.fp_compile(e, np.ones(degp + 1, dtype=np.uint64 if dt == "modp" else np.float64), s,
+                               modp=dt == "modp")
+            steps = args.steps if dt == "modp" else 1
+            ms = _timed(lambda: fpl.fp_compose(t, dt, dq, pcoeffs=dp, out=out), steps, 1 if dt == "f64" else args.warmup)
+            res["%s/%s" % (dt, s)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
+                                      "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3)}
+    line = {"metric": "compositions/s", "workload": "batched composition, %d pairs, deg p %d, deg q %d" %
+            (npairs, degp, degq), "results": res, "n_gpus": 1, "data": "synthetic"}
+    print(json.dumps(line))
+
+
+def run_eval_config(args):
+    """Per-configuration evaluation measurements: dense univariate 1024 terms at
+    65536 points (E), trivariate total degree 40 at 2^22 points (IV64, MODP)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    res = {}
+    e, c, x = W.univariate_case(1024, 65536, 1)
+    t = fpl.fp_compile(e, c, "E")
+    dx = torch.from_numpy(x).cuda()
+    ms = _timed(lambda: fpl.fp_eval(t, "f64", dx), 50, 5)
+    res["univariate_1024_E_f64_65536pts"] = {"ms": ms, "G_term_evals_per_s": 1024 * 65536 / (ms * 1e6)}
+    npts = 1 << 22
+    e, c, (lo, hi) = W.trivariate_case(40, npts, 300, "iv64")
+    t = fpl.fp_compile(e, c, "E")
+    dp = torch.from_numpy(np.ascontiguousarray(np.stack([lo, hi], axis=1))).cuda()
+    ms = _timed(lambda: fpl.fp_eval(t, "iv64", dp), 2, 1)
+    res["trivariate_deg40_E_iv64_2^22"] = {"ms": ms, "G_term_evals_per_s": len(e) * npts / (ms * 1e6)}
+    for s in ("E", "B"):
+        em, cm, xm = W.trivariate_case(40, npts, 301, "modp")
+        tm = fpl.fp_compile(em, cm, s, modp=True)
+        dm = torch.from_numpy(xm.view(np.int64)).cuda()
+        ms = _timed(lambda: fpl.fp_eval(tm, "modp", dm), 3, 1)
+        res["trivariate_deg40_%s_modp_2^22" % s] = {"ms": ms, "G_term_evals_per_s": len(em) * npts / (ms * 1e6)}
+    print(json.dumps({"metric": "G term-evals/s", "results": res, "n_gpus": 1, "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs"],
+                    help="univariate: the benchmark line; the others print their own measurement line")
+    ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--profile-case", action="store_true",
                     help="run two launches of one evaluation (for ncu) and exit")
     ap.add_argument("--profile-k", type=int, default=3000)
@@ -372,6 +450,10 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.workload == "compose":
+        run_compose(args)
+    elif args.workload == "eval-configs":
+        run_eval_config(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -50,114 +50,125 @@ __device__ __forceinline__ uint64_t d_add(uint64_t a, uint64_t b) {
 __device__ __forceinline__ uint64_t d_sub(uint64_t a, uint64_t b) { return a >= b ? a - b : a + (kP - b); }
 __device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP::mul_add(a, b, 0); }
 
-// Radix-2 transforms of one vector of length n held in shared memory by the
-// block.  Forward: decimation in frequency, natural order in, bit-reversed
-// order out.  Inverse: decimation in time, bit-reversed in, natural out
-// (unscaled).  tw[j] = w^j for the length-n root w (inverse: w^-j), j < n/2,
-// read with stride `ts` from a table of a longer length.
-__device__ void ntt_dif(uint64_t* a, int n, const uint64_t* tw, int ts) {
+// Radix-2 transforms of `count` vectors of length n held one after the other
+// in shared memory, all in lock step (one barrier per stage).  Forward:
+// decimation in frequency, natural order in, bit-reversed order out.
+// Inverse: decimation in time, bit-reversed in, natural out (unscaled).
+// tw[j] = w^j for the length-n root w (inverse table: w^-j), j < n/2.
+__device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
+  const int nb = count * (n >> 1);
   for (int half = n >> 1; half >= 1; half >>= 1) {
     __syncthreads();
-    const int step = (n / (2 * half)) * ts;
-    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+    const int step = n / (2 * half);
+    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+      const int v = e / (n >> 1), b = e - v * (n >> 1);
       const int grp = b / half, pos = b - grp * half;
+      uint64_t* x = a + v * n;
       const int i = grp * 2 * half + pos, j = i + half;
-      const uint64_t u = a[i], v = a[j];
-      a[i] = d_add(u, v);
-      a[j] = d_mul(d_sub(u, v), __ldg(tw + pos * step));
+      const uint64_t u = x[i], w = x[j];
+      x[i] = d_add(u, w);
+      x[j] = d_mul(d_sub(u, w), __ldg(tw + pos * step));
     }
   }
   __syncthreads();
 }
 
-__device__ void ntt_dit(uint64_t* a, int n, const uint64_t* tw, int ts) {
+__device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
+  const int nb = count * (n >> 1);
   for (int half = 1; half < n; half <<= 1) {
     __syncthreads();
-    const int step = (n / (2 * half)) * ts;
-    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+    const int step = n / (2 * half);
+    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+      const int v = e / (n >> 1), b = e - v * (n >> 1);
       const int grp = b / half, pos = b - grp * half;
+      uint64_t* x = a + v * n;
       const int i = grp * 2 * half + pos, j = i + half;
-      const uint64_t u = a[i], v = d_mul(a[j], __ldg(tw + pos * step));
-      a[i] = d_add(u, v);
-      a[j] = d_sub(u, v);
+      const uint64_t u = x[i], w = d_mul(x[j], __ldg(tw + pos * step));
+      x[i] = d_add(u, w);
+      x[j] = d_sub(u, w);
     }
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ int bitrev(int x, int logn) { return (int)(__brev((unsigned)x) >> (32 - logn)); }
+__device__ __forceinline__ int bitrev(int x, int logn) { return logn == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - logn)); }
 
 // ------------------------------------------------------------ MODP kernels
 // Forward transform of length n <= 4096 of src[pair][0..len) zero-padded,
-// into dst[pair][0..n).  One block per pair.
+// into dst[pair][0..n); vpb pairs per block.
 __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch,
-                                int n, const uint64_t* tw, int ts) {
+                                int n, int vpb, int64_t npairs, const uint64_t* tw) {
   extern __shared__ uint64_t sh[];
-  const int64_t pr = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = i < len ? src[pr * src_pitch + i] : 0;
-  ntt_dif(sh, n, tw, ts);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[pr * dst_pitch + i] = sh[i];
+  const int64_t p0 = (int64_t)blockIdx.x * vpb;
+  const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
+    const int v = e / n, i = e - v * n;
+    sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
+  }
+  ntt_dif(sh, n, vpb, tw);
+  for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+    const int v = e / n, i = e - v * n;
+    dst[(p0 + v) * dst_pitch + i] = sh[e];
+  }
 }
 
-// Inverse of a product: t = F(A) (in `prod`), multiplied by `fb` (the
-// transform of B), inverse transform, scaled by 1/n, then the first `outlen`
-// coefficients written (mode 0), or added into acc (mode 1), or written with
-// the constant `init[pair]` added at degree 0 (mode 2).
-__global__ void k_ntt_mul_inv_small(const uint64_t* prod, const uint64_t* fb, int64_t pitch, int n,
-                                    const uint64_t* twi, int ts, uint64_t ninv, uint64_t* out, int64_t out_pitch,
-                                    int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
+// Inverse of a product: F(A) (in `prod`) times F(B) (`fb`), inverse
+// transform, scaled by 1/n; the first `outlen` coefficients are written
+// (mode 0), added into out (mode 1), or written with init[pair] added at
+// degree 0 (mode 2).
+__global__ void k_ntt_mul_inv_small(const uint64_t* prod, int64_t pitch, const uint64_t* fb, int64_t fb_pitch, int n,
+                                    int vpb, int64_t npairs, const uint64_t* twi, uint64_t ninv, uint64_t* out,
+                                    int64_t out_pitch, int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
   extern __shared__ uint64_t sh[];
-  const int64_t pr = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = d_mul(prod[pr * pitch + i], fb[pr * pitch + i]);
-  ntt_dit(sh, n, twi, ts);
-  for (int i = threadIdx.x; i < outlen; i += blockDim.x) {
-    uint64_t v = d_mul(sh[i], ninv);
-    uint64_t* o = out + pr * out_pitch + i;
-    if (mode == 1) v = d_add(*o, v);
-    else if (mode == 2 && i == 0) v = d_add(v, init[pr * init_pitch]);
-    *o = v;
+  const int64_t p0 = (int64_t)blockIdx.x * vpb;
+  const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
+    const int v = e / n, i = e - v * n;
+    sh[e] = v < cnt ? d_mul(prod[(p0 + v) * pitch + i], fb[(p0 + v) * fb_pitch + i]) : 0;
+  }
+  ntt_dit(sh, n, vpb, twi);
+  for (int e = threadIdx.x; e < cnt * outlen; e += blockDim.x) {
+    const int v = e / outlen, i = e - v * outlen;
+    uint64_t val = d_mul(sh[v * n + i], ninv);
+    uint64_t* o = out + (p0 + v) * out_pitch + i;
+    if (mode == 1) val = d_add(*o, val);
+    else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
+    *o = val;
   }
 }
 
 // Four-step transform of length n = R * C (R, C <= 4096), vector x[C n1 + n2].
-// Column pass: for a tile of TC columns, each column (length R, stride C) is
-// transformed; forward multiplies by w_n^(k1 n2) afterwards, inverse divides
-// before.  Row pass: each row (length C, contiguous) is transformed.
-constexpr int kTileCols = 8;
-
+// Column pass: a tile of TC columns (length R, stride C) per block, all
+// transformed together; forward multiplies by w_n^(k1 n2) afterwards,
+// inverse divides before.  Row pass: rows of length C, contiguous.
 __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch, int R,
-                           int C, int logR, const uint64_t* twR, int tsR, const uint64_t* twn, int inverse,
+                           int C, int TC, int logR, const uint64_t* twR, const uint64_t* twn, int inverse,
                            uint64_t scale, int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
-  extern __shared__ uint64_t sh[];  // [kTileCols][R]
-  const int tiles = C / kTileCols;
+  extern __shared__ uint64_t sh[];  // [TC][R]
+  const int tiles = C / TC;
   const int64_t pr = blockIdx.x / tiles;
-  const int c0 = (blockIdx.x % tiles) * kTileCols;
+  const int c0 = (blockIdx.x % tiles) * TC;
   const int n = R * C;
-  for (int e = threadIdx.x; e < R * kTileCols; e += blockDim.x) {
-    const int r = e / kTileCols, c = e % kTileCols;
+  for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+    const int r = e / TC, c = e % TC;
     const int idx = r * C + c0 + c;
     uint64_t v = idx < len ? src[pr * src_pitch + idx] : 0;
     if (inverse) {
       // position r holds k1 = bitrev(r); undo the twiddle w^(k1 n2)
-      const int k1 = bitrev(r, logR);
-      const int64_t ex = ((int64_t)k1 * (c0 + c)) % n;
+      const int64_t ex = ((int64_t)bitrev(r, logR) * (c0 + c)) % n;
       v = d_mul(v, __ldg(twn + ((n - ex) % n)));
     }
     sh[c * R + r] = v;
   }
-  for (int c = 0; c < kTileCols; ++c) {
-    if (inverse) ntt_dit(sh + c * R, R, twR, tsR);
-    else ntt_dif(sh + c * R, R, twR, tsR);
-  }
-  for (int e = threadIdx.x; e < R * kTileCols; e += blockDim.x) {
-    const int r = e / kTileCols, c = e % kTileCols;
+  if (inverse) ntt_dit(sh, R, TC, twR);
+  else ntt_dif(sh, R, TC, twR);
+  for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
+    const int r = e / TC, c = e % TC;
     const int idx = r * C + c0 + c;
     uint64_t v = sh[c * R + r];
     if (!inverse) {
-      const int k1 = bitrev(r, logR);
-      const int64_t ex = ((int64_t)k1 * (c0 + c)) % n;
-      v = d_mul(v, __ldg(twn + ex));
-      dst[pr * dst_pitch + idx] = v;
+      const int64_t ex = ((int64_t)bitrev(r, logR) * (c0 + c)) % n;
+      dst[pr * dst_pitch + idx] = d_mul(v, __ldg(twn + ex));
     } else if (idx < outlen) {
       v = d_mul(v, scale);
       uint64_t* o = dst + pr * dst_pitch + idx;
@@ -168,17 +179,20 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
   }
 }
 
-__global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, const uint64_t* twC, int tsC, int inverse,
-                           const uint64_t* fb) {
+// rows (length C) of data[pair][R][C], vpb rows per block; the inverse pass
+// first multiplies by the matching rows of fb
+__global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, int vpb, const uint64_t* twC, int inverse,
+                           const uint64_t* fb, int64_t fb_pitch) {
   extern __shared__ uint64_t sh[];
-  const int64_t pr = blockIdx.x / R;
-  const int r = blockIdx.x % R;
-  uint64_t* row = data + pr * pitch + (int64_t)r * C;
-  const uint64_t* frow = fb ? fb + pr * pitch + (int64_t)r * C : nullptr;
-  for (int i = threadIdx.x; i < C; i += blockDim.x) sh[i] = frow ? d_mul(row[i], frow[i]) : row[i];
-  if (inverse) ntt_dit(sh, C, twC, tsC);
-  else ntt_dif(sh, C, twC, tsC);
-  for (int i = threadIdx.x; i < C; i += blockDim.x) row[i] = sh[i];
+  const int per_pair = R / vpb;
+  const int64_t pr = blockIdx.x / per_pair;
+  const int r0 = (blockIdx.x % per_pair) * vpb;
+  uint64_t* rows = data + pr * pitch + (int64_t)r0 * C;
+  const uint64_t* frows = fb ? fb + pr * fb_pitch + (int64_t)r0 * C : nullptr;
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = frows ? d_mul(rows[e], frows[e]) : rows[e];
+  if (inverse) ntt_dit(sh, C, vpb, twC);
+  else ntt_dif(sh, C, vpb, twC);
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) rows[e] = sh[e];
 }
 
 // leaf step: dst[0..len) = (init at degree 0 if first) + c[pair] * q^d
@@ -331,48 +345,62 @@ struct Composer {
     return tw[n];
   }
 
+  static void split(int n, int& R, int& C) {
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    C = 1 << ((lg + 1) / 2);
+    R = n / C;
+  }
+
   // forward transform of length n of src (first len coefficients) into dst
   void fwd(const Buf& src, int len, const Buf& dst, int n) {
     if (status != FP_OK) return;
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
-      k_ntt_fwd_small<<<(unsigned)npairs, 256, n * 8, st>>>((const uint64_t*)src.ptr, src.pitch, len,
-                                                            (uint64_t*)dst.ptr, dst.pitch, n, w.first, 1);
+      const int vpb = kNttSmemMax / n;
+      k_ntt_fwd_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, n, vpb, npairs, w.first);
     } else {
-      const int C = kNttSmemMax / 2 >= n / 2 ? n / 2 : 2048;  // row length
-      const int R = n / C;
+      int R, C;
+      split(n, R, C);
+      const int TC = kNttSmemMax / R;
       auto wR = twiddles(R);
       auto wC = twiddles(C);
       auto wn = twiddles(n);
-      k_ntt_cols<<<(unsigned)(npairs * (C / kTileCols)), 256, (size_t)R * kTileCols * 8, st>>>(
-          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, ilog2(R), wR.first, 1,
+      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)R * TC * 8, st>>>(
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, ilog2(R), wR.first,
           wn.first, 0, 1, 0, 0, nullptr, 0);
-      k_ntt_rows<<<(unsigned)(npairs * R), 256, (size_t)C * 8, st>>>((uint64_t*)dst.ptr, dst.pitch, R, C, wC.first,
-                                                                     1, 0, nullptr);
+      const int vpb = kNttSmemMax / C;
+      k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
+          (uint64_t*)dst.ptr, dst.pitch, R, C, vpb, wC.first, 0, nullptr, 0);
     }
     check();
   }
 
-  // out = first outlen coefficients of inverse(F(A) * F(B)), per mode
+  // out = first outlen coefficients of inverse(F(A) * F(B)), per mode;
+  // fa is overwritten
   void mul_inv(const Buf& fa, const Buf& fbuf, int n, const Buf& out, int outlen, int mode, const uint64_t* init,
                int64_t init_pitch) {
     if (status != FP_OK) return;
     const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
-      k_ntt_mul_inv_small<<<(unsigned)npairs, 256, n * 8, st>>>((const uint64_t*)fa.ptr, (const uint64_t*)fbuf.ptr,
-                                                                fa.pitch, n, w.second, 1, ninv, (uint64_t*)out.ptr,
-                                                                out.pitch, outlen, mode, init, init_pitch);
+      const int vpb = kNttSmemMax / n;
+      k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+          (const uint64_t*)fa.ptr, fa.pitch, (const uint64_t*)fbuf.ptr, fbuf.pitch, n, vpb, npairs, w.second, ninv,
+          (uint64_t*)out.ptr, out.pitch, outlen, mode, init, init_pitch);
     } else {
-      const int C = 2048;
-      const int R = n / C;
+      int R, C;
+      split(n, R, C);
+      const int TC = kNttSmemMax / R;
       auto wR = twiddles(R);
       auto wC = twiddles(C);
       auto wn = twiddles(n);
-      k_ntt_rows<<<(unsigned)(npairs * R), 256, (size_t)C * 8, st>>>((uint64_t*)fa.ptr, fa.pitch, R, C, wC.second,
-                                                                     1, 1, (const uint64_t*)fbuf.ptr);
-      k_ntt_cols<<<(unsigned)(npairs * (C / kTileCols)), 256, (size_t)R * kTileCols * 8, st>>>(
-          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, ilog2(R), wR.second, 1,
+      const int vpb = kNttSmemMax / C;
+      k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
+          (uint64_t*)fa.ptr, fa.pitch, R, C, vpb, wC.second, 1, (const uint64_t*)fbuf.ptr, fbuf.pitch);
+      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)R * TC * 8, st>>>(
+          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, ilog2(R), wR.second,
           wn.first, 1, ninv, outlen, mode, init, init_pitch);
     }
     check();
@@ -455,15 +483,29 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
   Buf ta{cm.alloc(npairs * Lmax * esz), Lmax}, tb{cm.alloc(npairs * Lmax * esz), Lmax};
   if (cm.status != FP_OK) { cm.release(); return cm.status; }
-  // product helper: dst (per mode) = A[0..alen) * B[0..blen)
-  auto product = [&](const Buf& A, int64_t alen, const Buf& B, int64_t blen, const Buf& dst, int mode,
+  // transforms of the powers q^d at the lengths they are used at
+  std::map<std::pair<int, int64_t>, Buf> qhat;
+  auto qhat_of = [&](int k, int64_t n) -> Buf {
+    auto key = std::make_pair(k, n);
+    auto it = qhat.find(key);
+    if (it != qhat.end()) return it->second;
+    Buf b{cm.alloc(npairs * n * esz), n};
+    cm.fwd(qp[k], (int)qp[k].pitch, b, (int)n);
+    qhat[key] = b;
+    return b;
+  };
+  // product helper: dst (per mode) = A[0..alen) * B[0..blen); B = q^d when bk >= 0
+  auto product = [&](const Buf& A, int64_t alen, const Buf& B, int64_t blen, int bk, const Buf& dst, int mode,
                      const void* init, int64_t init_pitch) {
     const int64_t rl = alen + blen - 1;
     if (modp) {
       const int n = (int)next_pow2(rl);
       cm.fwd(A, (int)alen, ta, n);
-      cm.fwd(B, (int)blen, tb, n);
-      cm.mul_inv(ta, tb, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
+      Buf fb = tb;
+      if (bk >= 0) fb = qhat_of(bk, n);
+      else cm.fwd(B, (int)blen, tb, n);
+      if (cm.status != FP_OK) return;
+      cm.mul_inv(ta, fb, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
     } else {
       // the source may be the destination slot: convolve from a copy
       k_copy_rows<double><<<grid_for(npairs * alen), 256, 0, st>>>((const double*)A.ptr, A.pitch, (double*)ta.ptr,
@@ -486,9 +528,9 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
           (const double*)q, degq + 1, (double*)qp[k].ptr, qp[k].pitch, degq + 1, npairs, 0);
       cm.check();
     } else if (op == kPowSq) {
-      product(qp[a1], qp[a1].pitch, qp[a1], qp[a1].pitch, qp[k], 0, nullptr, 0);
+      product(qp[a1], qp[a1].pitch, qp[a1], qp[a1].pitch, (int)a1, qp[k], 0, nullptr, 0);
     } else {
-      product(qp[a1], qp[a1].pitch, qp[a2], qp[a2].pitch, qp[k], 0, nullptr, 0);
+      product(qp[a1], qp[a1].pitch, qp[a2], qp[a2].pitch, (int)a2, qp[k], 0, nullptr, 0);
     }
   }
   // ---- the walk
@@ -501,7 +543,8 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
     const bool first = !seen[P];
     seen[P] = 1;
     const Buf& dst = acc[t->lh[P]];
-    const Buf& qd = qp[pid.at({0, t->pd[i]})];
+    const int qk = pid.at({0, t->pd[i]});
+    const Buf& qd = qp[qk];
     const int mode = first ? 2 : 1;
     const void* init = (const char*)cn.ptr + P * esz;
     if (!has_child[i]) {  // leaf: c_i * q^d
@@ -516,7 +559,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
             (const double*)init, N, npairs);
       cm.check();
     } else {
-      product(acc[t->lh[i]], degval(i) + 1, qd, qd.pitch, dst, mode, init, N);
+      product(acc[t->lh[i]], degval(i) + 1, qd, qd.pitch, qk, dst, mode, init, N);
     }
   }
   // ---- root: r = acc (or c) times q^d(root)
@@ -546,8 +589,9 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       else k_copy_rows<double><<<grid_for(npairs * outlen), 256, 0, st>>>((const double*)src.ptr, src.pitch, (double*)out, outlen, (int)outlen, npairs, 0);
       cm.check();
     } else {
-      const Buf& qd = qp[pid.at({0, d0})];
-      product(acc[t->lh[R]], degval(R) + 1, qd, qd.pitch, outb, 0, nullptr, 0);
+      const int qk = pid.at({0, d0});
+      const Buf& qd = qp[qk];
+      product(acc[t->lh[R]], degval(R) + 1, qd, qd.pitch, qk, outb, 0, nullptr, 0);
     }
   }
   const int rc = cm.status;

@@ -209,7 +209,19 @@ struct IV64 {
   using val = IV;
   using pw = IV;
   static __device__ __forceinline__ coef coef_from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
-  static __device__ __forceinline__ int cls(const IV& a) { return a.lo >= 0.0 ? 0 : (a.hi <= 0.0 ? 1 : 2); }
+  // Sign tests on the bit patterns (integer pipe; double compares would use
+  // the reduced-rate FP64 pipe): x >= 0.0 holds for sign bit clear or -0.0,
+  // x <= 0.0 for sign bit set or +0.0 (NaN bounds do not occur).
+  static __device__ __forceinline__ bool ge0(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ull;
+  }
+  static __device__ __forceinline__ bool le0(double x) {
+    const long long b = __double_as_longlong(x);
+    return b <= 0;  // sign bit set, or +0.0
+  }
+  static __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+  static __device__ __forceinline__ int cls(const IV& a) { return ge0(a.lo) ? 0 : (le0(a.hi) ? 1 : 2); }
   // Moore's nine sign cases: each bound is the directed rounding of the exact
   // extreme product.
   static __device__ __forceinline__ IV mul(const IV& a, const IV& b) {
@@ -264,7 +276,7 @@ struct IV64 {
     if (first) {
       IV r;
       r.lo = p.lo;
-      r.hi = (p.hi == 0.0) ? 0.0 : p.hi;
+      r.hi = is_zero(p.hi) ? 0.0 : p.hi;
       *dst = r;
     } else {
       const IV m = *dst;
