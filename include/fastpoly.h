@@ -195,6 +195,31 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
 int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
                int64_t npairs, void* out, void* stream);
 
+/*
+ * fp_compose_noalloc -- fp_compose for callers that must not allocate device
+ * memory: code running under a memory manager that owns the whole device
+ * (a serving engine that reserves HBM up front and forbids libraries from
+ * calling cudaMalloc / cudaMallocAsync), or code running where allocation
+ * calls are not allowed.  The paper has no counterpart; this is a property of
+ * the library, not of the method.
+ *
+ * Same arguments, layouts and results as fp_compose.  The work space comes
+ * from one region of FP_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits; nothing is allocated or freed.
+ *   - The first call on a device looks up that region's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the region and it keeps the last call's contents, so
+ *     calls that overlap on the GPU (other streams, other threads) race:
+ *     serialise them.
+ *   - A problem whose work space exceeds the region returns FP_E_TOO_LARGE
+ *     before any work is enqueued (roughly: npairs x deg(p) x degq x 8 bytes x
+ *     (lazy height + 6) must fit).
+ * The call synchronises `stream` while it uploads its small tables.
+ */
+#define FP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q,
+                       int32_t degq, int64_t npairs, void* out, void* stream);
+
 /* fp_eval_plain_f64 -- the comparison baseline: one launch per polynomial,
  * one thread per point, Horner's rule over the dense coefficient vector
  * coeffs[0..ncoeffs-1] (index = degree), FP64, no tree.  Device pointers. */

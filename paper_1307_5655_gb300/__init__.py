@@ -33,6 +33,7 @@ for _name, _args in {
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
+    "fp_compose_noalloc": [_P, _I, _P, _P, _I, _I64, _P, _P],
 }.items():
     getattr(_lib, _name).restype = _I
     getattr(_lib, _name).argtypes = _args
@@ -225,4 +226,24 @@ def fp_compose(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
     pc = None if pcoeffs is None else _ptr(pcoeffs)
     _check(_lib.fp_compose(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
                            _stream_handle(stream)), "fp_compose")
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def fp_compose_noalloc(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
+    """fp_compose without any device allocation by the library: the work space
+    is a fixed region (NOALLOC_SCRATCH_BYTES per device) shared by all calls,
+    so calls must not overlap on the GPU.  The output buffer `out` should be
+    provided by the caller (allocating it here would defeat the purpose)."""
+    import torch
+    npairs, nq = q.shape
+    if degp is None:
+        degp = int(tree.export()["node_e"][0, 0]) if tree.info()["nnodes"] else 0
+    if out is None:
+        out = torch.empty((npairs, degp * (nq - 1) + 1), dtype=_torch_dtype(dtype), device=q.device)
+    pc = None if pcoeffs is None else _ptr(pcoeffs)
+    _check(_lib.fp_compose_noalloc(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
+                                   _stream_handle(stream)), "fp_compose_noalloc")
     return out

@@ -230,7 +230,9 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
 }
 
 int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
-                   void* out, cudaStream_t st);
+                   void* out, cudaStream_t st, unsigned char* arena, size_t arena_cap);
+int compose_noalloc_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
+                           int64_t npairs, void* out, cudaStream_t st);
 
 }  // namespace fp
 
@@ -348,7 +350,14 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
                void* out, void* stream) {
   int dev = -1;
   if (p && (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev.device)) { cudaGetLastError(); return FP_E_BAD_VALUE; }
-  return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream);
+  return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream, nullptr, 0);
+}
+
+int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
+                       int64_t npairs, void* out, void* stream) {
+  int dev = -1;
+  if (p && (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev.device)) { cudaGetLastError(); return FP_E_BAD_VALUE; }
+  return compose_noalloc_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream);
 }
 
 int fp_eval_plain_f64(const double* coeffs, int64_t ncoeffs, const double* points, int64_t npts, double* out,

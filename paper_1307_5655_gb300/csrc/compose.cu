@@ -300,10 +300,24 @@ struct Composer {
   std::vector<void*> owned;
   // twiddles (MODP): forward/inverse powers of w_n for every length n used
   std::map<int, std::pair<uint64_t*, uint64_t*>> tw;
+  // when set, work space is carved from this caller-provided region instead
+  // of being allocated (fp_compose_noalloc)
+  unsigned char* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
 
   void* alloc(size_t bytes) {
     void* p = nullptr;
     if (status != FP_OK) return nullptr;
+    if (arena) {
+      const size_t sz = (bytes + 255) & ~(size_t)255;
+      if (arena_used + sz > arena_cap) {
+        status = FP_E_TOO_LARGE;
+        return nullptr;
+      }
+      p = arena + arena_used;
+      arena_used += sz;
+      return p;
+    }
     if (cudaMallocAsync(&p, bytes < 16 ? 16 : bytes, st) != cudaSuccess) {
       cudaGetLastError();
       status = FP_E_NOMEM;
@@ -417,7 +431,7 @@ int64_t next_pow2(int64_t x) {
 
 // Composition entry (declared in capi.cu).
 int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
-                   void* out, cudaStream_t st) {
+                   void* out, cudaStream_t st, unsigned char* arena = nullptr, size_t arena_cap = 0) {
   if (!t || !q || !out || degq < 0 || npairs < 0) return FP_E_BAD_VALUE;
   if (t->nvars != 1) return FP_E_BAD_VALUE;
   if (dtype == FP_MODP ? t->coeff_type != FP_MODP : (dtype != FP_F64 || t->coeff_type != FP_F64)) return FP_E_DTYPE;
@@ -430,6 +444,8 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   const size_t esz = 8;
   if (outlen > (1 << 26)) return FP_E_TOO_LARGE;
   Composer cm{t, dtype, degq, npairs, st};
+  cm.arena = arena;
+  cm.arena_cap = arena_cap;
   Buf outb{out, outlen};
   if (N == 0) {  // zero polynomial
     k_fill_zero<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, 0, (int)outlen, npairs);
@@ -597,6 +613,104 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   const int rc = cm.status;
   cm.release();
   return rc;
+}
+
+
+// ------------------------------------------------------------ allocation-free entry
+// Work space of fp_compose_noalloc: one region per device, reserved when the
+// library is loaded and held until the process exits.  Every call carves its
+// buffers from the start of it; calls that overlap on the device race.
+static __device__ __align__(256) unsigned char g_compose_scratch[FP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Bytes fp_compose's work space needs, buffer by buffer in the order the
+// driver carves them (each rounded up to 256 bytes).
+size_t compose_workspace_bytes(const fp_tree* t, bool modp, bool shared_coeffs, int32_t degq, int64_t npairs) {
+  auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const int64_t N = t->nnodes;
+  if (N == 0) return 0;
+  size_t total = r256(npairs * N * 8) + r256(N * 8);
+  if (shared_coeffs) total += r256(t->nterms_in * 8);
+  std::vector<int64_t> maxe(N);
+  for (int64_t i = 0; i < N; ++i) maxe[i] = t->node_e[i];
+  for (int64_t i = 0; i + 1 < N; ++i) maxe[t->parent[i]] = std::max(maxe[t->parent[i]], maxe[i]);
+  auto degval = [&](int64_t i) { return (maxe[i] - t->node_e[i]) * (int64_t)degq; };
+  std::vector<int64_t> cap(t->max_lh + 1, 1);
+  for (int64_t i = 0; i < N; ++i) cap[t->lh[i]] = std::max(cap[t->lh[i]], degval(i) + 1);
+  for (int64_t c : cap) total += r256(npairs * c * 8);
+  const int npow = (int)t->pow_prog.size();
+  int64_t maxprod = 1;
+  for (int k = 0; k < npow; ++k) {
+    total += r256(npairs * (t->pow_deg[k] * degq + 1) * 8);
+    maxprod = std::max(maxprod, t->pow_deg[k] * degq + 1);
+  }
+  for (int64_t i = 0; i + 1 < N; ++i) maxprod = std::max(maxprod, degval(i) + t->pd[i] * degq + 1);
+  const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
+  total += 2 * r256(npairs * Lmax * 8);
+  if (!modp) return total;
+  // transforms: twiddle tables per length and cached transforms of q^d
+  std::map<std::pair<int32_t, int64_t>, int> pid;
+  for (int k = 0; k < npow; ++k) pid[{t->pow_var[k], t->pow_deg[k]}] = k;
+  std::map<int64_t, int> tw;
+  std::map<std::pair<int, int64_t>, int> qh;
+  auto use = [&](int64_t rl, int bk) {
+    const int64_t n = next_pow2(rl);
+    if (n <= kNttSmemMax) tw[n] = 1;
+    else {
+      int lg = 0;
+      while ((1ll << lg) < n) ++lg;
+      const int64_t C = 1ll << ((lg + 1) / 2);
+      tw[n / C] = 1;
+      tw[C] = 1;
+      tw[n] = 1;
+    }
+    if (bk >= 0) qh[{bk, n}] = 1;
+  };
+  for (int k = 0; k < npow; ++k) {
+    const uint32_t w = t->pow_prog[k];
+    const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+    const int64_t l1 = t->pow_deg[a1] * degq + 1;
+    if (op == kPowSq) use(2 * l1 - 1, (int)a1);
+    else if (op == kPowMulX) use(l1 + t->pow_deg[a2] * degq, (int)a2);
+  }
+  std::vector<uint8_t> has_child(N, 0);
+  for (int64_t i = 0; i + 1 < N; ++i) has_child[t->parent[i]] = 1;
+  for (int64_t i = 0; i + 1 < N; ++i)
+    if (has_child[i]) use(degval(i) + 1 + t->pd[i] * degq, pid.at({0, t->pd[i]}));
+  const int64_t R = N - 1;
+  if (has_child[R] && t->pd[R] > 0) use(degval(R) + 1 + t->pd[R] * degq, pid.at({0, t->pd[R]}));
+  for (auto& kv : tw) total += 2 * r256(kv.first * 8);
+  for (auto& kv : qh) total += r256(npairs * kv.first.second * 8);
+  return total;
+}
+
+unsigned char* g_scratch_ptr[256];  // device address of g_compose_scratch, per device
+
+}  // namespace
+
+int compose_noalloc_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
+                           int64_t npairs, void* out, cudaStream_t st) {
+  if (!t || !q || !out || degq < 0 || npairs < 0) return FP_E_BAD_VALUE;
+  if (t->nvars != 1) return FP_E_BAD_VALUE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return FP_E_CUDA; }
+  if (!g_scratch_ptr[dev]) {
+    // set-up, once per device, with that device current: host code needs the
+    // device address of the array (the symbol itself is a host-side stand-in)
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_compose_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return FP_E_CUDA;
+    }
+    g_scratch_ptr[dev] = (unsigned char*)ptr;
+  }
+  const bool modp = dtype == FP_MODP;
+  if ((modp || dtype == FP_F64) && npairs > 0 && t->nnodes > 0 && t->dev.device >= 0 &&
+      compose_workspace_bytes(t, modp, pcoeffs == nullptr, degq, npairs) > (size_t)FP_NOALLOC_SCRATCH_BYTES)
+    return FP_E_TOO_LARGE;
+  return compose_device(t, dtype, pcoeffs, q, degq, npairs, out, st, g_scratch_ptr[dev],
+                        (size_t)FP_NOALLOC_SCRATCH_BYTES);
 }
 
 }  // namespace fp
