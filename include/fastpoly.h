@@ -169,6 +169,34 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
                    int32_t* pd_var, int64_t* pd, int32_t* lazy_height);
 
 /*
+ * Batched evaluation: many jobs (trees of uneven size, each with its own
+ * points) of one value type in one launch per shared-memory class.  Each job
+ * uses the layouts of fp_eval and gets the result fp_eval would give it; the
+ * most expensive jobs are scheduled first.  Jobs with npts = 0 are skipped;
+ * zero polynomials are refused (FP_E_BAD_VALUE: use fp_eval).
+ */
+typedef struct {
+  const fp_tree* tree;  /* compiled tree (serves the batch's value type) */
+  const void* points;   /* device, layout of fp_eval */
+  int64_t npts;
+  void* out;            /* device, layout of fp_eval */
+} fp_job;
+
+typedef struct fp_batch fp_batch;
+
+/* fp_eval_batch -- one-shot: plan, upload the job table (stream-ordered
+ * allocation, released after the launches) and launch. */
+int fp_eval_batch(fp_dtype dtype, const fp_job* jobs, int64_t njobs, void* stream);
+
+/* fp_batch_create -- plan a batch once and upload its job table (synchronous);
+ * fp_batch_launch enqueues its kernels only (no allocation, no copy), so it can
+ * be captured into a CUDA graph and replayed while the trees and buffers named
+ * by the jobs stay alive; fp_batch_free releases the table. */
+int fp_batch_create(fp_dtype dtype, const fp_job* jobs, int64_t njobs, fp_batch** out);
+int fp_batch_launch(const fp_batch* batch, void* stream);
+void fp_batch_free(fp_batch* batch);
+
+/*
  * fp_compose -- batched composition r_j(y) = p_j(q_j(y)) for j < npairs: the
  * coefficient walk (Sec. 2.1) of p's tree run over polynomial values, the
  * "composition" of the paper's title, where values grow with each product

@@ -247,3 +247,59 @@ def fp_compose_noalloc(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream
     _check(_lib.fp_compose_noalloc(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
                                    _stream_handle(stream)), "fp_compose_noalloc")
     return out
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("tree", ctypes.c_void_p), ("points", ctypes.c_void_p), ("npts", ctypes.c_int64),
+                ("out", ctypes.c_void_p)]
+
+
+_lib.fp_eval_batch.restype = _I
+_lib.fp_eval_batch.argtypes = [_I, _P, _I64, _P]
+_lib.fp_batch_create.restype = _I
+_lib.fp_batch_create.argtypes = [_I, _P, _I64, ctypes.POINTER(_P)]
+_lib.fp_batch_launch.restype = _I
+_lib.fp_batch_launch.argtypes = [_P, _P]
+_lib.fp_batch_free.restype = None
+_lib.fp_batch_free.argtypes = [_P]
+
+
+def _jobs_array(jobs):
+    arr = (_Job * max(1, len(jobs)))()
+    for i, (tree, pts, out) in enumerate(jobs):
+        arr[i] = _Job(tree.handle, pts.data_ptr(), pts.shape[-1], out.data_ptr())
+    return arr
+
+
+def fp_eval_batch(dtype, jobs, stream=None):
+    """jobs: list of (tree, points, out) with CUDA tensors in fp_eval layouts."""
+    arr = _jobs_array(jobs)
+    _check(_lib.fp_eval_batch(DTYPES[dtype], ctypes.cast(arr, ctypes.c_void_p), len(jobs), _stream_handle(stream)),
+           "fp_eval_batch")
+
+
+class Batch:
+    """A planned batch (fp_batch_create); launch() only enqueues kernels and
+    can be captured in a CUDA graph.  Keep the trees and tensors alive."""
+
+    def __init__(self, dtype, jobs):
+        self._keep = list(jobs)
+        arr = _jobs_array(jobs)
+        h = ctypes.c_void_p()
+        _check(_lib.fp_batch_create(DTYPES[dtype], ctypes.cast(arr, ctypes.c_void_p), len(jobs), ctypes.byref(h)),
+               "fp_batch_create")
+        self._h = h.value
+
+    def launch(self, stream=None):
+        _check(_lib.fp_batch_launch(self._h, _stream_handle(stream)), "fp_batch_launch")
+
+    def free(self):
+        if self._h:
+            _lib.fp_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

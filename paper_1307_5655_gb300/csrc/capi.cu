@@ -146,6 +146,58 @@ __global__ void plain_horner_kernel(const double* __restrict__ c, int64_t nc, co
 
 }  // namespace
 
+// Kernel arguments of one evaluation (shared by fp_eval and the batch path).
+int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, EvalArgs& a,
+                   OpArgs& o) {
+  if (!t || !dtype_ok(t, dt)) return FP_E_DTYPE;
+  if (t->nnodes == 0) return FP_E_BAD_VALUE;
+  a = EvalArgs{};
+  a.ctrl = t->dev.ctrl;
+  a.pow_prog = t->dev.pow_prog;
+  a.pow_dv = t->dev.pow_dv;
+  a.nsteps = t->nnodes - 1;
+  a.npow = (int)t->pow_prog.size();
+  a.nslot = t->max_lh + 1;
+  a.nvars = t->nvars;
+  a.root_leaf = t->root_leaf;
+  a.root_lh = t->root_lh;
+  a.root_pid = t->root_pid;
+  a.points = points;
+  a.npts = npts;
+  a.out = out;
+  o = OpArgs{};
+  o.nops = (int64_t)t->ops.size();
+  o.pid_x1 = t->pid_x1;
+  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->pid_pow[d];
+  const int64_t root = t->nnodes - 1;
+  switch (dt) {
+    case FP_F64:
+      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
+      o.recs = t->dev.ops_f64; o.stream = t->dev.st_f64;
+      std::memcpy(&a.root_c, &t->c_f64[root], 8);
+      break;
+    case FP_IV64:
+      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
+      std::memcpy(&a.root_c, &t->c_f64[root], 8);
+      break;
+    case FP_F32C: {
+      a.ca = t->dev.ca_f32; a.cb = t->dev.cb_f32;
+      o.recs = t->dev.ops_f32; o.stream = t->dev.st_f32;
+      const float c = (float)t->c_f64[root];
+      uint32_t bits;
+      std::memcpy(&bits, &c, 4);
+      a.root_c = bits;
+      break;
+    }
+    case FP_MODP:
+      a.ca = t->dev.ca_u64; a.cb = t->dev.cb_u64;
+      o.recs = t->dev.ops_u64; o.stream = t->dev.st_u64;
+      a.root_c = t->c_u64[root];
+      break;
+  }
+  return FP_OK;
+}
+
 int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st,
                 int variant = 0) {
   if (variant < 0 || variant > 2) return FP_E_BAD_VALUE;
@@ -164,58 +216,12 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
     else fill_zero32_kernel<<<blocks, 256, 0, st>>>((uint32_t*)out, bytes / 4);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
   }
-  EvalArgs a{};
-  a.ctrl = t->dev.ctrl;
-  a.pow_prog = t->dev.pow_prog;
-  a.pow_dv = t->dev.pow_dv;
-  a.nsteps = t->nnodes - 1;
-  a.npow = (int)t->pow_prog.size();
-  a.nslot = t->max_lh + 1;
-  a.nvars = t->nvars;
-  a.root_leaf = t->root_leaf;
-  a.root_lh = t->root_lh;
-  a.root_pid = t->root_pid;
-  a.points = points;
-  a.npts = npts;
-  a.out = out;
-  OpArgs o{};
-  o.nops = (int64_t)t->ops.size();
-  o.pid_x1 = t->pid_x1;
-  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->pid_pow[d];
-  const int64_t root = t->nnodes - 1;
-  size_t vbytes = 8, pbytes = 8;
-  int ppt = 1;
-  switch (dt) {
-    case FP_F64: {
-      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
-      o.recs = t->dev.ops_f64; o.stream = t->dev.st_f64;
-      std::memcpy(&a.root_c, &t->c_f64[root], 8);
-      break;
-    }
-    case FP_IV64: {
-      a.ca = t->dev.ca_f64; a.cb = t->dev.cb_f64;
-      std::memcpy(&a.root_c, &t->c_f64[root], 8);
-      vbytes = pbytes = 16;
-      break;
-    }
-    case FP_F32C: {
-      a.ca = t->dev.ca_f32; a.cb = t->dev.cb_f32;
-      o.recs = t->dev.ops_f32; o.stream = t->dev.st_f32;
-      const float c = (float)t->c_f64[root];
-      uint32_t bits;
-      std::memcpy(&bits, &c, 4);
-      a.root_c = bits;
-      ppt = 2;
-      break;
-    }
-    case FP_MODP: {
-      a.ca = t->dev.ca_u64; a.cb = t->dev.cb_u64;
-      o.recs = t->dev.ops_u64; o.stream = t->dev.st_u64;
-      a.root_c = t->c_u64[root];
-      ppt = 2;
-      break;
-    }
-  }
+  EvalArgs a;
+  OpArgs o;
+  const int frc = fill_eval_args(t, dt, points, npts, out, a, o);
+  if (frc != FP_OK) return frc;
+  const size_t vbytes = dt == FP_IV64 ? 16 : 8, pbytes = vbytes;
+  const int ppt = (dt == FP_F32C || dt == FP_MODP) ? 2 : 1;
   const size_t smem = (vbytes * (size_t)a.nslot + pbytes * (size_t)a.nvars) * ppt * kTPB;
   if (smem > kSmemMax) return FP_E_TOO_LARGE;
   cudaError_t e = cudaSuccess;

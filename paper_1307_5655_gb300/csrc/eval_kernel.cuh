@@ -317,15 +317,13 @@ __device__ __forceinline__ typename A::pw binexp(typename A::pw x, uint32_t d) {
 // node computes its power on the fly (trees with very many distinct powers,
 // e.g. the Direct scheme).
 template <class A, int PPT, bool TABLE>
-__global__ void __launch_bounds__(kTPB) eval_kernel(const EvalArgs g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void node_tile(const EvalArgs& g, int64_t base, unsigned char* smem_raw) {
   using V = typename A::val;
   using W = typename A::pw;
   using C = typename A::coef;
   V* acc = reinterpret_cast<V*>(smem_raw);                          // [nslot][PPT][TPB]
   W* pw = reinterpret_cast<W*>(smem_raw + sizeof(V) * (size_t)g.nslot * PPT * kTPB);
   const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * (kTPB * PPT);
 
   if (TABLE) {
     // power table: every distinct x_v^d once per point
@@ -396,6 +394,12 @@ __global__ void __launch_bounds__(kTPB) eval_kernel(const EvalArgs g) {
     }
     if (idx < g.npts) A::store(g.out, idx, g.npts, r);
   }
+}
+
+template <class A, int PPT, bool TABLE>
+__global__ void __launch_bounds__(kTPB) eval_kernel(const EvalArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  node_tile<A, PPT, TABLE>(g, (int64_t)blockIdx.x * (kTPB * PPT), smem_raw);
 }
 
 
@@ -523,15 +527,13 @@ __device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]
 }
 
 template <class A, int PPT, int SCHEME>
-__global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int64_t base, unsigned char* smem_raw) {
   using V = typename A::val;
   using W = typename A::pw;
   using C = typename A::coef;
   V* acc = reinterpret_cast<V*>(smem_raw);  // [nslot][PPT][TPB]
   W* pw = reinterpret_cast<W*>(smem_raw + sizeof(V) * (size_t)g.nslot * PPT * kTPB);  // [npow][PPT][TPB]
   const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * (kTPB * PPT);
 
   for (int k = 0; k < g.npow; ++k) {
     const uint32_t w = __ldg(g.pow_prog + k);
@@ -632,6 +634,12 @@ __global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const 
     if (g.root_pid >= 0) r = A::apply_root_power(r, pw[(g.root_pid * PPT + p) * kTPB + tid]);
     if (idx < g.npts) A::store(g.out, idx, g.npts, r);
   }
+}
+
+template <class A, int PPT, int SCHEME>
+__global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ops_tile<A, PPT, SCHEME>(g, o, (int64_t)blockIdx.x * (kTPB * PPT), smem_raw);
 }
 
 // Launch helpers (defined per type in eval_<type>.cu).  variant: 0 = choose,
