@@ -431,11 +431,113 @@ def run_eval_config(args):
     print(json.dumps({"metric": "G term-evals/s", "results": res, "n_gpus": 1, "data": "synthetic"}))
 
 
+def run_serve(args):
+    """Serving stream: requests each a univariate or bivariate polynomial with
+    term count log-uniform in [8, 65536] (bivariate: the first k monomials in
+    graded order), point count log-uniform in [1, 2^20], value type uniform
+    over FP64 / FP32C / IV64 / MODP, coefficients and points uniform; scheme E
+    (B when k is not a power of two).  Trees are compiled once and stay
+    resident (a pool of 8 per value type and variable count).  Measured: the
+    saturated throughput (all requests submitted at once), then Poisson
+    arrivals at 0.7 x that rate with p50/p99 latency, and the same requests
+    served one launch at a time (fp_eval_host per request)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    r = W.rng(5000)
+    dts = ["f64", "f32c", "iv64", "modp"]
+    maxp = 1 << 20
+    pools, trees = {}, {}
+    for dt in dts:
+        for nv in (1, 2):
+            n = maxp * nv * (2 if dt == "iv64" else 1)
+            npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
+            buf = torch.empty(n, dtype=torch.float64 if npdt in (np.float64,) else
+                              (torch.float32 if npdt == np.float32 else torch.int64), pin_memory=True).numpy()
+            if dt == "modp":
+                buf = buf.view(np.uint64)
+                buf[:] = W.residues(n, 11 + nv)
+            else:
+                buf[:] = W.uniform_f64(n, 13 + nv).astype(npdt)
+            pools[(dt, nv)] = buf
+            lst = []
+            for i in range(8):
+                k = int(np.exp(r.uniform(np.log(8), np.log(65536))))
+                e = W.dense_univariate_exps(k) if nv == 1 else W.graded_prefix_exps(k, 2)
+                c = W.residues(len(e), 100 + i) if dt == "modp" else W.uniform_f64(len(e), 100 + i)
+                lst.append((fpl.fp_compile(e, c, "E" if (k & (k - 1)) == 0 else "B", modp=dt == "modp"), len(e)))
+            trees[(dt, nv)] = lst
+    outs = {}
+    for dt in dts:
+        npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
+        t = torch.empty(2 * maxp * (2 if npdt == np.float32 else 1), dtype=torch.float64, pin_memory=True).numpy()
+        outs[dt] = t.view(npdt)
+    reqs = []
+    for j in range(args.requests):
+        dt = dts[int(r.integers(0, 4))]
+        nv = 1 + int(r.integers(0, 2))
+        tree, k = trees[(dt, nv)][int(r.integers(0, 8))]
+        npts = int(np.exp(r.uniform(0, np.log(maxp))))
+        per = nv * (2 if dt == "iv64" else 1)
+        pts = pools[(dt, nv)][: per * npts].reshape((nv, 2, npts) if dt == "iv64" else (nv, npts))
+        shp = fpl.out_shape(dt, npts)
+        out = outs[dt][: int(np.prod(shp))].reshape(shp)
+        reqs.append((tree, dt, pts, out, k * npts))
+    total_evals = sum(x[4] for x in reqs)
+
+    def serve(arrivals):
+        srv = fpl.Server(hbm_budget_bytes=args.hbm_budget << 20, max_batch_jobs=256, streams=4)
+        lat = []
+        t0 = time.perf_counter()
+        for (tree, dt, pts, out, _), ta in zip(reqs, arrivals):
+            if ta is not None:
+                while time.perf_counter() - t0 < ta:
+                    pass
+            srv.submit(tree, dt, pts, out)
+            if len(lat) < len(reqs):
+                lat += [x[2] for x in srv.poll()]
+        srv.drain(3600)
+        wall = time.perf_counter() - t0
+        lat += [x[2] for x in srv.poll()]
+        st = srv.stats()
+        srv.close()
+        return wall, np.array(lat), st
+
+    serve([None] * 8)  # warm-up on a few requests is implicit in the first call's trees
+    wall_sat, lat_sat, st_sat = serve([None] * len(reqs))
+    rate = len(reqs) / wall_sat
+    gaps = W.rng(5001).exponential(1.0 / (0.7 * rate), size=len(reqs))
+    wall_open, lat_open, st_open = serve(list(np.cumsum(gaps)))
+    t0 = time.perf_counter()
+    for tree, dt, pts, out, _ in reqs:
+        fpl.fp_eval_host(tree, dt, pts)
+    wall_seq = time.perf_counter() - t0
+    line = {
+        "metric": "p50/p99 serve latency and throughput",
+        "workload": "%d requests, uni/bivariate, k log-uniform [8, 65536], points log-uniform [1, 2^20], "
+                    "value types uniform over f64/f32c/iv64/modp" % len(reqs),
+        "term_evals": total_evals,
+        "saturated": {"wall_s": wall_sat, "requests_per_s": rate, "G_term_evals_per_s": total_evals / wall_sat / 1e9,
+                      "batches": st_sat["batches"], "peak_hbm_bytes": st_sat["peak_bytes"]},
+        "poisson_0.7": {"rate_per_s": 0.7 * rate, "wall_s": wall_open,
+                        "p50_ms": float(np.percentile(lat_open, 50)) / 1e3,
+                        "p99_ms": float(np.percentile(lat_open, 99)) / 1e3,
+                        "G_term_evals_per_s": total_evals / wall_open / 1e9, "batches": st_open["batches"]},
+        "one_launch_per_request": {"wall_s": wall_seq, "requests_per_s": len(reqs) / wall_seq,
+                                   "G_term_evals_per_s": total_evals / wall_seq / 1e9},
+        "hbm_budget_MiB": args.hbm_budget, "n_gpus": 1, "data": "synthetic",
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs"],
+    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--hbm-budget", type=int, default=8192, help="MiB of device memory for requests in flight")
     ap.add_argument("--profile-case", action="store_true",
                     help="run two launches of one evaluation (for ncu) and exit")
     ap.add_argument("--profile-k", type=int, default=3000)
@@ -454,6 +556,8 @@ def main():
         run_compose(args)
     elif args.workload == "eval-configs":
         run_eval_config(args)
+    elif args.workload == "serve":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -197,6 +197,46 @@ int fp_batch_launch(const fp_batch* batch, void* stream);
 void fp_batch_free(fp_batch* batch);
 
 /*
+ * Serving with continuous batching.  Requests (a resident compiled tree, a
+ * value type, host points, a host result buffer) are submitted from any
+ * thread and complete asynchronously.  A worker thread admits pending
+ * requests oldest first while their device footprint (points + results) fits
+ * in hbm_budget_bytes (a request larger than the whole budget runs alone),
+ * groups requests of one value type into one batched launch on one of
+ * `streams` streams (copies in, fp_eval_batch, copies out), and retires
+ * batches as they finish, so requests that arrive while batches run are
+ * admitted as soon as a stream and memory free up.  Results equal fp_eval's.
+ * Host buffers should be pinned (page-locked) for the copies to overlap; they
+ * must stay valid until the request completes.  Trees must outlive the
+ * requests that use them.
+ */
+typedef struct fp_server fp_server;
+typedef struct {
+  size_t hbm_budget_bytes;  /* device bytes for the points and results in flight (> 0) */
+  int max_batch_jobs;       /* requests per batched launch (<= 0: 1024) */
+  int streams;              /* batches in flight at once (<= 0: 4) */
+} fp_server_cfg;
+typedef struct {
+  int64_t ticket;     /* as returned by fp_server_submit */
+  int status;         /* FP_OK or an error code */
+  double latency_us;  /* from submission to observed completion */
+} fp_completion;
+
+int fp_server_create(const fp_server_cfg* cfg, fp_server** out);
+/* npts = 0 completes at once.  Errors: FP_E_BAD_VALUE, FP_E_DTYPE. */
+int fp_server_submit(fp_server* s, const fp_tree* tree, fp_dtype dtype, const void* points_host,
+                     int64_t npts, void* out_host, int64_t* ticket);
+/* Up to `max` completions since the last poll (any order), count in *n. */
+int fp_server_poll(fp_server* s, fp_completion* done, int max, int* n);
+/* Wait (at most timeout_s seconds; <= 0: 60) until every submitted request has
+ * completed; FP_E_TIMEOUT otherwise. */
+int fp_server_drain(fp_server* s, double timeout_s);
+/* Peak device bytes admitted at once, number of batches launched. */
+int fp_server_stats(const fp_server* s, size_t* peak_bytes, int64_t* batches);
+/* Stops after the requests already submitted have completed. */
+void fp_server_destroy(fp_server* s);
+
+/*
  * fp_compose -- batched composition r_j(y) = p_j(q_j(y)) for j < npairs: the
  * coefficient walk (Sec. 2.1) of p's tree run over polynomial values, the
  * "composition" of the paper's title, where values grow with each product

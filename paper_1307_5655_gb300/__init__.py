@@ -303,3 +303,79 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_jobs", ctypes.c_int), ("streams", ctypes.c_int)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int), ("latency_us", ctypes.c_double)]
+
+
+_lib.fp_server_create.restype = _I
+_lib.fp_server_create.argtypes = [_P, ctypes.POINTER(_P)]
+_lib.fp_server_submit.restype = _I
+_lib.fp_server_submit.argtypes = [_P, _P, _I, _P, _I64, _P, ctypes.POINTER(ctypes.c_int64)]
+_lib.fp_server_poll.restype = _I
+_lib.fp_server_poll.argtypes = [_P, _P, _I, ctypes.POINTER(ctypes.c_int)]
+_lib.fp_server_drain.restype = _I
+_lib.fp_server_drain.argtypes = [_P, ctypes.c_double]
+_lib.fp_server_stats.restype = _I
+_lib.fp_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int64)]
+_lib.fp_server_destroy.restype = None
+_lib.fp_server_destroy.argtypes = [_P]
+
+
+class Server:
+    """Continuous-batching server (fp_server_*).  Host arrays passed to
+    submit() are kept alive until their completion is polled; pinned arrays
+    (e.g. torch pinned tensors' .numpy()) let the copies overlap."""
+
+    def __init__(self, hbm_budget_bytes, max_batch_jobs=1024, streams=4):
+        import threading
+        cfg = _ServerCfg(hbm_budget_bytes, max_batch_jobs, streams)
+        h = ctypes.c_void_p()
+        _check(_lib.fp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fp_server_create")
+        self._h = h.value
+        self._live = {}
+        self._lock = threading.Lock()
+
+    def submit(self, tree, dtype, points, out):
+        t = ctypes.c_int64()
+        npts = points.shape[-1]
+        with self._lock:
+            _check(_lib.fp_server_submit(self._h, tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out),
+                                         ctypes.byref(t)), "fp_server_submit")
+            self._live[t.value] = (tree, points, out)
+        return t.value
+
+    def poll(self, max_items=4096):
+        buf = (_Completion * max_items)()
+        n = ctypes.c_int()
+        _check(_lib.fp_server_poll(self._h, ctypes.cast(buf, ctypes.c_void_p), max_items, ctypes.byref(n)),
+               "fp_server_poll")
+        res = [(buf[i].ticket, buf[i].status, buf[i].latency_us) for i in range(n.value)]
+        with self._lock:
+            for tk, _, _ in res:
+                self._live.pop(tk, None)
+        return res
+
+    def drain(self, timeout_s=60.0):
+        _check(_lib.fp_server_drain(self._h, timeout_s), "fp_server_drain")
+
+    def stats(self):
+        pk, nb = ctypes.c_size_t(), ctypes.c_int64()
+        _check(_lib.fp_server_stats(self._h, ctypes.byref(pk), ctypes.byref(nb)), "fp_server_stats")
+        return {"peak_bytes": pk.value, "batches": nb.value}
+
+    def close(self):
+        if self._h:
+            _lib.fp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
