@@ -57,6 +57,23 @@ def workload_config():
     }
 
 
+# ------------------------------------------------------------------ ranks
+def points_seed(rank):
+    """Each rank evaluates its own points (weak scaling, no data exchange)."""
+    return SEED + 1 + 7919 * rank
+
+
+def combine_ranks(units_per_rank, ms_local, dist=None, device=None):
+    """Weak scaling: every rank processed units_per_rank units; the job took as
+    long as the slowest rank.  Returns (units of all ranks, max time in ms)."""
+    if dist is None:
+        return units_per_rank, ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return units_per_rank * dist.get_world_size(), float(t.item())
+
+
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_chunk(args):
     k, lo, hi, seed = args
@@ -180,7 +197,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     # inputs resident in HBM; each rank evaluates its own points (weak scaling)
-    x64 = W.points_f64(1, NPTS, SEED + 1 + 7919 * rank)
+    x64 = W.points_f64(1, NPTS, points_seed(rank))
     d64 = torch.from_numpy(x64).to(dev)
     d32 = torch.from_numpy(W.to_f32(x64)).to(dev)
     out64 = torch.empty(NPTS, dtype=torch.float64, device=dev)
@@ -229,10 +246,7 @@ def run_ours(args):
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     clk = clocks.stop(torch.cuda.current_device()) if rank == 0 else None
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    units, ms = combine_ranks(workload_config()["term_evals_per_step"] * args.steps, ms, dist, dev)
 
     # dominant kernel: FP64 evaluation
     f64_ms = sum(a.elapsed_time(b) for dt, k, a, b, _ in launches if dt == "f64")
@@ -284,7 +298,6 @@ def run_ours(args):
     h2d = len(trees) * NPTS * (8 + 4)
     d2h = len(trees) * NPTS * (8 + 8)
 
-    units = workload_config()["term_evals_per_step"] * args.steps * world
     value = units / (ms * 1e-3) / 1e9
     e2e_value = workload_config()["term_evals_per_step"] * world / e2e_s / 1e9
 
