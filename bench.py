@@ -544,9 +544,70 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_accuracy(args):
+    """Error of the FP64 and compensated FP32 paths against the oracle per
+    (k, scheme) of the benchmark workload, on a sample of 4096 of its points:
+    max and median of |r - p| / sum |c_e x^e| (the condition scale)."""
+    import torch
+    import workloads as W
+    import oracle as O
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    x = W.points_f64(1, NPTS, points_seed(0))
+    idx = np.sort(W.rng(9).choice(NPTS, 4096, replace=False))
+    d64 = torch.from_numpy(x).cuda()
+    d32 = torch.from_numpy(W.to_f32(x)).cuda()
+    res = {}
+    for k in KS:
+        e, c, _ = W.univariate_case(k, 1, SEED + k)
+        want, S = O.eval_f64(e, c, x[:, idx])
+        c32 = W.to_f32(c).astype(np.float64)
+        want32, S32 = O.eval_f64(e, c32, W.to_f32(x[:, idx]).astype(np.float64))
+        for s in SCHEMES:
+            t = fpl.fp_compile(e, c, s)
+            g = fpl.fp_eval(t, "f64", d64).cpu().numpy()[idx]
+            g32 = fpl.fp_eval(t, "f32c", d32).cpu().numpy()[:, idx]
+            r64 = np.abs(g - want) / S
+            r32 = np.abs(g32[0].astype(np.float64) + g32[1].astype(np.float64) - want32) / S32
+            plain32 = np.abs(g32[0].astype(np.float64) - want32) / S32
+            res["%s/%d" % (s, k)] = {
+                "f64_max": float(r64.max()), "f64_median": float(np.median(r64)),
+                "f64_bound_4nu": 4 * (k - 1) * 2.0 ** -53,
+                "f32c_max": float(r32.max()), "f32c_median": float(np.median(r32)),
+                "f32c_hi_only_median": float(np.median(plain32)),
+            }
+    print(json.dumps({"metric": "relative error vs oracle (scaled by sum |c_e x^e|)", "sample_points": 4096,
+                      "results": res}))
+
+
+def run_staircase(args):
+    """The paper's staircase (Sec. 1.2, Sec. 3): composition time around a
+    power-of-two term count, Estrin vs Balanced, mod p, deg q = 64."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    npairs, degq = args.pairs, 64
+    res = {}
+    for terms in (254, 255, 256, 257, 258, 510, 511, 512, 513, 514):
+        degp = terms - 1
+        pc, qc = W.composition_case(npairs, degp, degq, 7000 + terms, "modp")
+        dq = torch.from_numpy(qc.view(np.int64)).cuda()
+        dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1]).view(np.int64)).cuda()
+        out = torch.empty((npairs, degp * degq + 1), dtype=torch.int64, device="cuda")
+        e = W.dense_univariate_exps(terms)
+        for s in ("E", "B"):
+            t = fpl.fp_compile(e, np.ones(terms, dtype=np.uint64), s, modp=True)
+            ms = _timed(lambda: fpl.fp_compose(t, "modp", dq, pcoeffs=dp, out=out), args.steps, 1)
+            res["%s/%d" % (s, terms)] = ms
+    print(json.dumps({"metric": "ms per batch of %d compositions mod p, deg q %d" % (npairs, degq),
+                      "results": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve"],
+    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve", "accuracy",
+                                                                "staircase"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=1000)
@@ -571,6 +632,10 @@ def main():
         run_eval_config(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "accuracy":
+        run_accuracy(args)
+    elif args.workload == "staircase":
+        run_staircase(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -50,42 +50,77 @@ __device__ __forceinline__ uint64_t d_add(uint64_t a, uint64_t b) {
 __device__ __forceinline__ uint64_t d_sub(uint64_t a, uint64_t b) { return a >= b ? a - b : a + (kP - b); }
 __device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP::mul_add(a, b, 0); }
 
-// Radix-2 transforms of `count` vectors of length n held one after the other
-// in shared memory, all in lock step (one barrier per stage).  Forward:
-// decimation in frequency, natural order in, bit-reversed order out.
-// Inverse: decimation in time, bit-reversed in, natural out (unscaled).
-// tw[j] = w^j for the length-n root w (inverse table: w^-j), j < n/2.
+// Transforms of `count` vectors of length n held one after the other in
+// shared memory, all in lock step.  Forward: decimation in frequency, natural
+// order in, bit-reversed order out.  Inverse: decimation in time,
+// bit-reversed in, natural out (unscaled).  tw[j] = w^j for the length-n root
+// w (inverse table: w^-j), j < n/2.  Two radix-2 stages are fused per pass
+// (radix 4: one barrier and one shared-memory round trip per two stages),
+// with one radix-2 stage when log2 n is odd.
+__device__ __forceinline__ int ilog2_dev(int n) { return 31 - __clz(n); }
+
 __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
-  const int nb = count * (n >> 1);
-  for (int half = n >> 1; half >= 1; half >>= 1) {
+  const int per = n >> 2;
+  int half = n >> 1;
+  for (; half >= 2; half >>= 2) {
     __syncthreads();
-    const int step = n / (2 * half);
-    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
-      const int v = e / (n >> 1), b = e - v * (n >> 1);
-      const int grp = b / half, pos = b - grp * half;
-      uint64_t* x = a + v * n;
-      const int i = grp * 2 * half + pos, j = i + half;
-      const uint64_t u = x[i], w = x[j];
-      x[i] = d_add(u, w);
-      x[j] = d_mul(d_sub(u, w), __ldg(tw + pos * step));
+    const int q = half >> 1, s1 = n / (2 * half), s2 = n / half;
+    for (int e = threadIdx.x; e < count * per; e += blockDim.x) {
+      const int v = e / per, u = e - v * per;
+      const int grp = u / q, pos = u - grp * q;
+      uint64_t* x = a + v * n + grp * 2 * half;
+      const int i0 = pos, i1 = pos + q, i2 = pos + half, i3 = pos + half + q;
+      const uint64_t a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
+      const uint64_t b0 = d_add(a0, a2), b2 = d_mul(d_sub(a0, a2), __ldg(tw + pos * s1));
+      const uint64_t b1 = d_add(a1, a3), b3 = d_mul(d_sub(a1, a3), __ldg(tw + (pos + q) * s1));
+      const uint64_t t = __ldg(tw + pos * s2);
+      x[i0] = d_add(b0, b1);
+      x[i1] = d_mul(d_sub(b0, b1), t);
+      x[i2] = d_add(b2, b3);
+      x[i3] = d_mul(d_sub(b2, b3), t);
+    }
+  }
+  if (half == 1) {  // last radix-2 stage: pairs (2g, 2g + 1), twiddle 1
+    __syncthreads();
+    for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
+      uint64_t* x = a + 2 * e;
+      const uint64_t u = x[0], w = x[1];
+      x[0] = d_add(u, w);
+      x[1] = d_sub(u, w);
     }
   }
   __syncthreads();
 }
 
 __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
-  const int nb = count * (n >> 1);
-  for (int half = 1; half < n; half <<= 1) {
+  int half = 1;
+  if (n >= 2 && (ilog2_dev(n) & 1)) {  // first radix-2 stage: pairs (2g, 2g + 1), twiddle 1
     __syncthreads();
-    const int step = n / (2 * half);
-    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
-      const int v = e / (n >> 1), b = e - v * (n >> 1);
-      const int grp = b / half, pos = b - grp * half;
-      uint64_t* x = a + v * n;
-      const int i = grp * 2 * half + pos, j = i + half;
-      const uint64_t u = x[i], w = d_mul(x[j], __ldg(tw + pos * step));
-      x[i] = d_add(u, w);
-      x[j] = d_sub(u, w);
+    for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
+      uint64_t* x = a + 2 * e;
+      const uint64_t u = x[0], w = x[1];
+      x[0] = d_add(u, w);
+      x[1] = d_sub(u, w);
+    }
+    half = 2;
+  }
+  const int per = n >> 2;
+  for (; half < n; half <<= 2) {
+    __syncthreads();
+    const int s1 = n / (2 * half), s2 = n / (4 * half);
+    for (int e = threadIdx.x; e < count * per; e += blockDim.x) {
+      const int v = e / per, u = e - v * per;
+      const int grp = u / half, pos = u - grp * half;
+      uint64_t* x = a + v * n + grp * 4 * half;
+      const int i0 = pos, i1 = pos + half, i2 = pos + 2 * half, i3 = pos + 3 * half;
+      const uint64_t t = __ldg(tw + pos * s1);
+      const uint64_t a0 = x[i0], a1 = d_mul(x[i1], t), a2 = x[i2], a3 = d_mul(x[i3], t);
+      const uint64_t b0 = d_add(a0, a1), b1 = d_sub(a0, a1), b2 = d_add(a2, a3), b3 = d_sub(a2, a3);
+      const uint64_t c2 = d_mul(b2, __ldg(tw + pos * s2)), c3 = d_mul(b3, __ldg(tw + (pos + half) * s2));
+      x[i0] = d_add(b0, c2);
+      x[i2] = d_sub(b0, c2);
+      x[i1] = d_add(b1, c3);
+      x[i3] = d_sub(b1, c3);
     }
   }
   __syncthreads();
@@ -125,6 +160,37 @@ __global__ void k_ntt_mul_inv_small(const uint64_t* prod, int64_t pitch, const u
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
     const int v = e / n, i = e - v * n;
     sh[e] = v < cnt ? d_mul(prod[(p0 + v) * pitch + i], fb[(p0 + v) * fb_pitch + i]) : 0;
+  }
+  ntt_dit(sh, n, vpb, twi);
+  for (int e = threadIdx.x; e < cnt * outlen; e += blockDim.x) {
+    const int v = e / outlen, i = e - v * outlen;
+    uint64_t val = d_mul(sh[v * n + i], ninv);
+    uint64_t* o = out + (p0 + v) * out_pitch + i;
+    if (mode == 1) val = d_add(*o, val);
+    else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
+    *o = val;
+  }
+}
+
+// A whole product for n <= 4096, one launch: transform of src (first len
+// coefficients, zero-padded), times the cached transform fb, inverse, scaled
+// by 1/n, written per mode as in k_ntt_mul_inv_small.  src may be the
+// destination: a block reads its rows completely before writing them.
+__global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int len, const uint64_t* fb,
+                                    int64_t fb_pitch, int n, int vpb, int64_t npairs, const uint64_t* tw,
+                                    const uint64_t* twi, uint64_t ninv, uint64_t* out, int64_t out_pitch, int outlen,
+                                    int mode, const uint64_t* init, int64_t init_pitch) {
+  extern __shared__ uint64_t sh[];
+  const int64_t p0 = (int64_t)blockIdx.x * vpb;
+  const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
+    const int v = e / n, i = e - v * n;
+    sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
+  }
+  ntt_dif(sh, n, vpb, tw);
+  for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
+    const int v = e / n, i = e - v * n;
+    if (v < cnt) sh[e] = d_mul(sh[e], fb[(p0 + v) * fb_pitch + i]);
   }
   ntt_dit(sh, n, vpb, twi);
   for (int e = threadIdx.x; e < cnt * outlen; e += blockDim.x) {
@@ -516,6 +582,18 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
     const int64_t rl = alen + blen - 1;
     if (modp) {
       const int n = (int)next_pow2(rl);
+      if (bk >= 0 && n <= kNttSmemMax) {  // one fused launch
+        const Buf fb = qhat_of(bk, n);
+        if (cm.status != FP_OK) return;
+        auto w = cm.twiddles(n);
+        const int vpb = kNttSmemMax / n;
+        const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
+        k_ntt_product_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+            (const uint64_t*)A.ptr, A.pitch, (int)alen, (const uint64_t*)fb.ptr, fb.pitch, n, vpb, npairs, w.first,
+            w.second, ninv, (uint64_t*)dst.ptr, dst.pitch, (int)rl, mode, (const uint64_t*)init, init_pitch);
+        cm.check();
+        return;
+      }
       cm.fwd(A, (int)alen, ta, n);
       Buf fb = tb;
       if (bk >= 0) fb = qhat_of(bk, n);

@@ -168,6 +168,8 @@ struct MODP {
     if (r >= P) r -= P;
     return r;
   }
+  // (a b + c) mod p from the 128-bit product (a carry-chain version on 32-bit
+  // limbs measured no faster than the compiler's 64-bit multiply)
   static __device__ __forceinline__ uint64_t mul_add(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t lo = a * b;
     uint64_t hi = __umul64hi(a, b);
