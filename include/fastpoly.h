@@ -140,13 +140,25 @@ int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, 
  * inside blocks) and satisfy the same error bounds. */
 typedef struct {
   int kernel;
-  int reserved[3];
+  int points_per_thread;  /* 0: automatic; 1, 2 or 4 (FP64 and IV64: 1 or 2) */
+  int reserved[2];
 } fp_launch_cfg;
 
 /* fp_eval_ex -- fp_eval with an explicit launch configuration (cfg may be
- * NULL: automatic). */
+ * NULL: automatic).  Points per thread change the launch shape only: results
+ * are identical for every count. */
 int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out,
                void* stream, const fp_launch_cfg* cfg);
+
+/* fp_tune -- the autotuner: times every launch configuration (kernel x points
+ * per thread) on the caller's points (three runs each after a warm-up),
+ * stores the fastest in the tree for this value type -- fp_eval then uses it
+ * -- and in a process-wide cache keyed by (value type, variables, scheme,
+ * log2 node count, log2 point count) that fp_eval consults for untuned trees
+ * of the same shape.  Leaves the tuned result in `out`; synchronises
+ * `stream`; writes the choice to *best when non-NULL. */
+int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
+            fp_launch_cfg* best);
 
 /* fp_eval_host -- the same as fp_eval with host buffers: copies the points to
  * the device, evaluates, copies the result back and synchronises `stream`.

@@ -29,6 +29,7 @@ for _name, _args in {
     "fp_eval": [_P, _I, _P, _I64, _P, _P],
     "fp_eval_host": [_P, _I, _P, _I64, _P, _P],
     "fp_eval_ex": [_P, _I, _P, _I64, _P, _P, _P],
+    "fp_tune": [_P, _I, _P, _I64, _P, _P, _P],
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
@@ -167,14 +168,15 @@ def fp_eval(tree, dtype, points, npts=None, out=None, stream=None):
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+    _fields_ = [("kernel", ctypes.c_int), ("points_per_thread", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 KERNELS = {"auto": 0, "ops": 1, "node": 2}
 
 
-def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=None):
-    """fp_eval with an explicit kernel choice ('auto', 'ops', 'node')."""
+def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=None, ppt=0):
+    """fp_eval with an explicit kernel choice ('auto', 'ops', 'node') and
+    points per thread (0: automatic)."""
     import torch
     if not points.is_cuda or not points.is_contiguous():
         raise ValueError("points must be a contiguous CUDA tensor")
@@ -182,10 +184,24 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
         npts = points.shape[-1]
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
-    cfg = LaunchCfg(KERNELS[kernel])
+    cfg = LaunchCfg(KERNELS[kernel], ppt)
     _check(_lib.fp_eval_ex(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
                            ctypes.byref(cfg)), "fp_eval_ex")
     return out
+
+
+def fp_tune(tree, dtype, points, out=None, stream=None):
+    """Autotune the launch configuration of this tree and value type on these
+    points (synchronous); returns (kernel name, points per thread)."""
+    import torch
+    npts = points.shape[-1]
+    if out is None:
+        out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    cfg = LaunchCfg()
+    _check(_lib.fp_tune(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
+                        ctypes.byref(cfg)), "fp_tune")
+    names = {v: k for k, v in KERNELS.items()}
+    return names[cfg.kernel], cfg.points_per_thread
 
 
 def fp_eval_host(tree, dtype, points, stream=None):

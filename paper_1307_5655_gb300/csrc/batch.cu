@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kTPB) eval_batch_kernel(const BatchJob* __rest
 }
 
 int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, EvalArgs& a, OpArgs& o);
+void lookup_tuned(const fp_tree* t, fp_dtype dt, int64_t npts, int& variant, int& ppt);
 
 namespace {
 
@@ -137,7 +138,11 @@ int batch_build(fp_dtype dt, const fp_job* jobs, int64_t njobs, fp_batch* b) {
     const size_t table = (vb * it.j.g.nslot + pb * it.j.g.npow) * ppt * kTPB;
     const size_t fly = (vb * it.j.g.nslot + pb * it.j.g.nvars) * ppt * kTPB;
     const bool fused = dt != FP_IV64;
-    if (fused && table <= kTableSmemCap && it.j.o.recs) {
+    // the kernel variant fp_eval would use for this job (tuned or default);
+    // points per thread do not change results, the variant can
+    int tv = 0, tp = 0;
+    lookup_tuned(in.tree, dt, in.npts, tv, tp);
+    if (fused && tv != 2 && table <= kTableSmemCap && it.j.o.recs) {
       it.j.mode = kModeOps;
       it.smem = table;
     } else if (table <= kTableSmemCap) {

@@ -1,5 +1,8 @@
 // C ABI of the library (declarations and contracts in include/fastpoly.h).
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -146,6 +149,41 @@ __global__ void plain_horner_kernel(const double* __restrict__ c, int64_t nc, co
 
 }  // namespace
 
+// ---- autotuner cache: (value type, variables, block scheme, log2 nodes,
+// log2 points) -> (kernel, points per thread), filled by fp_tune
+struct TuneKey {
+  int dt, nvars, scheme, lnodes, lpts;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dt, nvars, scheme, lnodes, lpts) < std::tie(o.dt, o.nvars, o.scheme, o.lnodes, o.lpts);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+int log2_bucket(int64_t v) {
+  int l = 0;
+  while ((int64_t)1 << (l + 1) <= v) ++l;
+  return l;
+}
+
+TuneKey tune_key(const fp_tree* t, fp_dtype dt, int64_t npts) {
+  return TuneKey{(int)dt, t->nvars, t->block_scheme, log2_bucket(t->nnodes), log2_bucket(npts)};
+}
+
+void lookup_tuned(const fp_tree* t, fp_dtype dt, int64_t npts, int& variant, int& ppt) {
+  if (t->tuned_kernel[dt] != 0) {
+    variant = t->tuned_kernel[dt];
+    ppt = t->tuned_ppt[dt];
+    return;
+  }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(tune_key(t, dt, npts));
+  if (it != g_tune.end()) {
+    variant = it->second.first;
+    ppt = it->second.second;
+  }
+}
+
 // Kernel arguments of one evaluation (shared by fp_eval and the batch path).
 int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, EvalArgs& a,
                    OpArgs& o) {
@@ -199,8 +237,9 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
 }
 
 int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st,
-                int variant = 0) {
+                int variant = 0, int ppt = 0) {
   if (variant < 0 || variant > 2) return FP_E_BAD_VALUE;
+  if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return FP_E_BAD_VALUE;
   if (!t) return FP_E_BAD_VALUE;
   if ((int)dt < FP_F64 || (int)dt > FP_MODP) return FP_E_DTYPE;
   if (!dtype_ok(t, dt)) return FP_E_DTYPE;
@@ -220,16 +259,21 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
   OpArgs o;
   const int frc = fill_eval_args(t, dt, points, npts, out, a, o);
   if (frc != FP_OK) return frc;
+  if (variant == 0 && ppt == 0) {  // a tuned configuration, from the tree or the shared cache
+    lookup_tuned(t, dt, npts, variant, ppt);
+  }
   const size_t vbytes = dt == FP_IV64 ? 16 : 8, pbytes = vbytes;
-  const int ppt = (dt == FP_F32C || dt == FP_MODP) ? 2 : 1;
+  if (ppt == 0) ppt = (dt == FP_F32C || dt == FP_MODP) ? 2 : 1;
+  if (dt == FP_F64 && ppt == 4) ppt = 2;
+  if (dt == FP_IV64 && ppt == 4) ppt = 2;
   const size_t smem = (vbytes * (size_t)a.nslot + pbytes * (size_t)a.nvars) * ppt * kTPB;
   if (smem > kSmemMax) return FP_E_TOO_LARGE;
   cudaError_t e = cudaSuccess;
   switch (dt) {
-    case FP_F64: e = launch_eval_f64(a, o, t->block_scheme, st, variant); break;
-    case FP_F32C: e = launch_eval_f32c(a, o, t->block_scheme, st, variant); break;
-    case FP_IV64: e = launch_eval_iv64(a, o, t->block_scheme, st, variant); break;
-    case FP_MODP: e = launch_eval_modp(a, o, t->block_scheme, st, variant); break;
+    case FP_F64: e = launch_eval_f64(a, o, t->block_scheme, st, variant, ppt); break;
+    case FP_F32C: e = launch_eval_f32c(a, o, t->block_scheme, st, variant, ppt); break;
+    case FP_IV64: e = launch_eval_iv64(a, o, t->block_scheme, st, variant, ppt); break;
+    case FP_MODP: e = launch_eval_modp(a, o, t->block_scheme, st, variant, ppt); break;
   }
   if (e == cudaErrorInvalidValue && variant == 1) { cudaGetLastError(); return FP_E_TOO_LARGE; }
   return e == cudaSuccess ? FP_OK : FP_E_CUDA;
@@ -298,7 +342,54 @@ int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, 
 
 int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
                const fp_launch_cfg* cfg) {
-  return eval_device(t, dtype, points, npts, out, (cudaStream_t)stream, cfg ? cfg->kernel : 0);
+  return eval_device(t, dtype, points, npts, out, (cudaStream_t)stream, cfg ? cfg->kernel : 0,
+                     cfg ? cfg->points_per_thread : 0);
+}
+
+int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
+            fp_launch_cfg* best) {
+  if (!t || npts <= 0 || !points || !out) return FP_E_BAD_VALUE;
+  if (!dtype_ok(t, dtype)) return FP_E_DTYPE;
+  if (t->nnodes == 0) return FP_E_BAD_VALUE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kernels[2] = {1, 2};
+  const int ppts[3] = {1, 2, 4};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { cudaGetLastError(); return FP_E_CUDA; }
+  float best_ms = 1e30f;
+  int bk = 0, bp = 0;
+  for (int k : kernels) {
+    if (k == 1 && dtype == FP_IV64) continue;
+    for (int p : ppts) {
+      if ((dtype == FP_F64 || dtype == FP_IV64) && p == 4) continue;
+      // warm-up run (also rejects configurations that do not fit)
+      if (eval_device(t, dtype, points, npts, out, st, k, p) != FP_OK) { cudaGetLastError(); continue; }
+      cudaEventRecord(e0, st);
+      int rc = FP_OK;
+      for (int r = 0; r < 3 && rc == FP_OK; ++r) rc = eval_device(t, dtype, points, npts, out, st, k, p);
+      cudaEventRecord(e1, st);
+      if (rc != FP_OK || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; bk = k; bp = p; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bk == 0) return FP_E_CUDA;
+  t->tuned_kernel[dtype] = bk;
+  t->tuned_ppt[dtype] = bp;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[tune_key(t, dtype, npts)] = {bk, bp};
+  }
+  // leave the tuned configuration's result in `out`
+  const int rc = eval_device(t, dtype, points, npts, out, st, bk, bp);
+  if (best) {
+    best->kernel = bk;
+    best->points_per_thread = bp;
+  }
+  return rc;
 }
 
 int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts, void* out_host,

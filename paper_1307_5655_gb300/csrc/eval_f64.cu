@@ -1,8 +1,13 @@
-// Instantiation of the evaluation kernels for the F64 value type.
+// Instantiation of the evaluation kernels for the F64 value type, for every
+// points-per-thread count the autotuner may choose (default 1).
 #include "eval_kernel.cuh"
 
 namespace fp {
-cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant) {
-  return launch_eval_fused<F64, 1, 1>(a, o, scheme, s, variant);
+cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt) {
+  switch (ppt) {
+    case 1: return launch_eval_fused<F64, 1, 1>(a, o, scheme, s, variant);
+    case 2: return launch_eval_fused<F64, 2, 2>(a, o, scheme, s, variant);
+    default: return launch_eval_fused<F64, 1, 1>(a, o, scheme, s, variant);
+  }
 }
 }  // namespace fp

@@ -647,10 +647,10 @@ __global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const 
 // Launch helpers (defined per type in eval_<type>.cu).  variant: 0 = choose,
 // 1 = register kernel, 2 = shared-memory kernel.
 // variant 1 = grouped-op kernel (fused types only), 2 = node-by-node kernel.
-cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
-cudaError_t launch_eval_f32c(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
-cudaError_t launch_eval_iv64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
-cudaError_t launch_eval_modp(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant);
+cudaError_t launch_eval_f64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt);
+cudaError_t launch_eval_f32c(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt);
+cudaError_t launch_eval_iv64(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt);
+cudaError_t launch_eval_modp(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt);
 
 // Shared memory of one block; the power table is used while it leaves room
 // for at least two resident blocks per SM.

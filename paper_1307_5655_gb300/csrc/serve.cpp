@@ -29,7 +29,7 @@
 
 namespace fp {
 int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts, void* out, cudaStream_t st,
-                int variant);
+                int variant, int ppt);
 }
 
 namespace {
@@ -147,7 +147,7 @@ struct fp_server {
       if (r.in_bytes && cudaMemcpyAsync(r.d_in, r.in_host, r.in_bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
         status = FP_E_CUDA;
       if (r.tree->nnodes == 0) {  // the zero polynomial goes through fp_eval
-        if (fp::eval_device(r.tree, r.dtype, r.d_in, r.npts, r.d_out, s.stream, 0) != FP_OK) status = FP_E_CUDA;
+        if (fp::eval_device(r.tree, r.dtype, r.d_in, r.npts, r.d_out, s.stream, 0, 0) != FP_OK) status = FP_E_CUDA;
       } else {
         fp_job j;
         j.tree = r.tree;

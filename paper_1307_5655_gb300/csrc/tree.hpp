@@ -103,6 +103,10 @@ struct fp_tree {
   int pid_x1 = -1;                 // power slot of x_1
   int pid_pow[fp::kMaxBlock + 1] = {};  // power slot of x_1^d, d <= kMaxBlock (-1: absent)
 
+  // launch configuration chosen by fp_tune per value type (kernel, ppt; 0 = not tuned)
+  int tuned_kernel[4] = {0, 0, 0, 0};
+  int tuned_ppt[4] = {0, 0, 0, 0};
+
   fp::DeviceSchedule dev;
 };
 
