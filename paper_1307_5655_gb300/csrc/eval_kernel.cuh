@@ -225,27 +225,33 @@ struct IV64 {
   static __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
   static __device__ __forceinline__ int cls(const IV& a) { return ge0(a.lo) ? 0 : (le0(a.hi) ? 1 : 2); }
   // Moore's nine sign cases: each bound is the directed rounding of the exact
-  // extreme product.
+  // extreme product.  The operands of the two products are selected per lane
+  // (lanes hold points of different signs, so branching per case would run
+  // several cases' multiplies in every warp); only the case where both
+  // intervals straddle zero needs two more products, taken by a branch.
+  //   lower bound operands        upper bound operands
+  //   P x P  a.lo b.lo            a.hi b.hi
+  //   P x N  a.hi b.lo            a.lo b.hi
+  //   P x M  a.hi b.lo            a.hi b.hi
+  //   N x P  a.lo b.hi            a.hi b.lo
+  //   N x N  a.hi b.hi            a.lo b.lo
+  //   N x M  a.lo b.hi            a.lo b.lo
+  //   M x P  a.lo b.hi            a.hi b.hi
+  //   M x N  a.hi b.lo            a.lo b.lo
+  //   M x M  min(a.lo b.hi, a.hi b.lo)   max(a.lo b.lo, a.hi b.hi)
   static __device__ __forceinline__ IV mul(const IV& a, const IV& b) {
     const int ca = cls(a), cb = cls(b);
+    const bool la_hi = (ca == 0 && cb != 0) || (cb == 1 && ca != 0);
+    const bool lb_hi = ca == 1 || (ca == 2 && cb != 1);
+    const bool ha_lo = (ca == 0 && cb == 1) || (ca != 0 && cb != 0);
+    const bool hb_lo = ca == 1 || (ca == 2 && cb != 0);
     IV r;
-    if (ca == 0) {
-      if (cb == 0) { r.lo = __dmul_rd(a.lo, b.lo); r.hi = __dmul_ru(a.hi, b.hi); }
-      else if (cb == 1) { r.lo = __dmul_rd(a.hi, b.lo); r.hi = __dmul_ru(a.lo, b.hi); }
-      else { r.lo = __dmul_rd(a.hi, b.lo); r.hi = __dmul_ru(a.hi, b.hi); }
-    } else if (ca == 1) {
-      if (cb == 0) { r.lo = __dmul_rd(a.lo, b.hi); r.hi = __dmul_ru(a.hi, b.lo); }
-      else if (cb == 1) { r.lo = __dmul_rd(a.hi, b.hi); r.hi = __dmul_ru(a.lo, b.lo); }
-      else { r.lo = __dmul_rd(a.lo, b.hi); r.hi = __dmul_ru(a.lo, b.lo); }
-    } else {
-      if (cb == 0) { r.lo = __dmul_rd(a.lo, b.hi); r.hi = __dmul_ru(a.hi, b.hi); }
-      else if (cb == 1) { r.lo = __dmul_rd(a.hi, b.lo); r.hi = __dmul_ru(a.lo, b.lo); }
-      else {
-        const double l1 = __dmul_rd(a.lo, b.hi), l2 = __dmul_rd(a.hi, b.lo);
-        const double h1 = __dmul_ru(a.lo, b.lo), h2 = __dmul_ru(a.hi, b.hi);
-        r.lo = l1 < l2 ? l1 : l2;
-        r.hi = h1 > h2 ? h1 : h2;
-      }
+    r.lo = __dmul_rd(la_hi ? a.hi : a.lo, lb_hi ? b.hi : b.lo);
+    r.hi = __dmul_ru(ha_lo ? a.lo : a.hi, hb_lo ? b.lo : b.hi);
+    if (ca == 2 && cb == 2) {
+      const double l2 = __dmul_rd(a.hi, b.lo), h2 = __dmul_ru(a.hi, b.hi);
+      r.lo = r.lo < l2 ? r.lo : l2;
+      r.hi = r.hi > h2 ? r.hi : h2;
     }
     return r;
   }
@@ -257,15 +263,17 @@ struct IV64 {
     return r;
   }
   static __device__ __forceinline__ pw dummy_point() { IV r; r.lo = 0.5; r.hi = 0.5; return r; }
+  // tight square: non-negative [lo^2, hi^2]; non-positive [hi^2, lo^2];
+  // straddling [+0, max(lo^2, hi^2)] (selected per lane as in mul)
   static __device__ __forceinline__ pw square(pw a) {
     IV r;
     const int c = cls(a);
-    if (c == 0) { r.lo = __dmul_rd(a.lo, a.lo); r.hi = __dmul_ru(a.hi, a.hi); }
-    else if (c == 1) { r.lo = __dmul_rd(a.hi, a.hi); r.hi = __dmul_ru(a.lo, a.lo); }
-    else {
-      const double h1 = __dmul_ru(a.lo, a.lo), h2 = __dmul_ru(a.hi, a.hi);
+    r.lo = __dmul_rd(c == 1 ? a.hi : a.lo, c == 1 ? a.hi : a.lo);
+    r.hi = __dmul_ru(c == 1 ? a.lo : a.hi, c == 1 ? a.lo : a.hi);
+    if (c == 2) {
+      const double h1 = __dmul_ru(a.lo, a.lo);
       r.lo = 0.0;
-      r.hi = h1 > h2 ? h1 : h2;
+      r.hi = h1 > r.hi ? h1 : r.hi;
     }
     return r;
   }
