@@ -618,10 +618,40 @@ def run_staircase(args):
                       "results": res}))
 
 
+def run_hybrid(args):
+    """The paper's combined scheme (Remark of Sec. 1.1): Estrin above k0 terms,
+    Horner below, against H, E and B, FP64 and compensated FP32, k = 10007 at
+    2^24 points (each tree autotuned)."""
+    import math
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    k = 10007
+    x = W.points_f64(1, NPTS, points_seed(0))
+    d64 = torch.from_numpy(x).cuda()
+    d32 = torch.from_numpy(W.to_f32(x)).cuda()
+    e, c, _ = W.univariate_case(k, 1, SEED + k)
+    res = {}
+    variants = [("H", None), ("E", None), ("B", None)]
+    for k0 in (4, 8, 16, 32, 64, 128, 512):
+        ft = np.ones(k + 1, dtype=np.int32)
+        for n in range(1, k + 1):
+            ft[n] = 2 ** int(math.floor(math.log2(n))) if n + 1 > k0 else 1
+        variants.append(("hybrid_k0_%d" % k0, ft))
+    for name, ft in variants:
+        t = fpl.fp_compile(e, c, "CUSTOM" if ft is not None else name, ft)
+        for dt, d in (("f64", d64), ("f32c", d32)):
+            fpl.fp_tune(t, dt, d[:, : 1 << 20].contiguous())
+            ms = _timed(lambda: fpl.fp_eval(t, dt, d), 3, 1)
+            res["%s/%s" % (dt, name)] = {"ms": ms, "G_term_evals_per_s": k * NPTS / (ms * 1e6)}
+    print(json.dumps({"metric": "G term-evals/s", "workload": "k = 10007, 2^24 points", "results": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve", "accuracy",
-                                                                "staircase"],
+                                                                "staircase", "hybrid"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=1000)
@@ -651,6 +681,8 @@ def main():
         run_accuracy(args)
     elif args.workload == "staircase":
         run_staircase(args)
+    elif args.workload == "hybrid":
+        run_hybrid(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
