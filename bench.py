@@ -374,9 +374,10 @@ def run_profile_case(args):
         pts = torch.from_numpy(x).cuda()
         t = fpl.fp_compile(e, c, scheme)
     for _ in range(2):
-        fpl.fp_eval_ex(t, dt, pts, kernel=args.profile_kernel)
+        fpl.fp_eval_ex(t, dt, pts, kernel=args.profile_kernel, ppt=args.profile_ppt)
     torch.cuda.synchronize()
-    print("profile case done: k=%d scheme=%s dtype=%s kernel=%s points=%d" % (k, scheme, dt, args.profile_kernel, NPTS))
+    print("profile case done: k=%d scheme=%s dtype=%s kernel=%s ppt=%d points=%d"
+          % (k, scheme, dt, args.profile_kernel, args.profile_ppt, NPTS))
 
 
 def _timed(fn, steps, warmup):
@@ -662,6 +663,7 @@ def main():
     ap.add_argument("--profile-scheme", default="E")
     ap.add_argument("--profile-dtype", default="f64")
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "ops", "node"])
+    ap.add_argument("--profile-ppt", type=int, default=0, help="points per thread (0: automatic)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

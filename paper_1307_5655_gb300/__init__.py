@@ -32,6 +32,7 @@ for _name, _args in {
     "fp_tune": [_P, _I, _P, _I64, _P, _P, _P],
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
+    "fp_tree_schedule": [_P] * 12,
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
     "fp_compose_noalloc": [_P, _I, _P, _P, _I, _I64, _P, _P],
@@ -111,6 +112,25 @@ class Tree:
         _check(_lib.fp_tree_export(self._h, _ptr(e), _ptr(tn), _ptr(par), _ptr(pv), _ptr(pd), _ptr(lh)),
                "fp_tree_export")
         return {"node_e": e, "term_of_node": tn, "parent": par, "pd_var": pv, "pd": pd, "lh": lh}
+
+    def schedule(self):
+        """The grouped-op schedule of the fused-type kernels (fp_tree_schedule)."""
+        nops, nst, npw = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.fp_tree_schedule(self._h, ctypes.byref(nops), None, None, None, ctypes.byref(nst), None,
+                                     ctypes.byref(npw), None, None, None, None), "fp_tree_schedule")
+        words = np.zeros((nops.value, 4), dtype=np.uint32)
+        a = np.zeros(nops.value, dtype=np.int64)
+        b = np.zeros(nops.value, dtype=np.int64)
+        st = np.zeros(nst.value, dtype=np.int64)
+        pv = np.zeros(npw.value, dtype=np.int32)
+        pd = np.zeros(npw.value, dtype=np.int64)
+        bs = ctypes.c_int32()
+        root = np.zeros(3, dtype=np.int32)
+        _check(_lib.fp_tree_schedule(self._h, None, _ptr(words), _ptr(a), _ptr(b), None, _ptr(st), None, _ptr(pv),
+                                     _ptr(pd), ctypes.byref(bs), _ptr(root)), "fp_tree_schedule")
+        return {"op_words": words, "op_a_node": a, "op_b_node": b, "stream": st, "pow_var": pv, "pow_deg": pd,
+                "block_scheme": bs.value, "root_leaf": int(root[0]), "root_lh": int(root[1]),
+                "root_pid": int(root[2])}
 
 
 def _compile(fn, exps, coeffs, scheme, ftab, modp):

@@ -443,6 +443,35 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
   return FP_OK;
 }
 
+int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_t* op_a_node, int64_t* op_b_node,
+                     int64_t* stream_len, int64_t* stream, int32_t* npow, int32_t* pow_var, int64_t* pow_deg,
+                     int32_t* block_scheme, int32_t* root_info) {
+  if (!t) return FP_E_BAD_VALUE;
+  const size_t n = t->ops.size(), ns = t->stream.size(), np = t->pow_prog.size();
+  if (nops) *nops = (int64_t)n;
+  if (stream_len) *stream_len = (int64_t)ns;
+  if (npow) *npow = (int32_t)np;
+  if (op_words)
+    for (size_t i = 0; i < n; ++i) {
+      op_words[4 * i + 0] = t->ops[i].x;
+      op_words[4 * i + 1] = t->ops[i].y;
+      op_words[4 * i + 2] = t->ops[i].z;
+      op_words[4 * i + 3] = t->ops[i].w;
+    }
+  if (op_a_node && n) std::memcpy(op_a_node, t->op_a_node.data(), n * sizeof(int64_t));
+  if (op_b_node && n) std::memcpy(op_b_node, t->op_b_node.data(), n * sizeof(int64_t));
+  if (stream && ns) std::memcpy(stream, t->stream.data(), ns * sizeof(int64_t));
+  if (pow_var && np) std::memcpy(pow_var, t->pow_var.data(), np * sizeof(int32_t));
+  if (pow_deg && np) std::memcpy(pow_deg, t->pow_deg.data(), np * sizeof(int64_t));
+  if (block_scheme) *block_scheme = t->block_scheme;
+  if (root_info) {
+    root_info[0] = t->root_leaf;
+    root_info[1] = t->root_lh;
+    root_info[2] = t->root_pid;
+  }
+  return FP_OK;
+}
+
 int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
                void* out, void* stream) {
   int dev = -1;

@@ -253,8 +253,14 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
   // a5': group the walk into ops (fused value types).  A block is a maximal
   // subtree of at most kMaxBlock nodes over consecutive exponents of a
   // univariate polynomial under E or B: its shape is the scheme's own split
-  // applied to a dense run, so a compile-time template evaluates it.  A chain
-  // is a run j0..j1 where each node is the only child of the next.
+  // applied to a dense run, so a compile-time template evaluates it.  A
+  // partial block is, for a node N with a larger subtree, N together with its
+  // last children when these form a dense run of at most kMaxBlock nodes: by
+  // the recursion of Def. 1.2 (p = a x^f + b, b split again by the same rule)
+  // that run is the lower part b of one of the splits of N's run, so the same
+  // templates evaluate it, with N's slot (c_N plus N's earlier, larger
+  // children) in place of c_N.  A chain is a run j0..j1 where each node is the
+  // only child of the next.
   {
     std::vector<int64_t> size(N, 1), nchild(N, 0);
     for (int64_t i = 0; i + 1 < N; ++i) {
@@ -263,11 +269,27 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     }
     const bool blocks = nvars == 1 && (scheme == FP_SCHEME_E || scheme == FP_SCHEME_B);
     t->block_scheme = blocks ? (int)scheme : 0;
-    std::vector<int64_t> block_len(N, 0);  // at the block's first node
+    std::vector<int64_t> block_len(N, 0);    // at the block's first node
+    std::vector<int64_t> partial_len(N, 0);  // at the partial block's first node
+    std::vector<uint8_t> in_partial(N, 0);   // node lies inside a partial block
     if (blocks) {
+      for (int64_t r = 0; r + 1 < N; ++r) {  // partial blocks (the root keeps its own path)
+        if (size[r] <= kMaxBlock) continue;
+        int64_t s = 1, pos = r - 1;
+        while (pos >= 0 && t->parent[pos] == r && s + size[pos] <= kMaxBlock) {
+          s += size[pos];
+          pos -= size[pos];
+        }
+        if (s < 2) continue;
+        const int64_t j0 = r - s + 1;
+        if (t->node_e[j0] - t->node_e[r] != s - 1) continue;  // not a dense run
+        if (j0 >= (1ll << 32)) continue;
+        partial_len[j0] = s;
+        for (int64_t j = j0; j <= r; ++j) in_partial[j] = 1;
+      }
       for (int64_t r = 0; r + 1 < N; ++r) {
         const int64_t s = size[r], q = t->parent[r];
-        if (s < 2 || s > kMaxBlock) continue;
+        if (s < 2 || s > kMaxBlock || in_partial[r]) continue;
         if (q != N - 1 && size[q] <= kMaxBlock) continue;  // not maximal
         const int64_t j0 = r - s + 1;
         if (t->node_e[j0] - t->node_e[r] != s - 1) continue;  // not a dense run
@@ -278,9 +300,11 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     auto pid_of = [&](int64_t i) { return (uint32_t)pid.at({t->pd_var[i], t->pd[i]}); };
     auto emit = [&](uint32_t kind, int64_t j0, int64_t j1) {
       const int64_t q = t->parent[j1];
-      const uint32_t leaf = has_child[j0] ? 0u : 1u;
-      uint32_t x = kind | (leaf ? 0u : (uint32_t)t->lh[j0]) << kOpS | (uint32_t)t->lh[q] << kOpD |
-                   leaf << kOpLeaf | (uint32_t)is_first[j1] << kOpFirst | pid_of(j1) << kOpPid;
+      // S: the slot an op starts from (a partial block adds its last node's slot)
+      const uint32_t leaf = (kind != kOpPartial && !has_child[j0]) ? 1u : 0u;
+      const uint32_t S = kind == kOpPartial ? (uint32_t)t->lh[j1] : leaf ? 0u : (uint32_t)t->lh[j0];
+      uint32_t x = kind | S << kOpS | (uint32_t)t->lh[q] << kOpD | leaf << kOpLeaf |
+                   (uint32_t)is_first[j1] << kOpFirst | pid_of(j1) << kOpPid;
       if (kind == kOpChain) {
         bool uni = true;
         for (int64_t j = j0; j < j1; ++j) uni = uni && pid_of(j) == pid_of(j0);
@@ -306,6 +330,12 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     t->op_b_node.clear();
     t->stream.clear();
     for (int64_t i = 0; i + 1 < N;) {
+      if (partial_len[i] > 0) {  // N = i + len - 1 is not a leaf: S is its slot
+        const int64_t r = i + partial_len[i] - 1;
+        emit(kOpPartial, i, r);
+        i = r + 1;
+        continue;
+      }
       if (block_len[i] > 0) {
         emit(kOpBlock, i, i + block_len[i] - 1);
         i += block_len[i];

@@ -76,7 +76,9 @@ struct F64 {
     *dst = fma(s, xd, init);
   }
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
+  static constexpr bool kSlotAtEnd = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
+  static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return __dmul_rn(r, xd); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((double*)out)[idx] = r; }
@@ -127,6 +129,13 @@ struct F32C {
     lo = __fmaf_rn(s.y, xd.x, lo);
     lo = __fmaf_rn(s.x, xd.y, lo);
     return make_float2(h, lo);
+  }
+  static constexpr bool kSlotAtEnd = true;
+  // a + b with the rounding error of the leading sum (TwoSum) kept in lo
+  static __device__ __forceinline__ val add(val a, val b) {
+    float h, e;
+    two_sum(a.x, b.x, h, e);
+    return make_float2(h, __fadd_rn(__fadd_rn(a.y, b.y), e));
   }
   static __device__ __forceinline__ val from_coef(coef c) { return make_float2(c, 0.0f); }
   static __device__ __forceinline__ void node(bool leaf, bool first, coef ca, coef cb, const val* src, val* dst, pw xd) {
@@ -190,7 +199,15 @@ struct MODP {
     *dst = mul_add(s, xd, init);
   }
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
+  static constexpr bool kSlotAtEnd = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
+  // a + b for residues a, b < p (2^64 == 2^32 - 1 on a carry)
+  static __device__ __forceinline__ val add(val a, val b) {
+    uint64_t r = a + b;
+    if (r < a) r += 0xFFFFFFFFull;
+    if (r >= P) r -= P;
+    return r;
+  }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return mul_add(r, xd, 0); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((uint64_t*)out)[idx] = r; }
@@ -465,16 +482,21 @@ __host__ __device__ constexpr bool block_uses_power(int d) {
 // value of the tree T_f over the dense run c[LO..HI] (index order: c[LO] is
 // the highest term), relative to the exponent of c[HI]:
 //   T(run) = T(b) + T(a) x^f(n),  b = the f(n) lowest terms (Def. 1.2)
-template <class A, int SCHEME, int LO, int HI>
+// BASE: the run ends at the block's last node, whose value is `base` (its
+// coefficient for a block; its slot, which holds c_N plus N's earlier
+// children, for a partial block)
+template <class A, int SCHEME, int LO, int HI, bool BASE>
 __device__ __forceinline__ typename A::val block_eval(const typename A::coef (&c)[kMaxBlock],
-                                                      const typename A::pw (&xp)[kMaxBlock + 1]) {
+                                                      const typename A::pw (&xp)[kMaxBlock + 1],
+                                                      const typename A::val& base) {
   if constexpr (LO == HI) {
-    return A::from_coef(c[HI]);
+    if constexpr (BASE) return base;
+    else return A::from_coef(c[HI]);
   } else {
     constexpr int n = HI - LO;
     constexpr int f = scheme_split<SCHEME>(n);
-    const typename A::val b = block_eval<A, SCHEME, HI - f + 1, HI>(c, xp);
-    const typename A::val a = block_eval<A, SCHEME, LO, HI - f>(c, xp);
+    const typename A::val b = block_eval<A, SCHEME, HI - f + 1, HI, BASE>(c, xp, base);
+    const typename A::val a = block_eval<A, SCHEME, LO, HI - f, false>(c, xp, base);
     return A::mad(a, xp[f], b);
   }
 }
@@ -491,13 +513,26 @@ __host__ __device__ constexpr bool block_needs_power(int d) {
   return false;
 }
 
+// The value of the block's last node N is its coefficient; for a partial
+// block it is N's slot (slot[p]).  Types with A::kSlotAtEnd evaluate the run
+// with 0 for N and add the slot afterwards (the slot's load then overlaps the
+// block's arithmetic; one add more), the others start from the slot.
 template <class A, int SCHEME, int PPT>
-__device__ __forceinline__ void block_dispatch(int len, const typename A::coef (&c)[kMaxBlock],
+__device__ __forceinline__ void block_dispatch(int len, bool partial, const typename A::coef (&c)[kMaxBlock],
                                                const typename A::pw (&xp)[PPT][kMaxBlock + 1],
-                                               typename A::val (&v)[PPT]) {
-#define FP_BLOCK_CASE(L)                                                          \
-  case L:                                                                         \
-    _Pragma("unroll") for (int p = 0; p < PPT; ++p) v[p] = block_eval<A, SCHEME, 0, L - 1>(c, xp[p]); \
+                                               const typename A::val (&slot)[PPT], typename A::val (&v)[PPT]) {
+#define FP_BLOCK_CASE(L)                                                                      \
+  case L:                                                                                     \
+    _Pragma("unroll") for (int p = 0; p < PPT; ++p) {                                         \
+      if constexpr (A::kSlotAtEnd) {                                                          \
+        const typename A::val base = A::from_coef(partial ? typename A::coef(0) : c[L - 1]);  \
+        v[p] = block_eval<A, SCHEME, 0, L - 1, true>(c, xp[p], base);                         \
+        if (partial) v[p] = A::add(v[p], slot[p]);                                            \
+      } else {                                                                                \
+        const typename A::val base = partial ? slot[p] : A::from_coef(c[L - 1]);              \
+        v[p] = block_eval<A, SCHEME, 0, L - 1, true>(c, xp[p], base);                         \
+      }                                                                                       \
+    }                                                                                         \
     break;
   switch (len) {
     FP_BLOCK_CASE(2) FP_BLOCK_CASE(3) FP_BLOCK_CASE(4) FP_BLOCK_CASE(5) FP_BLOCK_CASE(6)
@@ -624,7 +659,15 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
 #pragma unroll
           for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];
         }
-        block_dispatch<A, SCHEME, PPT>(len, c, xp, v);
+        // a partial block's last node N starts from its slot (c_N plus N's
+        // earlier children)
+        const bool partial = kind == kOpPartial;
+        V slot[PPT];
+        if (partial) {
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) slot[p] = acc[(S * PPT + p) * kTPB + tid];
+        }
+        block_dispatch<A, SCHEME, PPT>(len, partial, c, xp, slot, v);
       }
     }
     // the outgoing edge of the op's last node

@@ -31,7 +31,12 @@ constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 // record (32 bytes, read with two 128-bit loads) per op:
 //   x: bits 0..1 kind  (0: one node; 1: chain j0..j0+len-1, each node the only
 //                       child of the next; 2: dense subtree block of len nodes
-//                       evaluated by the scheme's own splits in registers)
+//                       evaluated by the scheme's own splits in registers;
+//                       3: partial block -- the last node N of the run and its
+//                       last children, which together are the lower part b of
+//                       a split p = a x^f + b of N's own run (Def. 1.2): b is
+//                       evaluated like a block, with N's slot S (c_N plus
+//                       N's earlier, larger children) as the value of N)
 //      bits 2..7 S, 8..13 D, 14 LEAF (first node of the op is a leaf),
 //      15 FIRST (last node is its parent's first child), 16 UNIFORM (all
 //      powers inside a chain are the same), 17..31 PID of the outgoing edge
@@ -39,7 +44,7 @@ constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 //   a: leaf coefficient of a single-node op   b: parent coefficient if FIRST
 // The coefficients of chains and blocks are stored per op in a stream, each
 // op's run starting at a multiple of 4 elements (aligned vector loads).
-constexpr uint32_t kOpNode = 0, kOpChain = 1, kOpBlock = 2;
+constexpr uint32_t kOpNode = 0, kOpChain = 1, kOpBlock = 2, kOpPartial = 3;
 constexpr uint32_t kOpS = 2, kOpD = 8, kOpLeaf = 14, kOpFirst = 15, kOpUniform = 16, kOpPid = 17;
 constexpr int kMaxChain = 64, kMaxBlock = 16, kStreamAlign = 4;
 

@@ -1,0 +1,153 @@
+"""Host-side replay of the grouped schedule (no GPU).
+
+The FP64 / FP32C / MODP kernels replay the walk of Sec. 2.1 grouped into ops
+(single nodes, chains, dense blocks, partial blocks).  This test exports that
+schedule through `fp_tree_schedule` and replays it in exact arithmetic modulo
+p = 2^64 - 2^32 + 1 with Python integers; the result must equal the plain
+definition sum c x^e mod p of the oracle at every point.  A wrong slot, a
+wrong power, a dropped or doubled coefficient (e.g. c_N counted both by a
+partial block and by the first child's initial value) changes the value.
+The block templates are replayed from Def. 1.2 directly: the value of a
+dense run is T(b) + T(a) x^f with b its f lowest terms."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+import paper_1307_5655_gb300 as fpl
+
+P = (1 << 64) - (1 << 32) + 1
+
+
+def _split(scheme, n):
+    if scheme == 2:  # Estrin: the largest power of two <= n
+        return 1 << (n.bit_length() - 1)
+    return (n + 1) // 2  # Balanced: ceil(n / 2)
+
+
+def _run_value(scheme, c, xpow):
+    """T_f over the dense run c[0..len-1] (c[0] the highest term), relative to
+    the exponent of its last (lowest) term."""
+    def rec(lo, hi):
+        if lo == hi:
+            return c[hi]
+        f = _split(scheme, hi - lo)
+        b = rec(hi - f + 1, hi)
+        a = rec(lo, hi - f)
+        return (a * xpow(f) + b) % P
+    return rec(0, len(c) - 1)
+
+
+def _replay(t, coeffs, x, counts=None):
+    ex = t.export()
+    sc = t.schedule()
+    n = len(ex["parent"])
+    node_c = [int(coeffs[k]) if k >= 0 else 0 for k in ex["term_of_node"]]
+    pv, pdg = sc["pow_var"], sc["pow_deg"]
+    pw = [pow(int(x[int(pv[k])]), int(pdg[k]), P) for k in range(len(pv))]
+    x1 = int(x[0])
+
+    def xpow(d):
+        return pow(x1, d, P)
+
+    acc = {}
+    for rec_, a_node, b_node in zip(sc["op_words"], sc["op_a_node"], sc["op_b_node"]):
+        w0, ln, j0, off = (int(v) for v in rec_)
+        kind, S, D = w0 & 3, (w0 >> 2) & 63, (w0 >> 8) & 63
+        leaf, first, uniform, pid = (w0 >> 14) & 1, (w0 >> 15) & 1, (w0 >> 16) & 1, w0 >> 17
+        ln += 1
+        j1 = j0 + ln - 1
+        if counts is not None:
+            counts[kind] += 1
+        # the op's outgoing edge is the edge of its last node
+        assert int(pdg[pid]) == int(ex["pd"][j1]) and int(pv[pid]) == int(ex["pd_var"][j1])
+        if kind == 0:
+            assert ln == 1
+            v = node_c[a_node] if leaf else acc[S]
+            if leaf:
+                assert a_node == j0
+        else:
+            st = [int(s) for s in sc["stream"][off:off + ln]]
+            assert st == list(range(j0, j1 + 1)) and off % 4 == 0
+            cs = [node_c[j] for j in st]
+            if kind == 1:
+                v = cs[0] if leaf else acc[S]
+                pids = set()
+                for i in range(1, ln):
+                    j = j0 + i - 1
+                    assert int(ex["parent"][j]) == j + 1
+                    pids.add((int(ex["pd_var"][j]), int(ex["pd"][j])))
+                    v = (v * pow(int(x[int(ex["pd_var"][j])]), int(ex["pd"][j]), P) + cs[i]) % P
+                if uniform:
+                    assert len(pids) == 1
+            else:
+                assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 16
+                exps = ex["node_e"][j0:j1 + 1, 0]
+                assert np.array_equal(exps, np.arange(exps[0], exps[0] - ln, -1))
+                if kind == 3:  # N's slot (c_N and its earlier children) stands for c_N
+                    cs = cs[:-1] + [acc[S]]
+                v = _run_value(sc["block_scheme"], cs, xpow)
+        q = int(ex["parent"][j1])
+        if first:
+            init = node_c[b_node] if b_node >= 0 else 0
+            if b_node >= 0:
+                assert b_node == q
+        else:
+            init = acc[D]
+        acc[D] = (v * pw[pid] + init) % P
+    root = n - 1
+    r = node_c[root] if sc["root_leaf"] else acc[sc["root_lh"]]
+    if sc["root_pid"] >= 0:
+        r = r * pw[sc["root_pid"]] % P
+    return r
+
+
+def _check(exps, coeffs, scheme, ftab=None, npts=3, seed=0, counts=None):
+    t = fpl.fp_compile_host(exps, coeffs, scheme, ftab, modp=True)
+    nvars = 1 if np.ndim(exps) == 1 else np.shape(exps)[1]
+    x = W.points_modp(nvars, npts, seed + 77)
+    ref = O.eval_modp(exps, coeffs, x)
+    for p in range(npts):
+        got = _replay(t, coeffs, [int(v) for v in x[:, p]], counts)
+        assert got == int(ref[p]), (scheme, p)
+    t.free()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 17, 18, 33, 100, 513, 1000, 3000])
+@pytest.mark.parametrize("scheme", ["H", "E", "B", "D"])
+def test_univariate_schedule_replays_to_the_polynomial(k, scheme):
+    e, c, _ = W.univariate_case(k, 1, 1000 + k, "modp")
+    _check(e, c, scheme, npts=2, seed=k)
+
+
+def test_large_univariate_schedules_use_partial_blocks():
+    # 10007 terms: every node above the blocks carries a partial block
+    for scheme in ("E", "B"):
+        counts = [0, 0, 0, 0]
+        e, c, _ = W.univariate_case(10007, 1, 4242, "modp")
+        _check(e, c, scheme, npts=1, counts=counts)
+        assert counts[3] > 0 and counts[2] > 0
+        # a partial block absorbs the small children: far fewer ops than nodes
+        assert sum(counts) * 6 < 10007, counts
+
+
+def test_sparse_and_hybrid_schedules():
+    r = W.rng(5)
+    e = np.sort(r.choice(5000, size=700, replace=False))[::-1].astype(np.int32)
+    c = W.residues(700, 6)
+    for scheme in ("E", "B", "H"):
+        _check(e, c, scheme, npts=2, seed=1)
+    ft = np.zeros(1001, dtype=np.int32)
+    for n in range(1, 1001):
+        ft[n] = 2 ** int(math.floor(math.log2(n))) if n > 10 else 1
+    e2, c2, _ = W.univariate_case(1000, 1, 9, "modp")
+    _check(e2, c2, "CUSTOM", ft, npts=2, seed=2)
+
+
+@pytest.mark.parametrize("scheme", ["E", "B"])
+def test_multivariate_schedule(scheme):
+    e = W.total_degree_exps(3, 8)
+    c = W.residues(len(e), 11)
+    _check(e, c, scheme, npts=2, seed=3)
