@@ -181,32 +181,40 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
                    int32_t* pd_var, int64_t* pd, int32_t* lazy_height);
 
 /* fp_tree_schedule -- the grouped schedule that the FP64, FP32C and MODP
- * kernels replay: the walk of Sec. 2.1 in node index order, grouped into ops
- * (no counterpart in the paper; for inspection and host-side checks).  Every
- * op ends with the multiply-add of its last node into its parent's slot.
- *   *nops, *stream_len, *npow: sizes (always written when non-NULL; call once
- *       with the arrays NULL to size them).
+ * kernels replay: the walk of Sec. 2.1 in node index order, grouped into ops,
+ * with the per-point table those kernels use (no counterpart in the paper;
+ * for inspection and host-side checks).  Every op ends with the multiply-add
+ * of its last node into its parent's slot.
+ *   *nops, *stream_len, *nprog: sizes (always written when non-NULL; call
+ *       once with the arrays NULL to size them).
  *   op_words [nops][4] uint32: word 0 = kind (bits 0..1: 0 one node, 1 chain
  *       of single-child nodes, 2 dense subtree block evaluated by the scheme's
  *       own splits, 3 partial block = a node N and its last children forming
  *       the lower part b of a split of N's run, evaluated with N's slot as
- *       N's value) | S (the slot
- *       read, bits 2..7) | D (the parent's slot, 8..13) | LEAF (14) | FIRST
- *       (15: the last node is its parent's first child) | UNIFORM (16: one
- *       power along a chain) | PID (17..31: power of the outgoing edge);
- *       word 1 = length - 1; word 2 = first node; word 3 = stream offset.
+ *       N's value) | S (the slot read, bits 2..7) | D (the parent's slot,
+ *       8..13) | LEAF (14) | FIRST (15: the last node is its parent's first
+ *       child) | UNIFORM (16: one power along a chain) | PID (17..31: table
+ *       position of the outgoing edge's power); word 1 = length - 1;
+ *       word 2 = first node; word 3 = stream offset.
  *   op_a_node, op_b_node [nops]: node whose coefficient is the op's leaf value
  *       (single-node ops) / initialises the parent's slot when FIRST; -1 = 0.
  *   stream [stream_len]: node whose coefficient sits in each slot of the
  *       coefficient stream of chains and blocks, -1 for padding.
- *   pow_var, pow_deg [npow]: power table entry k is x_{pow_var[k]}^pow_deg[k].
- *   block_scheme: FP_SCHEME_E or FP_SCHEME_B when blocks are used, else 0.
- *   root_info[3]: root is a leaf, root slot, power id applied to the root
- *       value (-1: none).
+ *   prog [nprog][2]: the power program per point, {op | A1 << 2 | A2 << 17,
+ *       destination position}; op 0 loads variable A1, 1 squares position
+ *       A1, 2 multiplies positions A1 and A2.
+ *   chain_pid [nnodes - 1]: table position of each node's edge power (read
+ *       inside chains).
+ *   block_pow [17]: table position of x_1^d read by the block templates
+ *       after the program (-1: absent).
+ *   layout [7]: nlive (the walk's powers sit at positions [0, nlive)),
+ *       nslot (slot s sits at position nlive + s), table entries per point,
+ *       block scheme (FP_SCHEME_E / FP_SCHEME_B when blocks are used, else 0),
+ *       root is a leaf, root slot, position of the root's power (-1: none).
  * Any array pointer may be NULL.  FP_E_BAD_VALUE for a NULL tree. */
 int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_t* op_a_node,
-                     int64_t* op_b_node, int64_t* stream_len, int64_t* stream, int32_t* npow,
-                     int32_t* pow_var, int64_t* pow_deg, int32_t* block_scheme, int32_t* root_info);
+                     int64_t* op_b_node, int64_t* stream_len, int64_t* stream, int32_t* nprog,
+                     uint32_t* prog, uint32_t* chain_pid, int32_t* block_pow, int32_t* layout);
 
 /*
  * Batched evaluation: many jobs (trees of uneven size, each with its own

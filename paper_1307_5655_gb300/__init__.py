@@ -115,22 +115,24 @@ class Tree:
 
     def schedule(self):
         """The grouped-op schedule of the fused-type kernels (fp_tree_schedule)."""
-        nops, nst, npw = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        nops, nst, nprog = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         _check(_lib.fp_tree_schedule(self._h, ctypes.byref(nops), None, None, None, ctypes.byref(nst), None,
-                                     ctypes.byref(npw), None, None, None, None), "fp_tree_schedule")
+                                     ctypes.byref(nprog), None, None, None, None), "fp_tree_schedule")
+        n = self.info()["nnodes"]
         words = np.zeros((nops.value, 4), dtype=np.uint32)
         a = np.zeros(nops.value, dtype=np.int64)
         b = np.zeros(nops.value, dtype=np.int64)
         st = np.zeros(nst.value, dtype=np.int64)
-        pv = np.zeros(npw.value, dtype=np.int32)
-        pd = np.zeros(npw.value, dtype=np.int64)
-        bs = ctypes.c_int32()
-        root = np.zeros(3, dtype=np.int32)
-        _check(_lib.fp_tree_schedule(self._h, None, _ptr(words), _ptr(a), _ptr(b), None, _ptr(st), None, _ptr(pv),
-                                     _ptr(pd), ctypes.byref(bs), _ptr(root)), "fp_tree_schedule")
-        return {"op_words": words, "op_a_node": a, "op_b_node": b, "stream": st, "pow_var": pv, "pow_deg": pd,
-                "block_scheme": bs.value, "root_leaf": int(root[0]), "root_lh": int(root[1]),
-                "root_pid": int(root[2])}
+        prog = np.zeros((nprog.value, 2), dtype=np.uint32)
+        cp = np.zeros(max(n - 1, 0), dtype=np.uint32)
+        bp = np.zeros(17, dtype=np.int32)
+        lay = np.zeros(7, dtype=np.int32)
+        _check(_lib.fp_tree_schedule(self._h, None, _ptr(words), _ptr(a), _ptr(b), None, _ptr(st), None, _ptr(prog),
+                                     _ptr(cp), _ptr(bp), _ptr(lay)), "fp_tree_schedule")
+        return {"op_words": words, "op_a_node": a, "op_b_node": b, "stream": st, "prog": prog, "chain_pid": cp,
+                "block_pow": bp, "nlive": int(lay[0]), "nslot": int(lay[1]), "entries": int(lay[2]),
+                "block_scheme": int(lay[3]), "root_leaf": int(lay[4]), "root_lh": int(lay[5]),
+                "root_pid": int(lay[6])}
 
 
 def _compile(fn, exps, coeffs, scheme, ftab, modp):

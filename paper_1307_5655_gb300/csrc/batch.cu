@@ -137,14 +137,15 @@ int batch_build(fp_dtype dt, const fp_job* jobs, int64_t njobs, fp_batch* b) {
     if (rc != FP_OK) return rc;
     const size_t table = (vb * it.j.g.nslot + pb * it.j.g.npow) * ppt * kTPB;
     const size_t fly = (vb * it.j.g.nslot + pb * it.j.g.nvars) * ppt * kTPB;
+    const size_t ops_table = vb * (size_t)it.j.o.entries * ppt * kTPB;
     const bool fused = dt != FP_IV64;
     // the kernel variant fp_eval would use for this job (tuned or default);
     // points per thread do not change results, the variant can
     int tv = 0, tp = 0;
     lookup_tuned(in.tree, dt, in.npts, tv, tp);
-    if (fused && tv != 2 && table <= kTableSmemCap && it.j.o.recs) {
+    if (fused && tv != 2 && ops_table <= kTableSmemCap && it.j.o.recs) {
       it.j.mode = kModeOps;
-      it.smem = table;
+      it.smem = ops_table;
     } else if (table <= kTableSmemCap) {
       it.j.mode = kModeNodeTable;
       it.smem = table;

@@ -25,7 +25,7 @@ int upload(const std::vector<T>& h, T** d) {
 void release(fp_tree* t) {
   DeviceSchedule& d = t->dev;
   void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64,
-                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64};
+                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64, d.ops_prog, d.ops_chain_pid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceSchedule{};
@@ -54,6 +54,8 @@ int upload_schedule(fp_tree* t) {
   const int64_t N = t->nnodes, S = N - 1;
   int rc = upload(t->ctrl, &d.ctrl);
   if (rc == FP_OK) rc = upload(t->pow_prog, &d.pow_prog);
+  if (rc == FP_OK) rc = upload(t->ops_prog, &d.ops_prog);
+  if (rc == FP_OK) rc = upload(t->ops_chain_pid, &d.ops_chain_pid);
   if (rc != FP_OK) return rc;
   std::vector<uint2> dv(t->pow_prog.size());
   for (size_t k = 0; k < dv.size(); ++k) dv[k] = make_uint2((unsigned)t->pow_var[k], (unsigned)t->pow_deg[k]);
@@ -205,8 +207,15 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
   a.out = out;
   o = OpArgs{};
   o.nops = (int64_t)t->ops.size();
-  o.pid_x1 = t->pid_x1;
-  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->pid_pow[d];
+  o.prog = t->dev.ops_prog;
+  o.chain_pid = t->dev.ops_chain_pid;
+  o.nprog = (int)t->ops_prog.size();
+  o.nlive = t->ops_nlive;
+  o.nslot = t->ops_nslot;
+  o.entries = t->ops_entries;
+  o.root_lh = t->ops_root_lh;
+  o.root_pid = t->ops_root_pid;
+  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t root = t->nnodes - 1;
   switch (dt) {
     case FP_F64:
@@ -444,13 +453,14 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
 }
 
 int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_t* op_a_node, int64_t* op_b_node,
-                     int64_t* stream_len, int64_t* stream, int32_t* npow, int32_t* pow_var, int64_t* pow_deg,
-                     int32_t* block_scheme, int32_t* root_info) {
+                     int64_t* stream_len, int64_t* stream, int32_t* nprog, uint32_t* prog, uint32_t* chain_pid,
+                     int32_t* block_pow, int32_t* layout) {
   if (!t) return FP_E_BAD_VALUE;
-  const size_t n = t->ops.size(), ns = t->stream.size(), np = t->pow_prog.size();
+  const size_t n = t->ops.size(), ns = t->stream.size(), np = t->ops_prog.size();
+  const size_t nsteps = t->ops_chain_pid.size();
   if (nops) *nops = (int64_t)n;
   if (stream_len) *stream_len = (int64_t)ns;
-  if (npow) *npow = (int32_t)np;
+  if (nprog) *nprog = (int32_t)np;
   if (op_words)
     for (size_t i = 0; i < n; ++i) {
       op_words[4 * i + 0] = t->ops[i].x;
@@ -461,13 +471,22 @@ int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_
   if (op_a_node && n) std::memcpy(op_a_node, t->op_a_node.data(), n * sizeof(int64_t));
   if (op_b_node && n) std::memcpy(op_b_node, t->op_b_node.data(), n * sizeof(int64_t));
   if (stream && ns) std::memcpy(stream, t->stream.data(), ns * sizeof(int64_t));
-  if (pow_var && np) std::memcpy(pow_var, t->pow_var.data(), np * sizeof(int32_t));
-  if (pow_deg && np) std::memcpy(pow_deg, t->pow_deg.data(), np * sizeof(int64_t));
-  if (block_scheme) *block_scheme = t->block_scheme;
-  if (root_info) {
-    root_info[0] = t->root_leaf;
-    root_info[1] = t->root_lh;
-    root_info[2] = t->root_pid;
+  if (prog)
+    for (size_t k = 0; k < np; ++k) {
+      prog[2 * k] = t->ops_prog[k].x;
+      prog[2 * k + 1] = t->ops_prog[k].y;
+    }
+  if (chain_pid && nsteps) std::memcpy(chain_pid, t->ops_chain_pid.data(), nsteps * sizeof(uint32_t));
+  if (block_pow)
+    for (int d = 0; d <= kMaxBlock; ++d) block_pow[d] = t->ops_pid_pow[d];
+  if (layout) {
+    layout[0] = t->ops_nlive;
+    layout[1] = t->ops_nslot;
+    layout[2] = t->ops_entries;
+    layout[3] = t->block_scheme;
+    layout[4] = t->root_leaf;
+    layout[5] = t->ops_root_lh;
+    layout[6] = t->ops_root_pid;
   }
   return FP_OK;
 }

@@ -111,6 +111,140 @@ void emit_with_roots(const std::vector<int64_t>& order, int64_t lo, int64_t hi, 
   }
 }
 
+// a6: the grouped-op kernel's own per-point table (shared memory is what
+// bounds its occupancy).  The ops form a tree of their own: an op feeds the
+// slot of its last node's parent and reads at most one slot (its first node's
+// for a node or chain, its last node's for a partial block; none for a block
+// or a run starting at a leaf).  Only nodes that ops feed own a slot, and the
+// lazy-height rule of Def. 1.3 applied to that tree, with -1 for an op that
+// reads no slot, numbers the slots: lh(N) = max(lh(C1), 1 + max_{i>=2} lh(Ci)).
+// The table holds, at positions [0, nlive), the powers the walk reads (op
+// edges, chain edges, the root's) and above them the slots; the power
+// program writes explicit positions, so its temporaries and the powers only
+// the block templates use (read into registers before the walk) live above
+// nlive too, where the slots later reuse the space.
+int ops_layout(fp_tree* t) {
+  const int64_t N = t->nnodes;
+  const size_t nops = t->ops.size();
+  // op-tree lazy heights
+  std::vector<int32_t> first_h(N, -1), rest_h(N, -2), olh(N, 0);
+  std::vector<uint8_t> fed(N, 0), done(N, 0);
+  auto finalize = [&](int64_t r) {
+    if (!done[r]) {
+      olh[r] = fed[r] ? std::max({first_h[r], rest_h[r] + 1, 0}) : 0;
+      done[r] = 1;
+    }
+    return olh[r];
+  };
+  std::vector<int64_t> reads(nops, -1);
+  for (size_t i = 0; i < nops; ++i) {
+    const uint32_t x = t->ops[i].x, kind = x & 3u;
+    const int64_t j0 = t->ops[i].z, j1 = j0 + t->ops[i].y;
+    const bool leaf = (x >> kOpLeaf) & 1u;
+    if (kind == kOpPartial) reads[i] = j1;
+    else if (kind != kOpBlock && !leaf) reads[i] = j0;
+    const int32_t h = reads[i] >= 0 ? finalize(reads[i]) : -1;
+    const int64_t q = t->parent[j1];
+    if (!fed[q]) {
+      fed[q] = 1;
+      first_h[q] = h;
+    } else {
+      rest_h[q] = std::max(rest_h[q], h);
+    }
+  }
+  const int32_t root_h = t->root_leaf ? 0 : finalize(N - 1);
+  int32_t nslot = 1;
+  for (int64_t r = 0; r < N; ++r)
+    if (fed[r]) nslot = std::max(nslot, finalize(r) + 1);
+  if (nslot - 1 > FP_MAX_LAZY_HEIGHT) return FP_E_TOO_LARGE;  // 6-bit slot fields
+
+  // powers the walk reads, and the block templates' powers
+  const size_t np = t->pow_prog.size();
+  std::vector<uint8_t> live(np, 0), tmpl(np, 0), needed(np, 0);
+  for (size_t i = 0; i < nops; ++i) {
+    live[t->ops[i].x >> kOpPid] = 1;
+    if ((t->ops[i].x & 3u) == kOpChain)
+      for (int64_t j = t->ops[i].z; j < (int64_t)t->ops[i].z + t->ops[i].y; ++j) live[t->ctrl[j] >> kCtrlPid] = 1;
+  }
+  if (t->root_pid >= 0) live[t->root_pid] = 1;
+  if (t->block_scheme)
+    for (int d = 1; d <= kMaxBlock; ++d)
+      if (t->pid_pow[d] >= 0) tmpl[t->pid_pow[d]] = 1;
+  for (size_t k = 0; k < np; ++k) needed[k] = live[k] | tmpl[k];
+  for (size_t k = np; k-- > 0;) {  // operands of needed powers (program order is dependency order)
+    if (!needed[k]) continue;
+    const uint32_t w = t->pow_prog[k], op = w & 3u;
+    if (op == kPowSq || op == kPowMulX) needed[(w >> 2) & 0x7FFFu] = 1;
+    if (op == kPowMulX) needed[w >> 17] = 1;
+  }
+  std::vector<int32_t> pos(np, -1);
+  int32_t nlive = 0;
+  for (size_t k = 0; k < np; ++k)
+    if (live[k]) pos[k] = nlive++;
+  std::vector<int64_t> last_use(np, -1);
+  for (size_t k = 0; k < np; ++k) {
+    if (!needed[k]) continue;
+    const uint32_t w = t->pow_prog[k], op = w & 3u;
+    if (op == kPowSq || op == kPowMulX) last_use[(w >> 2) & 0x7FFFu] = (int64_t)k;
+    if (op == kPowMulX) last_use[w >> 17] = (int64_t)k;
+  }
+  std::vector<int32_t> free_pos;
+  int32_t top = nlive;  // one past the highest position written
+  t->ops_prog.clear();
+  for (size_t k = 0; k < np; ++k) {
+    if (!needed[k]) continue;
+    if (pos[k] < 0) {
+      if (!free_pos.empty()) {
+        pos[k] = free_pos.back();
+        free_pos.pop_back();
+      } else {
+        pos[k] = top++;
+      }
+    }
+    const uint32_t w = t->pow_prog[k], op = w & 3u;
+    uint32_t a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+    if (op == kPowSq || op == kPowMulX) a1 = (uint32_t)pos[a1];
+    if (op == kPowMulX) a2 = (uint32_t)pos[a2];
+    if (top > (int32_t)kMaxPowers) return FP_E_TOO_LARGE;
+    uint2 e;
+    e.x = op | a1 << 2 | a2 << 17;
+    e.y = (uint32_t)pos[k];
+    t->ops_prog.push_back(e);
+    // temporaries die after their last use (template powers stay until the walk)
+    for (uint32_t o : {(w >> 2) & 0x7FFFu, w >> 17}) {
+      if (op == kPowLoad || (o == (w >> 17) && op != kPowMulX)) continue;
+      if (!live[o] && !tmpl[o] && last_use[o] == (int64_t)k && pos[o] >= nlive) {
+        free_pos.push_back(pos[o]);
+        last_use[o] = -1;  // x^(2k+1) = x^(2k) x may name one operand twice
+      }
+    }
+  }
+  t->ops_nlive = nlive;
+  t->ops_nslot = nslot;
+  t->ops_entries = std::max(top, nlive + nslot);
+
+  // op records in this layout
+  for (size_t i = 0; i < nops; ++i) {
+    uint32_t x = t->ops[i].x;
+    const int64_t j1 = (int64_t)t->ops[i].z + t->ops[i].y;
+    const uint32_t S = reads[i] >= 0 ? (uint32_t)olh[reads[i]] : 0u;
+    const uint32_t D = (uint32_t)olh[t->parent[j1]];
+    const uint32_t P = (uint32_t)pos[x >> kOpPid];
+    x &= ~((63u << kOpS) | (63u << kOpD) | (0x7FFFu << kOpPid));
+    t->ops[i].x = x | S << kOpS | D << kOpD | P << kOpPid;
+  }
+  t->ops_chain_pid.assign(N > 0 ? N - 1 : 0, 0);
+  for (int64_t j = 0; j + 1 < N; ++j) {
+    const int32_t p = pos[t->ctrl[j] >> kCtrlPid];
+    t->ops_chain_pid[j] = p >= 0 ? (uint32_t)p : 0u;
+  }
+  t->ops_root_lh = root_h;
+  t->ops_root_pid = t->root_pid >= 0 ? pos[t->root_pid] : -1;
+  for (int d = 0; d <= kMaxBlock; ++d) t->ops_pid_pow[d] = t->pid_pow[d] >= 0 ? pos[t->pid_pow[d]] : -1;
+  return FP_OK;
+}
+
+
 }  // namespace
 
 int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
@@ -356,7 +490,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
   t->root_leaf = has_child[N - 1] ? 0 : 1;
   t->root_lh = t->lh[N - 1];
   t->root_pid = t->pd[N - 1] > 0 ? pid.at({0, t->pd[N - 1]}) : -1;
-  return FP_OK;
+  return ops_layout(t);
 }
 
 }  // namespace fp

@@ -452,12 +452,18 @@ __device__ __forceinline__ T shfl_any(T v, int src) {
   return v;
 }
 
+// The grouped-op kernel's table per point: entries of 8 bytes, the walk's
+// powers at [0, nlive), the slots at [nlive, nlive + nslot); the power
+// program writes explicit positions (its temporaries above nlive).
 struct OpArgs {
   const void* recs;    // OpRec<coef> [nops]
   const void* stream;  // coefficients of chains and blocks
+  const uint2* prog;   // [nprog] {op | A1 << 2 | A2 << 17, destination}
+  const uint32_t* chain_pid;  // [nsteps] position of each node's edge power
   int64_t nops;
-  int pid_x1;       // power slot of x
-  int pid_pow[kMaxBlock + 1];  // power slot of x^d for the block templates (-1: absent)
+  int nprog, nlive, nslot, entries;
+  int root_lh, root_pid;      // root slot, position of the root's power (-1: none)
+  int pid_pow[kMaxBlock + 1];  // position of x^d for the block templates (-1: absent)
 };
 
 template <int SCHEME>
@@ -576,13 +582,14 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
   using V = typename A::val;
   using W = typename A::pw;
   using C = typename A::coef;
-  V* acc = reinterpret_cast<V*>(smem_raw);  // [nslot][PPT][TPB]
-  W* pw = reinterpret_cast<W*>(smem_raw + sizeof(V) * (size_t)g.nslot * PPT * kTPB);  // [npow][PPT][TPB]
+  static_assert(sizeof(V) == sizeof(W), "powers and slots share one table");
+  W* pw = reinterpret_cast<W*>(smem_raw);                        // [entries][PPT][TPB]
+  V* acc = reinterpret_cast<V*>(smem_raw) + (size_t)o.nlive * PPT * kTPB;  // slots above the walk's powers
   const int tid = threadIdx.x;
 
-  for (int k = 0; k < g.npow; ++k) {
-    const uint32_t w = __ldg(g.pow_prog + k);
-    const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+  for (int k = 0; k < o.nprog; ++k) {
+    const uint2 e = __ldg(o.prog + k);
+    const uint32_t op = e.x & 3u, a1 = (e.x >> 2) & 0x7FFFu, a2 = e.x >> 17, dst = e.y;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int64_t idx = base + p * kTPB + tid;
@@ -590,13 +597,13 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
       if (op == kPowLoad) r = idx < g.npts ? A::load_point(g.points, (int)a1, idx, g.npts) : A::dummy_point();
       else if (op == kPowSq) r = A::square(pw[(a1 * PPT + p) * kTPB + tid]);
       else r = A::mulx(pw[(a1 * PPT + p) * kTPB + tid], pw[(a2 * PPT + p) * kTPB + tid]);
-      pw[(k * PPT + p) * kTPB + tid] = r;
+      pw[(dst * PPT + p) * kTPB + tid] = r;
     }
   }
 
   // powers x^d of the block templates: every one is a partial degree of the
   // tree, so it is read from the power table (recomputing them per block
-  // would cost FP64 multiplies)
+  // would cost FP64 multiplies), before the slots reuse the temporaries' space
   W xp[PPT][kMaxBlock + 1];
   if constexpr (SCHEME != 0) {
 #pragma unroll
@@ -631,7 +638,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
 #pragma unroll
       for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(__ldg(cs)) : acc[(S * PPT + p) * kTPB + tid];
       if ((h.x >> kOpUniform) & 1u) {
-        const int pc = (int)(__ldg(g.ctrl + j0) >> kCtrlPid);
+        const int pc = (int)__ldg(o.chain_pid + j0);
         W xu[PPT];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) xu[p] = pw[(pc * PPT + p) * kTPB + tid];
@@ -642,7 +649,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
         }
       } else {
         for (int t = 1; t < len; ++t) {
-          const int pc = (int)(__ldg(g.ctrl + j0 + t - 1) >> kCtrlPid);
+          const int pc = (int)__ldg(o.chain_pid + j0 + t - 1);
           const V cj = A::from_coef(__ldg(cs + t));
 #pragma unroll
           for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
@@ -683,8 +690,8 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     const int64_t idx = base + p * kTPB + tid;
-    V r = A::root(g.root_leaf, rc, &acc[(g.root_lh * PPT + p) * kTPB + tid]);
-    if (g.root_pid >= 0) r = A::apply_root_power(r, pw[(g.root_pid * PPT + p) * kTPB + tid]);
+    V r = A::root(g.root_leaf, rc, &acc[(o.root_lh * PPT + p) * kTPB + tid]);
+    if (o.root_pid >= 0) r = A::apply_root_power(r, pw[(o.root_pid * PPT + p) * kTPB + tid]);
     if (idx < g.npts) A::store(g.out, idx, g.npts, r);
   }
 }
@@ -739,9 +746,14 @@ cudaError_t launch_eval_smem(const EvalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class A, int PPT>
+size_t ops_smem(const OpArgs& o) {
+  return sizeof(typename A::pw) * (size_t)o.entries * PPT * kTPB;
+}
+
 template <class A, int PPT, int SCHEME>
 cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
-  const size_t smem = (sizeof(typename A::val) * (size_t)a.nslot + sizeof(typename A::pw) * (size_t)a.npow) * PPT * kTPB;
+  const size_t smem = ops_smem<A, PPT>(o);
   if (smem > kSmemMax) return cudaErrorInvalidValue;
   static int configured_dev = -1;
   int dev = 0;
@@ -763,8 +775,7 @@ cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) 
 // table fits in shared memory, else the node-by-node kernel (on-the-fly powers).
 template <class A, int PPT_OPS, int PPT_NODE>
 cudaError_t launch_eval_fused(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant) {
-  const size_t table = (sizeof(typename A::val) * (size_t)a.nslot + sizeof(typename A::pw) * (size_t)a.npow) * PPT_OPS * kTPB;
-  const bool ops_ok = table <= kTableSmemCap && o.recs != nullptr;
+  const bool ops_ok = ops_smem<A, PPT_OPS>(o) <= kTableSmemCap && o.recs != nullptr;
   if (variant == 1 && !ops_ok) return cudaErrorInvalidValue;
   if (variant != 2 && ops_ok) {
     if (scheme == FP_SCHEME_E) return launch_eval_ops<A, PPT_OPS, FP_SCHEME_E>(a, o, s);

@@ -71,6 +71,8 @@ struct DeviceSchedule {
   double* st_f64 = nullptr;          // coefficient stream of chains and blocks
   float* st_f32 = nullptr;
   uint64_t* st_u64 = nullptr;
+  uint2* ops_prog = nullptr;         // power program of the grouped-op kernel
+  uint32_t* ops_chain_pid = nullptr;  // [nsteps]
 };
 
 }  // namespace fp
@@ -107,6 +109,15 @@ struct fp_tree {
   int block_scheme = 0;            // FP_SCHEME_E or FP_SCHEME_B when blocks are used, else 0
   int pid_x1 = -1;                 // power slot of x_1
   int pid_pow[fp::kMaxBlock + 1] = {};  // power slot of x_1^d, d <= kMaxBlock (-1: absent)
+
+  // the grouped-op kernel's per-point table: the walk's powers at positions
+  // [0, ops_nlive), its slots at [ops_nlive, ops_nlive + ops_nslot); the op
+  // records above carry slots and powers in this layout
+  std::vector<uint2> ops_prog;          // {op | A1 << 2 | A2 << 17 (positions), destination}
+  std::vector<uint32_t> ops_chain_pid;  // [nnodes-1] position of each node's edge power
+  int ops_nlive = 0, ops_nslot = 1, ops_entries = 1;
+  int ops_root_lh = 0, ops_root_pid = -1;
+  int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_1^d for the block templates (-1: absent)
 
   // launch configuration chosen by fp_tune per value type (kernel, ppt; 0 = not tuned)
   int tuned_kernel[4] = {0, 0, 0, 0};

@@ -41,18 +41,45 @@ def _run_value(scheme, c, xpow):
 
 
 def _replay(t, coeffs, x, counts=None):
+    """Run the power program and the ops on one table per point, as the
+    kernel does: powers at their positions, slot s at position nlive + s.
+    A temporary or a slot that overwrote a power still in use, or a slot
+    still in use, would change the value."""
     ex = t.export()
     sc = t.schedule()
     n = len(ex["parent"])
     node_c = [int(coeffs[k]) if k >= 0 else 0 for k in ex["term_of_node"]]
-    pv, pdg = sc["pow_var"], sc["pow_deg"]
-    pw = [pow(int(x[int(pv[k])]), int(pdg[k]), P) for k in range(len(pv))]
+    E, nlive = sc["entries"], sc["nlive"]
+    assert nlive + sc["nslot"] <= E
+    tab = [None] * E
+    for w, dst in sc["prog"]:
+        w, dst = int(w), int(dst)
+        op, a1, a2 = w & 3, (w >> 2) & 0x7FFF, w >> 17
+        assert dst < E
+        if op == 0:
+            tab[dst] = int(x[a1]) % P
+        elif op == 1:
+            tab[dst] = tab[a1] * tab[a1] % P
+        else:
+            tab[dst] = tab[a1] * tab[a2] % P
     x1 = int(x[0])
+    # the block templates read their powers right after the program
+    xp = {d: tab[int(q)] for d, q in enumerate(sc["block_pow"]) if q >= 0}
+    for d, v in xp.items():
+        assert v == pow(x1, d, P), d
 
     def xpow(d):
-        return pow(x1, d, P)
+        return xp[d]
 
-    acc = {}
+    def slot(s_):
+        assert 0 <= s_ < sc["nslot"]
+        return nlive + s_
+
+    def power(pos, deg, var):  # a walk power: below nlive, and the right one
+        assert 0 <= pos < nlive
+        assert tab[pos] == pow(int(x[var]), deg, P), (pos, deg, var)
+        return tab[pos]
+
     for rec_, a_node, b_node in zip(sc["op_words"], sc["op_a_node"], sc["op_b_node"]):
         w0, ln, j0, off = (int(v) for v in rec_)
         kind, S, D = w0 & 3, (w0 >> 2) & 63, (w0 >> 8) & 63
@@ -61,11 +88,9 @@ def _replay(t, coeffs, x, counts=None):
         j1 = j0 + ln - 1
         if counts is not None:
             counts[kind] += 1
-        # the op's outgoing edge is the edge of its last node
-        assert int(pdg[pid]) == int(ex["pd"][j1]) and int(pv[pid]) == int(ex["pd_var"][j1])
         if kind == 0:
             assert ln == 1
-            v = node_c[a_node] if leaf else acc[S]
+            v = node_c[a_node] if leaf else tab[slot(S)]
             if leaf:
                 assert a_node == j0
         else:
@@ -73,13 +98,14 @@ def _replay(t, coeffs, x, counts=None):
             assert st == list(range(j0, j1 + 1)) and off % 4 == 0
             cs = [node_c[j] for j in st]
             if kind == 1:
-                v = cs[0] if leaf else acc[S]
+                v = cs[0] if leaf else tab[slot(S)]
                 pids = set()
                 for i in range(1, ln):
                     j = j0 + i - 1
                     assert int(ex["parent"][j]) == j + 1
-                    pids.add((int(ex["pd_var"][j]), int(ex["pd"][j])))
-                    v = (v * pow(int(x[int(ex["pd_var"][j])]), int(ex["pd"][j]), P) + cs[i]) % P
+                    pc = int(sc["chain_pid"][j])
+                    pids.add(pc)
+                    v = (v * power(pc, int(ex["pd"][j]), int(ex["pd_var"][j])) + cs[i]) % P
                 if uniform:
                     assert len(pids) == 1
             else:
@@ -87,20 +113,22 @@ def _replay(t, coeffs, x, counts=None):
                 exps = ex["node_e"][j0:j1 + 1, 0]
                 assert np.array_equal(exps, np.arange(exps[0], exps[0] - ln, -1))
                 if kind == 3:  # N's slot (c_N and its earlier children) stands for c_N
-                    cs = cs[:-1] + [acc[S]]
+                    cs = cs[:-1] + [tab[slot(S)]]
                 v = _run_value(sc["block_scheme"], cs, xpow)
         q = int(ex["parent"][j1])
+        # the op's outgoing edge is the edge of its last node
+        xd = power(pid, int(ex["pd"][j1]), int(ex["pd_var"][j1]))
         if first:
             init = node_c[b_node] if b_node >= 0 else 0
             if b_node >= 0:
                 assert b_node == q
         else:
-            init = acc[D]
-        acc[D] = (v * pw[pid] + init) % P
+            init = tab[slot(D)]
+        tab[slot(D)] = (v * xd + init) % P
     root = n - 1
-    r = node_c[root] if sc["root_leaf"] else acc[sc["root_lh"]]
+    r = node_c[root] if sc["root_leaf"] else tab[slot(sc["root_lh"])]
     if sc["root_pid"] >= 0:
-        r = r * pw[sc["root_pid"]] % P
+        r = r * power(sc["root_pid"], int(ex["pd"][root]), 0) % P
     return r
 
 
