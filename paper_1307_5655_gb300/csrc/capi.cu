@@ -215,6 +215,7 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
   o.entries = t->ops_entries;
   o.root_lh = t->ops_root_lh;
   o.root_pid = t->ops_root_pid;
+  o.pos_x1 = t->ops_pos_x1;
   for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t root = t->nnodes - 1;
   switch (dt) {

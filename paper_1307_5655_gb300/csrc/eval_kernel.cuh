@@ -78,6 +78,8 @@ struct F64 {
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
+  template <bool SC, bool IC, bool X1>
+  static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return fma(s, xd, init); }
   static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return __dmul_rn(r, xd); }
@@ -128,6 +130,20 @@ struct F32C {
     float lo = __fadd_rn(init.y, __fadd_rn(pe, se));
     lo = __fmaf_rn(s.y, xd.x, lo);
     lo = __fmaf_rn(s.x, xd.y, lo);
+    return make_float2(h, lo);
+  }
+  // mad with operands known to have a zero low part: SC, s is a coefficient;
+  // IC, init is a coefficient; X1, the power is x itself (a loaded FP32
+  // point).  The terms dropped are exact zeros, so the value is mad's.
+  template <bool SC, bool IC, bool X1>
+  static __device__ __forceinline__ val mad_k(val s, pw xd, val init) {
+    const float p = __fmul_rn(s.x, xd.x);
+    const float pe = __fmaf_rn(s.x, xd.x, -p);
+    float h, se;
+    two_sum(init.x, p, h, se);
+    float lo = IC ? __fadd_rn(pe, se) : __fadd_rn(init.y, __fadd_rn(pe, se));
+    if constexpr (!SC) lo = __fmaf_rn(s.y, xd.x, lo);
+    if constexpr (!X1) lo = __fmaf_rn(s.x, xd.y, lo);
     return make_float2(h, lo);
   }
   static constexpr bool kSlotAtEnd = true;
@@ -201,6 +217,8 @@ struct MODP {
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
+  template <bool SC, bool IC, bool X1>
+  static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return mul_add(s, xd, init); }
   // a + b for residues a, b < p (2^64 == 2^32 - 1 on a carry)
   static __device__ __forceinline__ val add(val a, val b) {
     uint64_t r = a + b;
@@ -463,6 +481,7 @@ struct OpArgs {
   int64_t nops;
   int nprog, nlive, nslot, entries;
   int root_lh, root_pid;      // root slot, position of the root's power (-1: none)
+  int pos_x1;                 // position of x_1^1 among the walk's powers (-1: none)
   int pid_pow[kMaxBlock + 1];  // position of x^d for the block templates (-1: absent)
 };
 
@@ -503,7 +522,11 @@ __device__ __forceinline__ typename A::val block_eval(const typename A::coef (&c
     constexpr int f = scheme_split<SCHEME>(n);
     const typename A::val b = block_eval<A, SCHEME, HI - f + 1, HI, BASE>(c, xp, base);
     const typename A::val a = block_eval<A, SCHEME, LO, HI - f, false>(c, xp, base);
-    return A::mad(a, xp[f], b);
+    // a single term is a bare coefficient; the base is one when the type
+    // adds a partial block's slot after the block (A::kSlotAtEnd)
+    constexpr bool a_coef = LO == HI - f;
+    constexpr bool b_coef = f == 1 && (!BASE || A::kSlotAtEnd);
+    return A::template mad_k<a_coef, b_coef, f == 1>(a, xp[f], b);
   }
 }
 
@@ -642,17 +665,26 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
         W xu[PPT];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) xu[p] = pw[(pc * PPT + p) * kTPB + tid];
-        for (int t = 1; t < len; ++t) {
-          const V cj = A::from_coef(__ldg(cs + t));
+        if (pc == o.pos_x1) {  // Horner runs over consecutive exponents
+          for (int t = 1; t < len; ++t) {
+            const V cj = A::from_coef(__ldg(cs + t));
 #pragma unroll
-          for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xu[p], cj);
+            for (int p = 0; p < PPT; ++p) v[p] = A::template mad_k<false, true, true>(v[p], xu[p], cj);
+          }
+        } else {
+          for (int t = 1; t < len; ++t) {
+            const V cj = A::from_coef(__ldg(cs + t));
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) v[p] = A::template mad_k<false, true, false>(v[p], xu[p], cj);
+          }
         }
       } else {
         for (int t = 1; t < len; ++t) {
           const int pc = (int)__ldg(o.chain_pid + j0 + t - 1);
           const V cj = A::from_coef(__ldg(cs + t));
 #pragma unroll
-          for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
+          for (int p = 0; p < PPT; ++p)
+            v[p] = A::template mad_k<false, true, false>(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
         }
       }
     } else {

@@ -117,6 +117,7 @@ struct fp_tree {
   std::vector<uint32_t> ops_chain_pid;  // [nnodes-1] position of each node's edge power
   int ops_nlive = 0, ops_nslot = 1, ops_entries = 1;
   int ops_root_lh = 0, ops_root_pid = -1;
+  int ops_pos_x1 = -1;  // position of x_1^1 when the walk reads it
   int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_1^d for the block templates (-1: absent)
 
   // launch configuration chosen by fp_tune per value type (kernel, ppt; 0 = not tuned)
