@@ -357,17 +357,24 @@ def run_profile_case(args):
     import paper_1307_5655_gb300 as fpl
     k, scheme, dt = args.profile_k, args.profile_scheme, args.profile_dtype
     torch.cuda.set_device(0)
-    x = W.points_f64(1, NPTS, SEED + 1)
-    e, c, _ = W.univariate_case(k, 1, SEED + k)
+    # k > 0: dense univariate with k terms at 2^24 points; k = 0: trivariate
+    # total degree 40 (12341 terms) at 2^22 points
+    nv, npts = (1, NPTS) if k > 0 else (3, 1 << 22)
+    x = W.points_f64(nv, npts, SEED + 1)
+    if k > 0:
+        e, c, _ = W.univariate_case(k, 1, SEED + k)
+        em, cm, _ = W.univariate_case(k, 1, SEED + k, "modp")
+    else:
+        e, c, _ = W.trivariate_case(40, 1, SEED, "f64")
+        em, cm, _ = W.trivariate_case(40, 1, SEED, "modp")
     if dt == "modp":
-        e, c, _ = W.univariate_case(k, 1, SEED + k, "modp")
-        pts = torch.from_numpy(W.points_modp(1, NPTS, SEED + 2).view(np.int64)).cuda()
-        t = fpl.fp_compile(e, c, scheme, modp=True)
+        pts = torch.from_numpy(W.points_modp(nv, npts, SEED + 2).view(np.int64)).cuda()
+        t = fpl.fp_compile(em, cm, scheme, modp=True)
     elif dt == "f32c":
         pts = torch.from_numpy(W.to_f32(x)).cuda()
         t = fpl.fp_compile(e, c, scheme)
     elif dt == "iv64":
-        lo, hi = W.boxes(1, NPTS, SEED + 3)
+        lo, hi = W.boxes(nv, npts, SEED + 3)
         pts = torch.from_numpy(np.ascontiguousarray(np.stack([lo, hi], axis=1))).cuda()
         t = fpl.fp_compile(e, c, scheme)
     else:
@@ -377,7 +384,7 @@ def run_profile_case(args):
         fpl.fp_eval_ex(t, dt, pts, kernel=args.profile_kernel, ppt=args.profile_ppt)
     torch.cuda.synchronize()
     print("profile case done: k=%d scheme=%s dtype=%s kernel=%s ppt=%d points=%d"
-          % (k, scheme, dt, args.profile_kernel, args.profile_ppt, NPTS))
+          % (k, scheme, dt, args.profile_kernel, args.profile_ppt, npts))
 
 
 def _timed(fn, steps, warmup):
@@ -429,7 +436,8 @@ def run_compose(args):
 
 def run_eval_config(args):
     """Per-configuration evaluation measurements: dense univariate 1024 terms at
-    65536 points (E), trivariate total degree 40 at 2^22 points (IV64, MODP)."""
+    65536 points (E), trivariate total degree 40 at 2^22 points (IV64, MODP,
+    and FP64 / FP32C for the grouped-op kernel on a multivariate tree)."""
     import torch
     import workloads as W
     import paper_1307_5655_gb300 as fpl
@@ -456,6 +464,14 @@ def run_eval_config(args):
         ms = _timed(lambda: fpl.fp_eval(tm, "modp", dm), 3, 1)
         res["trivariate_deg40_%s_modp_2^22" % s] = {"ms": ms, "G_term_evals_per_s": len(em) * npts / (ms * 1e6),
                                                      "launch": tune}
+        ef, cf, xf = W.trivariate_case(40, npts, 302, "f64")
+        tf = fpl.fp_compile(ef, cf, s)
+        df = torch.from_numpy(xf).cuda()
+        for dt, d in (("f64", df), ("f32c", torch.from_numpy(W.to_f32(xf)).cuda())):
+            tune = fpl.fp_tune(tf, dt, d[:, : 1 << 20].contiguous()) if not args.no_tune else None
+            ms = _timed(lambda: fpl.fp_eval(tf, dt, d), 3, 1)
+            res["trivariate_deg40_%s_%s_2^22" % (s, dt)] = {"ms": ms, "G_term_evals_per_s": len(ef) * npts / (ms * 1e6),
+                                                           "launch": tune}
     print(json.dumps({"metric": "G term-evals/s", "results": res, "n_gpus": 1, "data": "synthetic"}))
 
 
@@ -659,7 +675,7 @@ def main():
     ap.add_argument("--hbm-budget", type=int, default=8192, help="MiB of device memory for requests in flight")
     ap.add_argument("--profile-case", action="store_true",
                     help="run two launches of one evaluation (for ncu) and exit")
-    ap.add_argument("--profile-k", type=int, default=3000)
+    ap.add_argument("--profile-k", type=int, default=3000, help="terms (0: trivariate total degree 40)")
     ap.add_argument("--profile-scheme", default="E")
     ap.add_argument("--profile-dtype", default="f64")
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "ops", "node"])

@@ -205,8 +205,9 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
  *       A1, 2 multiplies positions A1 and A2.
  *   chain_pid [nnodes - 1]: table position of each node's edge power (read
  *       inside chains).
- *   block_pow [17]: table position of x_1^d read by the block templates
- *       after the program (-1: absent).
+ *   block_pow [17]: table position of x_b^d read by the block templates
+ *       after the program (-1: absent); b = nvars - 1, the innermost
+ *       variable, whose groups are univariate polynomials under the scheme.
  *   layout [7]: nlive (the walk's powers sit at positions [0, nlive)),
  *       nslot (slot s sits at position nlive + s), table entries per point,
  *       block scheme (FP_SCHEME_E / FP_SCHEME_B when blocks are used, else 0),

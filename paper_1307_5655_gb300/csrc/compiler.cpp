@@ -402,7 +402,21 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
       size[t->parent[i]] += size[i];
       nchild[t->parent[i]]++;
     }
-    const bool blocks = nvars == 1 && (scheme == FP_SCHEME_E || scheme == FP_SCHEME_B);
+    // blocks run over the innermost variable (the only one, for univariate
+    // polynomials): its groups are univariate polynomials under the scheme
+    const int bv = nvars - 1;
+    const bool blocks = scheme == FP_SCHEME_E || scheme == FP_SCHEME_B;
+    // nodes j0..r have consecutive exponents of x_bv and equal exponents of the others
+    auto dense_run = [&](int64_t j0, int64_t r) {
+      const int32_t* er = &t->node_e[r * nvars];
+      for (int64_t j = j0; j < r; ++j) {
+        const int32_t* ej = &t->node_e[j * nvars];
+        for (int v = 0; v < bv; ++v)
+          if (ej[v] != er[v]) return false;
+        if (ej[bv] - er[bv] != r - j) return false;
+      }
+      return true;
+    };
     t->block_scheme = blocks ? (int)scheme : 0;
     std::vector<int64_t> block_len(N, 0);    // at the block's first node
     std::vector<int64_t> partial_len(N, 0);  // at the partial block's first node
@@ -417,7 +431,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
         }
         if (s < 2) continue;
         const int64_t j0 = r - s + 1;
-        if (t->node_e[j0] - t->node_e[r] != s - 1) continue;  // not a dense run
+        if (!dense_run(j0, r)) continue;
         if (j0 >= (1ll << 32)) continue;
         partial_len[j0] = s;
         for (int64_t j = j0; j <= r; ++j) in_partial[j] = 1;
@@ -427,7 +441,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
         if (s < 2 || s > kMaxBlock || in_partial[r]) continue;
         if (q != N - 1 && size[q] <= kMaxBlock) continue;  // not maximal
         const int64_t j0 = r - s + 1;
-        if (t->node_e[j0] - t->node_e[r] != s - 1) continue;  // not a dense run
+        if (!dense_run(j0, r)) continue;
         if (j0 >= (1ll << 32)) continue;
         block_len[j0] = s;
       }
@@ -483,8 +497,8 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
       emit(j > i ? kOpChain : kOpNode, i, j);
       i = j + 1;
     }
-    t->pid_x1 = pid.count({0, 1}) ? pid.at({0, 1}) : -1;
-    for (int d = 0; d <= kMaxBlock; ++d) t->pid_pow[d] = pid.count({0, d}) ? pid.at({0, d}) : -1;
+    t->pid_x1 = pid.count({bv, 1}) ? pid.at({bv, 1}) : -1;
+    for (int d = 0; d <= kMaxBlock; ++d) t->pid_pow[d] = pid.count({bv, d}) ? pid.at({bv, d}) : -1;
     if (t->pid_x1 < 0) t->block_scheme = 0;
   }
 

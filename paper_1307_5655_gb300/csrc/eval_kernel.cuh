@@ -77,6 +77,7 @@ struct F64 {
   }
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
+  static constexpr bool kExact = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return fma(s, xd, init); }
@@ -147,6 +148,7 @@ struct F32C {
     return make_float2(h, lo);
   }
   static constexpr bool kSlotAtEnd = true;
+  static constexpr bool kExact = false;
   // a + b with the rounding error of the leading sum (TwoSum) kept in lo
   static __device__ __forceinline__ val add(val a, val b) {
     float h, e;
@@ -216,6 +218,7 @@ struct MODP {
   }
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
+  static constexpr bool kExact = true;  // any evaluation order gives the same residue
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return mul_add(s, xd, init); }
@@ -481,7 +484,7 @@ struct OpArgs {
   int64_t nops;
   int nprog, nlive, nslot, entries;
   int root_lh, root_pid;      // root slot, position of the root's power (-1: none)
-  int pos_x1;                 // position of x_1^1 among the walk's powers (-1: none)
+  int pos_x1;                 // position of x_b (b: the blocks' variable) among the walk's powers (-1: none)
   int pid_pow[kMaxBlock + 1];  // position of x^d for the block templates (-1: absent)
 };
 
@@ -687,6 +690,23 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
             v[p] = A::template mad_k<false, true, false>(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
         }
       }
+    } else if constexpr (SCHEME != 0 && A::kExact) {
+      // exact arithmetic: the run's value does not depend on the order of
+      // its operations, so the block is evaluated by Horner's rule over the
+      // same run (one short loop instead of an unrolled template per length)
+      const C* cs = st + off;
+      const bool partial = kind == kOpPartial;
+      const V c0 = A::from_coef(__ldg(cs));
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) v[p] = c0;
+      for (int t = 1; t + 1 < len; ++t) {
+        const V ct = A::from_coef(__ldg(cs + t));
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xp[p][1], ct);
+      }
+      const V cl = A::from_coef(__ldg(cs + len - 1));
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xp[p][1], partial ? acc[(S * PPT + p) * kTPB + tid] : cl);
     } else {
       if constexpr (SCHEME != 0) {
         C c[kMaxBlock];

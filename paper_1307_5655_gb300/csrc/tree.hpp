@@ -107,8 +107,8 @@ struct fp_tree {
   std::vector<int64_t> op_b_node;  // parent whose coefficient initialises the slot, or -1
   std::vector<int64_t> stream;     // node whose coefficient sits at each stream slot, or -1 (padding)
   int block_scheme = 0;            // FP_SCHEME_E or FP_SCHEME_B when blocks are used, else 0
-  int pid_x1 = -1;                 // power slot of x_1
-  int pid_pow[fp::kMaxBlock + 1] = {};  // power slot of x_1^d, d <= kMaxBlock (-1: absent)
+  int pid_x1 = -1;                 // power slot of x_b, b = the innermost variable (blocks run over it)
+  int pid_pow[fp::kMaxBlock + 1] = {};  // power slot of x_b^d, d <= kMaxBlock (-1: absent)
 
   // the grouped-op kernel's per-point table: the walk's powers at positions
   // [0, ops_nlive), its slots at [ops_nlive, ops_nlive + ops_nslot); the op
@@ -117,8 +117,8 @@ struct fp_tree {
   std::vector<uint32_t> ops_chain_pid;  // [nnodes-1] position of each node's edge power
   int ops_nlive = 0, ops_nslot = 1, ops_entries = 1;
   int ops_root_lh = 0, ops_root_pid = -1;
-  int ops_pos_x1 = -1;  // position of x_1^1 when the walk reads it
-  int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_1^d for the block templates (-1: absent)
+  int ops_pos_x1 = -1;  // position of x_b when the walk reads it
+  int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_b^d for the block templates (-1: absent)
 
   // launch configuration chosen by fp_tune per value type (kernel, ppt; 0 = not tuned)
   int tuned_kernel[4] = {0, 0, 0, 0};

@@ -62,7 +62,7 @@ def _replay(t, coeffs, x, counts=None):
             tab[dst] = tab[a1] * tab[a1] % P
         else:
             tab[dst] = tab[a1] * tab[a2] % P
-    x1 = int(x[0])
+    x1 = int(x[len(x) - 1])  # blocks run over the innermost variable
     # the block templates read their powers right after the program
     xp = {d: tab[int(q)] for d, q in enumerate(sc["block_pow"]) if q >= 0}
     for d, v in xp.items():
@@ -110,8 +110,9 @@ def _replay(t, coeffs, x, counts=None):
                     assert len(pids) == 1
             else:
                 assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 16
-                exps = ex["node_e"][j0:j1 + 1, 0]
-                assert np.array_equal(exps, np.arange(exps[0], exps[0] - ln, -1))
+                run = ex["node_e"][j0:j1 + 1]
+                assert np.array_equal(run[:, -1], np.arange(run[0, -1], run[0, -1] - ln, -1))
+                assert (run[:, :-1] == run[-1, :-1]).all()
                 if kind == 3:  # N's slot (c_N and its earlier children) stands for c_N
                     cs = cs[:-1] + [tab[slot(S)]]
                 v = _run_value(sc["block_scheme"], cs, xpow)
@@ -174,8 +175,35 @@ def test_sparse_and_hybrid_schedules():
     _check(e2, c2, "CUSTOM", ft, npts=2, seed=2)
 
 
-@pytest.mark.parametrize("scheme", ["E", "B"])
+@pytest.mark.parametrize("scheme", ["E", "B", "H"])
 def test_multivariate_schedule(scheme):
+    counts = [0, 0, 0, 0]
     e = W.total_degree_exps(3, 8)
     c = W.residues(len(e), 11)
-    _check(e, c, scheme, npts=2, seed=3)
+    _check(e, c, scheme, npts=2, seed=3, counts=counts)
+    if scheme != "H":  # the innermost variable's dense runs become blocks
+        assert counts[2] > 0
+
+
+@pytest.mark.parametrize("scheme", ["E", "B"])
+def test_trivariate_degree40_schedule(scheme):
+    counts = [0, 0, 0, 0]
+    e = W.total_degree_exps(3, 40)
+    c = W.residues(len(e), 12)
+    _check(e, c, scheme, npts=1, seed=4, counts=counts)
+    assert counts[2] > 0 and counts[3] > 0
+    assert sum(counts) * 4 < len(e), counts
+
+
+def test_multivariate_with_virtual_roots_and_gaps():
+    r = W.rng(8)
+    e = W.total_degree_exps(3, 12)
+    keep = r.random(len(e)) < 0.7  # gaps in every variable, missing group roots
+    e = e[keep]
+    c = W.residues(len(e), 13)
+    for scheme in ("E", "B"):
+        _check(e, c, scheme, npts=2, seed=5)
+    e2 = W.total_degree_exps(2, 30)
+    c2 = W.residues(len(e2), 14)
+    for scheme in ("E", "B"):
+        _check(e2, c2, scheme, npts=2, seed=6)
