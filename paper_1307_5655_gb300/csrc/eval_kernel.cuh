@@ -763,8 +763,9 @@ cudaError_t launch_eval_iv64(const EvalArgs& a, const OpArgs& o, int scheme, cud
 cudaError_t launch_eval_modp(const EvalArgs& a, const OpArgs& o, int scheme, cudaStream_t s, int variant, int ppt);
 
 // Shared memory of one block; the power table is used while it leaves room
-// for at least two resident blocks per SM.
-constexpr size_t kTableSmemCap = 100 * 1024;
+// for at least two resident blocks per SM (228 KB per SM, 1 KB of it reserved
+// per block).
+constexpr size_t kTableSmemCap = 113 * 1024;
 constexpr size_t kSmemMax = 227 * 1024;
 
 template <class A, int PPT>
