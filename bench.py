@@ -411,7 +411,7 @@ def run_compose(args):
     torch.cuda.set_device(0)
     npairs, degp, degq = args.pairs, 512, 64
     res = {}
-    for dt in ("modp", "f64"):
+    for dt in args.compose_dtypes.split(","):
         pc, qc = W.composition_case(npairs, degp, degq, 4000, dt)
         e = W.dense_univariate_exps(degp + 1)
         if dt == "modp":
@@ -422,7 +422,7 @@ def run_compose(args):
             dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1])).cuda()
         out = torch.empty((npairs, degp * degq + 1), dtype=torch.int64 if dt == "modp" else torch.float64,
                           device="cuda")
-        for s in ("E", "B"):
+        for s in args.compose_schemes.split(","):
             t = fpl.fp_compile(e, np.ones(degp + 1, dtype=np.uint64 if dt == "modp" else np.float64), s,
                                modp=dt == "modp")
             steps = args.steps if dt == "modp" else 1
@@ -680,6 +680,8 @@ def main():
     ap.add_argument("--profile-dtype", default="f64")
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "ops", "node"])
     ap.add_argument("--profile-ppt", type=int, default=0, help="points per thread (0: automatic)")
+    ap.add_argument("--compose-dtypes", default="modp,f64", help="value types of --workload compose")
+    ap.add_argument("--compose-schemes", default="E,B", help="schemes of --workload compose")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

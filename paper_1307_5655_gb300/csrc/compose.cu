@@ -60,27 +60,29 @@ __device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP:
 __device__ __forceinline__ int ilog2_dev(int n) { return 31 - __clz(n); }
 
 __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
-  const int per = n >> 2;
-  int half = n >> 1;
-  for (; half >= 2; half >>= 2) {
+  // all sizes are powers of two: indices by shifts and masks
+  const int logn = ilog2_dev(n), lper = logn - 2;
+  int lhalf = logn - 1;
+  for (; lhalf >= 1; lhalf -= 2) {  // half = 2^lhalf >= 2: two stages
     __syncthreads();
-    const int q = half >> 1, s1 = n / (2 * half), s2 = n / half;
-    for (int e = threadIdx.x; e < count * per; e += blockDim.x) {
-      const int v = e / per, u = e - v * per;
-      const int grp = u / q, pos = u - grp * q;
-      uint64_t* x = a + v * n + grp * 2 * half;
-      const int i0 = pos, i1 = pos + q, i2 = pos + half, i3 = pos + half + q;
+    const int lq = lhalf - 1, q = 1 << lq;
+    const int ls1 = logn - 1 - lhalf, ls2 = logn - lhalf;  // s1 = n / (2 half), s2 = n / half
+    for (int e = threadIdx.x; e < (count << lper); e += blockDim.x) {
+      const int v = e >> lper, u = e & ((1 << lper) - 1);
+      const int grp = u >> lq, pos = u & (q - 1);
+      uint64_t* x = a + (v << logn) + (grp << (lhalf + 1));
+      const int i0 = pos, i1 = pos + q, i2 = pos + (1 << lhalf), i3 = pos + (1 << lhalf) + q;
       const uint64_t a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
-      const uint64_t b0 = d_add(a0, a2), b2 = d_mul(d_sub(a0, a2), __ldg(tw + pos * s1));
-      const uint64_t b1 = d_add(a1, a3), b3 = d_mul(d_sub(a1, a3), __ldg(tw + (pos + q) * s1));
-      const uint64_t t = __ldg(tw + pos * s2);
+      const uint64_t b0 = d_add(a0, a2), b2 = d_mul(d_sub(a0, a2), __ldg(tw + (pos << ls1)));
+      const uint64_t b1 = d_add(a1, a3), b3 = d_mul(d_sub(a1, a3), __ldg(tw + ((pos + q) << ls1)));
+      const uint64_t t = __ldg(tw + (pos << ls2));
       x[i0] = d_add(b0, b1);
       x[i1] = d_mul(d_sub(b0, b1), t);
       x[i2] = d_add(b2, b3);
       x[i3] = d_mul(d_sub(b2, b3), t);
     }
   }
-  if (half == 1) {  // last radix-2 stage: pairs (2g, 2g + 1), twiddle 1
+  if (lhalf == 0) {  // last radix-2 stage: pairs (2g, 2g + 1), twiddle 1
     __syncthreads();
     for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
       uint64_t* x = a + 2 * e;
@@ -93,8 +95,9 @@ __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
 }
 
 __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
-  int half = 1;
-  if (n >= 2 && (ilog2_dev(n) & 1)) {  // first radix-2 stage: pairs (2g, 2g + 1), twiddle 1
+  const int logn = ilog2_dev(n), lper = logn - 2;
+  int lhalf = 0;
+  if (n >= 2 && (logn & 1)) {  // first radix-2 stage: pairs (2g, 2g + 1), twiddle 1
     __syncthreads();
     for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
       uint64_t* x = a + 2 * e;
@@ -102,21 +105,21 @@ __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
       x[0] = d_add(u, w);
       x[1] = d_sub(u, w);
     }
-    half = 2;
+    lhalf = 1;
   }
-  const int per = n >> 2;
-  for (; half < n; half <<= 2) {
+  for (; lhalf < logn; lhalf += 2) {  // half = 2^lhalf, 4 half <= n: two stages
     __syncthreads();
-    const int s1 = n / (2 * half), s2 = n / (4 * half);
-    for (int e = threadIdx.x; e < count * per; e += blockDim.x) {
-      const int v = e / per, u = e - v * per;
-      const int grp = u / half, pos = u - grp * half;
-      uint64_t* x = a + v * n + grp * 4 * half;
+    const int half = 1 << lhalf;
+    const int ls1 = logn - 1 - lhalf, ls2 = logn - 2 - lhalf;  // s1 = n / (2 half), s2 = n / (4 half)
+    for (int e = threadIdx.x; e < (count << lper); e += blockDim.x) {
+      const int v = e >> lper, u = e & ((1 << lper) - 1);
+      const int grp = u >> lhalf, pos = u & (half - 1);
+      uint64_t* x = a + (v << logn) + (grp << (lhalf + 2));
       const int i0 = pos, i1 = pos + half, i2 = pos + 2 * half, i3 = pos + 3 * half;
-      const uint64_t t = __ldg(tw + pos * s1);
+      const uint64_t t = __ldg(tw + (pos << ls1));
       const uint64_t a0 = x[i0], a1 = d_mul(x[i1], t), a2 = x[i2], a3 = d_mul(x[i3], t);
       const uint64_t b0 = d_add(a0, a1), b1 = d_sub(a0, a1), b2 = d_add(a2, a3), b3 = d_sub(a2, a3);
-      const uint64_t c2 = d_mul(b2, __ldg(tw + pos * s2)), c3 = d_mul(b3, __ldg(tw + (pos + half) * s2));
+      const uint64_t c2 = d_mul(b2, __ldg(tw + (pos << ls2))), c3 = d_mul(b3, __ldg(tw + ((pos + half) << ls2)));
       x[i0] = d_add(b0, c2);
       x[i2] = d_sub(b0, c2);
       x[i1] = d_add(b1, c3);
@@ -129,6 +132,24 @@ __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
 __device__ __forceinline__ int bitrev(int x, int logn) { return logn == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - logn)); }
 
 // ------------------------------------------------------------ MODP kernels
+// The first outlen coefficients of cnt inverse transforms in sh (vectors of
+// length n), scaled by 1/n: written (mode 0), added into out (mode 1), or
+// written with init[pair] added at degree 0 (mode 2).
+__device__ __forceinline__ void store_product(const uint64_t* sh, int n, int cnt, int64_t p0, uint64_t ninv,
+                                              uint64_t* out, int64_t out_pitch, int outlen, int mode,
+                                              const uint64_t* init, int64_t init_pitch) {
+  const int logn = ilog2_dev(n);
+  for (int e = threadIdx.x; e < (cnt << logn); e += blockDim.x) {
+    const int v = e >> logn, i = e & (n - 1);
+    if (i >= outlen) continue;
+    uint64_t* o = out + (p0 + v) * out_pitch + i;
+    uint64_t val = d_mul(sh[e], ninv);
+    if (mode == 1) val = d_add(*o, val);
+    else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
+    *o = val;
+  }
+}
+
 // Forward transform of length n <= 4096 of src[pair][0..len) zero-padded,
 // into dst[pair][0..n); vpb pairs per block.
 __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch,
@@ -136,13 +157,14 @@ __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len,
   extern __shared__ uint64_t sh[];
   const int64_t p0 = (int64_t)blockIdx.x * vpb;
   const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  const int logn = ilog2_dev(n);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
-    const int v = e / n, i = e - v * n;
+    const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
   ntt_dif(sh, n, vpb, tw);
   for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-    const int v = e / n, i = e - v * n;
+    const int v = e >> logn, i = e & (n - 1);
     dst[(p0 + v) * dst_pitch + i] = sh[e];
   }
 }
@@ -157,19 +179,13 @@ __global__ void k_ntt_mul_inv_small(const uint64_t* prod, int64_t pitch, const u
   extern __shared__ uint64_t sh[];
   const int64_t p0 = (int64_t)blockIdx.x * vpb;
   const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  const int logn = ilog2_dev(n);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
-    const int v = e / n, i = e - v * n;
+    const int v = e >> logn, i = e & (n - 1);
     sh[e] = v < cnt ? d_mul(prod[(p0 + v) * pitch + i], fb[(p0 + v) * fb_pitch + i]) : 0;
   }
   ntt_dit(sh, n, vpb, twi);
-  for (int e = threadIdx.x; e < cnt * outlen; e += blockDim.x) {
-    const int v = e / outlen, i = e - v * outlen;
-    uint64_t val = d_mul(sh[v * n + i], ninv);
-    uint64_t* o = out + (p0 + v) * out_pitch + i;
-    if (mode == 1) val = d_add(*o, val);
-    else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
-    *o = val;
-  }
+  store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
 // A whole product for n <= 4096, one launch: transform of src (first len
@@ -183,24 +199,18 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
   extern __shared__ uint64_t sh[];
   const int64_t p0 = (int64_t)blockIdx.x * vpb;
   const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
+  const int logn = ilog2_dev(n);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
-    const int v = e / n, i = e - v * n;
+    const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
   ntt_dif(sh, n, vpb, tw);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
-    const int v = e / n, i = e - v * n;
+    const int v = e >> logn, i = e & (n - 1);
     if (v < cnt) sh[e] = d_mul(sh[e], fb[(p0 + v) * fb_pitch + i]);
   }
   ntt_dit(sh, n, vpb, twi);
-  for (int e = threadIdx.x; e < cnt * outlen; e += blockDim.x) {
-    const int v = e / outlen, i = e - v * outlen;
-    uint64_t val = d_mul(sh[v * n + i], ninv);
-    uint64_t* o = out + (p0 + v) * out_pitch + i;
-    if (mode == 1) val = d_add(*o, val);
-    else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
-    *o = val;
-  }
+  store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
 // Four-step transform of length n = R * C (R, C <= 4096), vector x[C n1 + n2].
@@ -214,26 +224,27 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
   const int tiles = C / TC;
   const int64_t pr = blockIdx.x / tiles;
   const int c0 = (blockIdx.x % tiles) * TC;
-  const int n = R * C;
+  const int n = R * C, mask = n - 1;  // n, R, C, TC: powers of two
+  const int lTC = ilog2_dev(TC);
   for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
-    const int r = e / TC, c = e % TC;
+    const int r = e >> lTC, c = e & (TC - 1);
     const int idx = r * C + c0 + c;
     uint64_t v = idx < len ? src[pr * src_pitch + idx] : 0;
     if (inverse) {
       // position r holds k1 = bitrev(r); undo the twiddle w^(k1 n2)
-      const int64_t ex = ((int64_t)bitrev(r, logR) * (c0 + c)) % n;
-      v = d_mul(v, __ldg(twn + ((n - ex) % n)));
+      const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
+      v = d_mul(v, __ldg(twn + ((n - ex) & mask)));
     }
     sh[c * R + r] = v;
   }
   if (inverse) ntt_dit(sh, R, TC, twR);
   else ntt_dif(sh, R, TC, twR);
   for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
-    const int r = e / TC, c = e % TC;
+    const int r = e >> lTC, c = e & (TC - 1);
     const int idx = r * C + c0 + c;
     uint64_t v = sh[c * R + r];
     if (!inverse) {
-      const int64_t ex = ((int64_t)bitrev(r, logR) * (c0 + c)) % n;
+      const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
       dst[pr * dst_pitch + idx] = d_mul(v, __ldg(twn + ex));
     } else if (idx < outlen) {
       v = d_mul(v, scale);

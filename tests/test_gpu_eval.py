@@ -257,6 +257,33 @@ def test_grouped_and_node_kernels(scheme, k):
         run(t, "iv64", (lo, hi), kernel="ops")  # intervals keep the paper's node order
 
 
+@pytest.mark.parametrize("scheme", ["E", "B"])
+@pytest.mark.parametrize("nvars,kind,size", [(3, "total", 14), (2, "graded", 300), (3, "sparse", 150)])
+def test_grouped_and_node_kernels_multivariate(scheme, nvars, kind, size):
+    """Blocks and partial blocks over the innermost variable of a multivariate
+    tree: MODP identical to the node-by-node kernel bit for bit, FP64 and
+    FP32C within the bound."""
+    e = _multi(nvars, kind, size, 21)
+    c = W.uniform_f64(len(e), 22)
+    x = W.points_f64(nvars, 3000 + 5, 23)
+    t = fpl.fp_compile(e, c, scheme)
+    cm = W.residues(len(e), 24)
+    xm = W.points_modp(nvars, 3000 + 5, 25)
+    tm = fpl.fp_compile(e, cm, scheme, modp=True)
+    sched = tm.schedule()
+    assert (sched["op_words"][:, 0] & 3 >= 2).any()  # the grouped kernel has blocks here
+    for dt, tree, pts in (("f64", t, x), ("f32c", t, x), ("modp", tm, xm)):
+        a = run(tree, dt, pts, kernel="ops")
+        b = run(tree, dt, pts, kernel="node")
+        if dt == "modp":
+            assert np.array_equal(a, b)
+            check_modp(e, cm, xm, a)
+        elif dt == "f64":
+            check_f64(e, c, x, a)
+        else:
+            check_f32c(e, c, x, a)
+
+
 def deep_ftab(kmax):
     """A function scheme maximising the lazy height (dynamic programming over
     the split f at every size): lh grows linearly, about (k - 1) / 2."""
