@@ -59,8 +59,9 @@ __device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP:
 // with one radix-2 stage when log2 n is odd.
 __device__ __forceinline__ int ilog2_dev(int n) { return 31 - __clz(n); }
 
-__device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
-  // all sizes are powers of two: indices by shifts and masks
+__device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw, int stride) {
+  // all sizes are powers of two: indices by shifts and masks; vector v starts
+  // at a + v * stride (stride >= n)
   const int logn = ilog2_dev(n), lper = logn - 2;
   int lhalf = logn - 1;
   for (; lhalf >= 1; lhalf -= 2) {  // half = 2^lhalf >= 2: two stages
@@ -70,7 +71,7 @@ __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
     for (int e = threadIdx.x; e < (count << lper); e += blockDim.x) {
       const int v = e >> lper, u = e & ((1 << lper) - 1);
       const int grp = u >> lq, pos = u & (q - 1);
-      uint64_t* x = a + (v << logn) + (grp << (lhalf + 1));
+      uint64_t* x = a + v * stride + (grp << (lhalf + 1));
       const int i0 = pos, i1 = pos + q, i2 = pos + (1 << lhalf), i3 = pos + (1 << lhalf) + q;
       const uint64_t a0 = x[i0], a1 = x[i1], a2 = x[i2], a3 = x[i3];
       const uint64_t b0 = d_add(a0, a2), b2 = d_mul(d_sub(a0, a2), __ldg(tw + (pos << ls1)));
@@ -85,7 +86,7 @@ __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
   if (lhalf == 0) {  // last radix-2 stage: pairs (2g, 2g + 1), twiddle 1
     __syncthreads();
     for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
-      uint64_t* x = a + 2 * e;
+      uint64_t* x = a + (e >> (logn - 1)) * stride + 2 * (e & ((n >> 1) - 1));
       const uint64_t u = x[0], w = x[1];
       x[0] = d_add(u, w);
       x[1] = d_sub(u, w);
@@ -94,13 +95,13 @@ __device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw) {
   __syncthreads();
 }
 
-__device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
+__device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw, int stride) {
   const int logn = ilog2_dev(n), lper = logn - 2;
   int lhalf = 0;
   if (n >= 2 && (logn & 1)) {  // first radix-2 stage: pairs (2g, 2g + 1), twiddle 1
     __syncthreads();
     for (int e = threadIdx.x; e < count * (n >> 1); e += blockDim.x) {
-      uint64_t* x = a + 2 * e;
+      uint64_t* x = a + (e >> (logn - 1)) * stride + 2 * (e & ((n >> 1) - 1));
       const uint64_t u = x[0], w = x[1];
       x[0] = d_add(u, w);
       x[1] = d_sub(u, w);
@@ -114,7 +115,7 @@ __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw) {
     for (int e = threadIdx.x; e < (count << lper); e += blockDim.x) {
       const int v = e >> lper, u = e & ((1 << lper) - 1);
       const int grp = u >> lhalf, pos = u & (half - 1);
-      uint64_t* x = a + (v << logn) + (grp << (lhalf + 2));
+      uint64_t* x = a + v * stride + (grp << (lhalf + 2));
       const int i0 = pos, i1 = pos + half, i2 = pos + 2 * half, i3 = pos + 3 * half;
       const uint64_t t = __ldg(tw + (pos << ls1));
       const uint64_t a0 = x[i0], a1 = d_mul(x[i1], t), a2 = x[i2], a3 = d_mul(x[i3], t);
@@ -162,7 +163,7 @@ __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len,
     const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
-  ntt_dif(sh, n, vpb, tw);
+  ntt_dif(sh, n, vpb, tw, n);
   for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
     const int v = e >> logn, i = e & (n - 1);
     dst[(p0 + v) * dst_pitch + i] = sh[e];
@@ -184,7 +185,7 @@ __global__ void k_ntt_mul_inv_small(const uint64_t* prod, int64_t pitch, const u
     const int v = e >> logn, i = e & (n - 1);
     sh[e] = v < cnt ? d_mul(prod[(p0 + v) * pitch + i], fb[(p0 + v) * fb_pitch + i]) : 0;
   }
-  ntt_dit(sh, n, vpb, twi);
+  ntt_dit(sh, n, vpb, twi, n);
   store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
@@ -204,12 +205,12 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
     const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
-  ntt_dif(sh, n, vpb, tw);
+  ntt_dif(sh, n, vpb, tw, n);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
     const int v = e >> logn, i = e & (n - 1);
     if (v < cnt) sh[e] = d_mul(sh[e], fb[(p0 + v) * fb_pitch + i]);
   }
-  ntt_dit(sh, n, vpb, twi);
+  ntt_dit(sh, n, vpb, twi, n);
   store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
@@ -220,7 +221,8 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
 __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch, int R,
                            int C, int TC, int logR, const uint64_t* twR, const uint64_t* twn, int inverse,
                            uint64_t scale, int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
-  extern __shared__ uint64_t sh[];  // [TC][R]
+  extern __shared__ uint64_t sh[];  // [TC][R + 1]: the padding spreads a transposed row over the banks
+  const int RS = R + 1;
   const int tiles = C / TC;
   const int64_t pr = blockIdx.x / tiles;
   const int c0 = (blockIdx.x % tiles) * TC;
@@ -235,14 +237,14 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
       const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
       v = d_mul(v, __ldg(twn + ((n - ex) & mask)));
     }
-    sh[c * R + r] = v;
+    sh[c * RS + r] = v;
   }
-  if (inverse) ntt_dit(sh, R, TC, twR);
-  else ntt_dif(sh, R, TC, twR);
+  if (inverse) ntt_dit(sh, R, TC, twR, RS);
+  else ntt_dif(sh, R, TC, twR, RS);
   for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
     const int r = e >> lTC, c = e & (TC - 1);
     const int idx = r * C + c0 + c;
-    uint64_t v = sh[c * R + r];
+    uint64_t v = sh[c * RS + r];
     if (!inverse) {
       const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
       dst[pr * dst_pitch + idx] = d_mul(v, __ldg(twn + ex));
@@ -267,8 +269,8 @@ __global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, int vpb,
   uint64_t* rows = data + pr * pitch + (int64_t)r0 * C;
   const uint64_t* frows = fb ? fb + pr * fb_pitch + (int64_t)r0 * C : nullptr;
   for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = frows ? d_mul(rows[e], frows[e]) : rows[e];
-  if (inverse) ntt_dit(sh, C, vpb, twC);
-  else ntt_dif(sh, C, vpb, twC);
+  if (inverse) ntt_dit(sh, C, vpb, twC, C);
+  else ntt_dif(sh, C, vpb, twC, C);
   for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) rows[e] = sh[e];
 }
 
@@ -458,7 +460,7 @@ struct Composer {
       auto wR = twiddles(R);
       auto wC = twiddles(C);
       auto wn = twiddles(n);
-      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)R * TC * 8, st>>>(
+      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
           (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, ilog2(R), wR.first,
           wn.first, 0, 1, 0, 0, nullptr, 0);
       const int vpb = kNttSmemMax / C;
@@ -490,7 +492,7 @@ struct Composer {
       const int vpb = kNttSmemMax / C;
       k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
           (uint64_t*)fa.ptr, fa.pitch, R, C, vpb, wC.second, 1, (const uint64_t*)fbuf.ptr, fbuf.pitch);
-      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)R * TC * 8, st>>>(
+      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
           (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, ilog2(R), wR.second,
           wn.first, 1, ninv, outlen, mode, init, init_pitch);
     }
