@@ -40,6 +40,10 @@ SEED = 1000  # configuration index x 1000
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = 2 * SM_COUNT * SM_MAX_MHZ * 1e6 * 2 / 1e12
+FP64_DFMA_GPS = FP64_PEAK_TFLOPS * 1e3 / 2  # 629 G DFMA/s
+# Goldilocks multiply-add-reduce, measured on GB300 (dependent chains, 8 per
+# thread, 1216 blocks of 256 threads, 1987 MHz): the MODP roofline
+MODP_MULADD_GPS = 671.0
 
 CPU_SAMPLE_POINTS = 1 << 18  # points per evaluation in the CPU-oracle sample
 
@@ -402,6 +406,70 @@ def _timed(fn, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
+def compose_work(t, degq, modp):
+    """Algorithmic operations of one batched composition per pair, following
+    the walk's products as the library sizes them: MODP counts modular
+    multiplications (radix-2 count (n/2) log2 n per transform of length n,
+    plus pointwise products, scaling by 1/n, the four-step twiddles and
+    leaf scalings); FP64 counts the multiply-adds of the direct convolutions."""
+    import math
+    ex = t.export()
+    n_nodes = len(ex["parent"])
+    e = ex["node_e"][:, 0].astype(np.int64)
+    par, pd = ex["parent"], ex["pd"]
+    maxe = e.copy()
+    for i in range(n_nodes - 1):
+        maxe[par[i]] = max(maxe[par[i]], maxe[i])
+    degval = (maxe - e) * degq
+    has_child = np.zeros(n_nodes, dtype=bool)
+    has_child[par[:-1]] = True
+    # powers q^d: closure of the edge degrees under d -> d/2 (even), d-1 (odd)
+    need = set(int(d) for d in pd[:-1] if d > 0)
+    if pd[-1] > 0:
+        need.add(int(pd[-1]))
+    stack = list(need)
+    while stack:
+        d = stack.pop()
+        if d > 1:
+            m = d // 2 if d % 2 == 0 else d - 1
+            if m not in need:
+                need.add(m)
+                stack.append(m)
+    cached = set()
+    total = 0
+
+    def ntt(n):
+        return (n // 2) * int(math.log2(n)) + (n if n > 4096 else 0)  # four-step twiddles
+
+    def product(alen, blen, bkey):
+        nonlocal total
+        rl = alen + blen - 1
+        if not modp:
+            total += alen * blen
+            return
+        n = 1 << max(0, (rl - 1).bit_length())
+        total += ntt(n)                      # forward transform of A
+        if (bkey, n) not in cached:          # transform of q^d, once per length
+            cached.add((bkey, n))
+            total += ntt(n)
+        total += n + ntt(n) + rl             # pointwise, inverse, scaling
+
+    for d in sorted(need):
+        if d == 1:
+            continue
+        if d % 2 == 0:
+            product((d // 2) * degq + 1, (d // 2) * degq + 1, d // 2)
+        else:
+            product((d - 1) * degq + 1, degq + 1, 1)
+    for i in range(n_nodes - 1):
+        qlen = int(pd[i]) * degq + 1
+        if has_child[i]:
+            product(int(degval[i]) + 1, qlen, int(pd[i]))
+        elif modp:
+            total += qlen                    # leaf: c * q^d
+    return total
+
+
 def run_compose(args):
     """Batched composition: 4096 pairs, deg p = 512, deg q = 64 (E and B
     schemes; MODP exact by NTT, FP64 by direct convolution)."""
@@ -427,8 +495,14 @@ def run_compose(args):
                                modp=dt == "modp")
             steps = args.steps if dt == "modp" else 1
             ms = _timed(lambda: fpl.fp_compose(t, dt, dq, pcoeffs=dp, out=out), steps, 1 if dt == "f64" else args.warmup)
+            work = compose_work(t, degq, dt == "modp") * npairs
+            rate = work / (ms * 1e-3) / 1e9
             res["%s/%s" % (dt, s)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
-                                      "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3)}
+                                      "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3),
+                                      "roofline": {"unit": "G mulmod/s" if dt == "modp" else "G DFMA/s",
+                                                   "algorithmic_ops": work, "achieved": rate,
+                                                   "peak": MODP_MULADD_GPS if dt == "modp" else FP64_DFMA_GPS,
+                                                   "frac": rate / (MODP_MULADD_GPS if dt == "modp" else FP64_DFMA_GPS)}}
     line = {"metric": "compositions/s", "workload": "batched composition, %d pairs, deg p %d, deg q %d" %
             (npairs, degp, degq), "results": res, "n_gpus": 1, "data": "synthetic"}
     print(json.dumps(line))
