@@ -337,6 +337,38 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
 int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q,
                        int32_t degq, int64_t npairs, void* out, void* stream);
 
+/* fp_measure_rates -- sustained arithmetic rates of this GPU for the
+ * operations the evaluation kernels are bound by: the roofline denominators
+ * (no counterpart in the paper).  Each rate is measured with the library's
+ * own arithmetic, 8 independent dependent chains per thread, 8 blocks of 256
+ * threads per SM, one warm-up launch, then 3 launches timed with CUDA events
+ * on `stream` (synchronous; a few tens of ms per rate).  rates[i], in G
+ * operations per second, for i < nrates (at most FP_RATE_COUNT):
+ *   FP_RATE_DFMA         FP64 fused multiply-add (one FP64 node of the walk)
+ *   FP_RATE_DADD_RD      FP64 add rounded down
+ *   FP_RATE_DMUL_RU      FP64 multiply rounded up
+ *   FP_RATE_FFMA         FP32 fused multiply-add
+ *   FP_RATE_F32C_MAD     compensated FP32 multiply-add, general form (one
+ *                        FP32C node with no operand known exact)
+ *   FP_RATE_F32C_HORNER  the same with a coefficient added and x a point
+ *                        (exact zero low parts dropped: a Horner step)
+ *   FP_RATE_MODP_MULADD  (a b + c) mod p (one MODP node)
+ * An interval node is 2 additions, 2 products and 2 additions with directed
+ * rounding: its bound is FP_RATE_DADD_RD / 6 (the products issue at the same
+ * rate as the additions). 
+ * Errors: FP_E_BAD_VALUE (NULL rates, negative nrates), FP_E_NOMEM, FP_E_CUDA. */
+enum {
+  FP_RATE_DFMA = 0,
+  FP_RATE_DADD_RD = 1,
+  FP_RATE_DMUL_RU = 2,
+  FP_RATE_FFMA = 3,
+  FP_RATE_F32C_MAD = 4,
+  FP_RATE_F32C_HORNER = 5,
+  FP_RATE_MODP_MULADD = 6,
+  FP_RATE_COUNT = 7
+};
+int fp_measure_rates(double* rates, int nrates, void* stream);
+
 /* fp_eval_plain_f64 -- the comparison baseline: one launch per polynomial,
  * one thread per point, Horner's rule over the dense coefficient vector
  * coeffs[0..ncoeffs-1] (index = degree), FP64, no tree.  Device pointers. */

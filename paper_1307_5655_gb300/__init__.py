@@ -32,6 +32,7 @@ for _name, _args in {
     "fp_tune": [_P, _I, _P, _I64, _P, _P, _P],
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
+    "fp_measure_rates": [_P, ctypes.c_int, _P],
     "fp_tree_schedule": [_P] * 12,
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
@@ -210,6 +211,17 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
     _check(_lib.fp_eval_ex(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
                            ctypes.byref(cfg)), "fp_eval_ex")
     return out
+
+
+RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd")
+
+
+def fp_measure_rates(stream=None):
+    """Sustained rates (G op/s) of the arithmetic the kernels are bound by,
+    measured on the current device (fp_measure_rates)."""
+    rates = np.zeros(len(RATE_NAMES), dtype=np.float64)
+    _check(_lib.fp_measure_rates(_ptr(rates), len(RATE_NAMES), _stream_handle(stream)), "fp_measure_rates")
+    return dict(zip(RATE_NAMES, rates.tolist()))
 
 
 def fp_tune(tree, dtype, points, out=None, stream=None):

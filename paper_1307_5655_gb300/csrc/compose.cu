@@ -83,43 +83,8 @@ __device__ __forceinline__ uint64_t d_sub(uint64_t a, uint64_t b) {
       : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
   return (uint64_t)r1 << 32 | r0;
 }
-// a b mod p: the 128-bit product lo + 2^64 hi, hi = h1 2^32 + h0, is
-// congruent to lo - h1 + h0 (2^32 - 1) (2^96 = -1, 2^64 = 2^32 - 1).
-//   t = lo - h1, less 2^32 - 1 on a borrow (then t >= 2^32);
-//   u = h0 (2^32 - 1) = h0 2^32 - h0;
-//   r = t + u, and on a carry (true value r + 2^64) add 2^32 - 1, which
-//   cannot carry again (r < (2^32 - 1)^2 there); finally one conditional
-//   subtraction of p as in d_add.
-__device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) {
-  const uint64_t lo = a * b, hi = __umul64hi(a, b);
-  uint32_t r0, r1;
-  asm("{\n\t"
-      ".reg .u32 t0, t1, m, u0, u1, s0, s1, c, v0, v1;\n\t"
-      ".reg .pred q;\n\t"
-      "sub.cc.u32 t0, %2, %5;\n\t"
-      "subc.cc.u32 t1, %3, 0;\n\t"
-      "subc.u32 m, 0, 0;\n\t"
-      "sub.cc.u32 t0, t0, m;\n\t"
-      "subc.u32 t1, t1, 0;\n\t"
-      "sub.cc.u32 u0, 0, %4;\n\t"
-      "subc.u32 u1, %4, 0;\n\t"
-      "add.cc.u32 s0, t0, u0;\n\t"
-      "addc.cc.u32 s1, t1, u1;\n\t"
-      "addc.u32 c, 0, 0;\n\t"
-      "neg.s32 m, c;\n\t"
-      "add.cc.u32 s0, s0, m;\n\t"
-      "addc.u32 s1, s1, 0;\n\t"
-      "add.cc.u32 v0, s0, 0xFFFFFFFF;\n\t"
-      "addc.cc.u32 v1, s1, 0;\n\t"
-      "addc.u32 c, 0, 0;\n\t"
-      "setp.ne.u32 q, c, 0;\n\t"
-      "selp.u32 %0, v0, s0, q;\n\t"
-      "selp.u32 %1, v1, s1, q;\n\t"
-      "}"
-      : "=r"(r0), "=r"(r1)
-      : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi), "r"((uint32_t)(hi >> 32)));
-  return (uint64_t)r1 << 32 | r0;
-}
+// a b mod p: the 128-bit product reduced by the carry-chain reduction
+__device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP::reduce(a * b, __umul64hi(a, b)); }
 
 // Transforms of `count` vectors of length n held one after the other in
 // shared memory, all in lock step.  Forward: decimation in frequency, natural

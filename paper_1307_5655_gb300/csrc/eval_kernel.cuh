@@ -185,18 +185,42 @@ struct MODP {
   using pw = uint64_t;
   static constexpr uint64_t P = 0xFFFFFFFF00000001ull;
   static __device__ __forceinline__ coef coef_from_bits(uint64_t b) { return b; }
+  // lo + 2^64 hi mod p, hi = h1 2^32 + h0: congruent to lo - h1 + h0 (2^32 - 1)
+  // (2^96 = -1, 2^64 = 2^32 - 1), on 32-bit halves with the carry flag:
+  //   t = lo - h1, less 2^32 - 1 on a borrow (then t >= 2^32);
+  //   u = h0 (2^32 - 1) = h0 2^32 - h0;
+  //   r = t + u, plus 2^32 - 1 on a carry (r < (2^32 - 1)^2 there: no second
+  //   carry); r + (2^32 - 1) carries out exactly when r >= p, and then equals r - p.
   static __device__ __forceinline__ uint64_t reduce(uint64_t lo, uint64_t hi) {
-    const uint64_t hh = hi >> 32, hl = hi & 0xFFFFFFFFull;
-    uint64_t t0 = lo - hh;
-    if (lo < hh) t0 -= 0xFFFFFFFFull;           // borrow of 2^64 == 2^32 - 1
-    const uint64_t t1 = (hl << 32) - hl;        // hl * (2^32 - 1)
-    uint64_t r = t0 + t1;
-    if (r < t1) r += 0xFFFFFFFFull;             // carry of 2^64
-    if (r >= P) r -= P;
-    return r;
+    uint32_t r0, r1;
+    asm("{\n\t"
+        ".reg .u32 t0, t1, m, u0, u1, s0, s1, c, v0, v1;\n\t"
+        ".reg .pred q;\n\t"
+        "sub.cc.u32 t0, %2, %5;\n\t"
+        "subc.cc.u32 t1, %3, 0;\n\t"
+        "subc.u32 m, 0, 0;\n\t"
+        "sub.cc.u32 t0, t0, m;\n\t"
+        "subc.u32 t1, t1, 0;\n\t"
+        "sub.cc.u32 u0, 0, %4;\n\t"
+        "subc.u32 u1, %4, 0;\n\t"
+        "add.cc.u32 s0, t0, u0;\n\t"
+        "addc.cc.u32 s1, t1, u1;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "neg.s32 m, c;\n\t"
+        "add.cc.u32 s0, s0, m;\n\t"
+        "addc.u32 s1, s1, 0;\n\t"
+        "add.cc.u32 v0, s0, 0xFFFFFFFF;\n\t"
+        "addc.cc.u32 v1, s1, 0;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "setp.ne.u32 q, c, 0;\n\t"
+        "selp.u32 %0, v0, s0, q;\n\t"
+        "selp.u32 %1, v1, s1, q;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1)
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi), "r"((uint32_t)(hi >> 32)));
+    return (uint64_t)r1 << 32 | r0;
   }
-  // (a b + c) mod p from the 128-bit product (a carry-chain version on 32-bit
-  // limbs measured no faster than the compiler's 64-bit multiply)
+  // (a b + c) mod p from the 128-bit product (a b + c < 2^128: no overflow)
   static __device__ __forceinline__ uint64_t mul_add(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t lo = a * b;
     uint64_t hi = __umul64hi(a, b);
