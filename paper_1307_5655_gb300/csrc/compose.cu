@@ -419,6 +419,25 @@ struct Composer {
   // of being allocated (fp_compose_noalloc)
   unsigned char* arena = nullptr;
   size_t arena_cap = 0, arena_used = 0;
+  int sms = 0;  // multiprocessors of the current device
+
+  // vectors of length n <= 4096 per block of an in-shared-memory transform:
+  // as many as fill 4096 elements, fewer when that would leave the device
+  // with under two blocks per multiprocessor (short transforms of few pairs)
+  int small_vpb(int n) {
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 1;
+      }
+    }
+    int vpb = kNttSmemMax / n;
+    while (vpb > 1 && (npairs + vpb - 1) / vpb < 2 * (int64_t)sms) vpb >>= 1;
+    return vpb;
+  }
+  // threads of such a block: one per radix-4 butterfly, 32 to 256
+  static int small_threads(int vpb, int n) { return std::max(32, std::min(256, vpb * n / 4)); }
 
   void* alloc(size_t bytes) {
     void* p = nullptr;
@@ -486,8 +505,8 @@ struct Composer {
     if (status != FP_OK) return;
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
-      const int vpb = kNttSmemMax / n;
-      k_ntt_fwd_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+      const int vpb = small_vpb(n);
+      k_ntt_fwd_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
           (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, n, vpb, npairs, w.first);
     } else {
       int R, C;
@@ -514,8 +533,8 @@ struct Composer {
     const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
-      const int vpb = kNttSmemMax / n;
-      k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+      const int vpb = small_vpb(n);
+      k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
           (const uint64_t*)fa.ptr, fa.pitch, (const uint64_t*)fbuf.ptr, fbuf.pitch, n, vpb, npairs, w.second, ninv,
           (uint64_t*)out.ptr, out.pitch, outlen, mode, init, init_pitch);
     } else {
@@ -635,9 +654,9 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
         const Buf fb = qhat_of(bk, n);
         if (cm.status != FP_OK) return;
         auto w = cm.twiddles(n);
-        const int vpb = kNttSmemMax / n;
+        const int vpb = cm.small_vpb(n);
         const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
-        k_ntt_product_small<<<(unsigned)((npairs + vpb - 1) / vpb), 256, (size_t)vpb * n * 8, st>>>(
+        k_ntt_product_small<<<(unsigned)((npairs + vpb - 1) / vpb), cm.small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
             (const uint64_t*)A.ptr, A.pitch, (int)alen, (const uint64_t*)fb.ptr, fb.pitch, n, vpb, npairs, w.first,
             w.second, ninv, (uint64_t*)dst.ptr, dst.pitch, (int)rl, mode, (const uint64_t*)init, init_pitch);
         cm.check();
