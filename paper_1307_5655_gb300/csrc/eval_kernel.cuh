@@ -81,7 +81,6 @@ struct F64 {
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return fma(s, xd, init); }
-  static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return __dmul_rn(r, xd); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((double*)out)[idx] = r; }
@@ -246,13 +245,6 @@ struct MODP {
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return mul_add(s, xd, init); }
-  // a + b for residues a, b < p (2^64 == 2^32 - 1 on a carry)
-  static __device__ __forceinline__ val add(val a, val b) {
-    uint64_t r = a + b;
-    if (r < a) r += 0xFFFFFFFFull;
-    if (r >= P) r -= P;
-    return r;
-  }
   static __device__ __forceinline__ val root(bool leaf, coef c, const val* acc) { return leaf ? c : *acc; }
   static __device__ __forceinline__ val apply_root_power(val r, pw xd) { return mul_add(r, xd, 0); }
   static __device__ __forceinline__ void store(void* out, int64_t idx, int64_t, val r) { ((uint64_t*)out)[idx] = r; }
