@@ -405,10 +405,12 @@ def _timed(fn, steps, warmup):
 
 def compose_work(t, degq, modp):
     """Algorithmic operations of one batched composition per pair, following
-    the walk's products as the library sizes them: MODP counts modular
-    multiplications (radix-2 count (n/2) log2 n per transform of length n,
-    plus pointwise products, scaling by 1/n, the four-step twiddles and
-    leaf scalings); FP64 counts the multiply-adds of the direct convolutions."""
+    the walk's products as the library sizes them.  MODP: (butterflies,
+    multiplications) -- a transform of length n is (n/2) log2 n radix-2
+    butterflies (one multiplication, one addition, one subtraction each);
+    pointwise products, scaling by 1/n, four-step twiddles and leaf scalings
+    are single multiplications.  FP64: (0, multiply-adds of the direct
+    convolutions)."""
     import math
     ex = t.export()
     n_nodes = len(ex["parent"])
@@ -433,23 +435,27 @@ def compose_work(t, degq, modp):
                 need.add(m)
                 stack.append(m)
     cached = set()
-    total = 0
+    bfly, mul = 0, 0
 
     def ntt(n):
-        return (n // 2) * int(math.log2(n)) + (n if n > 4096 else 0)  # four-step twiddles
+        nonlocal bfly, mul
+        bfly += (n // 2) * int(math.log2(n))
+        if n > 4096:
+            mul += n  # four-step twiddles
 
     def product(alen, blen, bkey):
-        nonlocal total
+        nonlocal mul
         rl = alen + blen - 1
         if not modp:
-            total += alen * blen
+            mul += alen * blen
             return
         n = 1 << max(0, (rl - 1).bit_length())
-        total += ntt(n)                      # forward transform of A
+        ntt(n)                               # forward transform of A
         if (bkey, n) not in cached:          # transform of q^d, once per length
             cached.add((bkey, n))
-            total += ntt(n)
-        total += n + ntt(n) + rl             # pointwise, inverse, scaling
+            ntt(n)
+        mul += n + rl                        # pointwise, scaling
+        ntt(n)                               # inverse
 
     for d in sorted(need):
         if d == 1:
@@ -463,8 +469,8 @@ def compose_work(t, degq, modp):
         if has_child[i]:
             product(int(degval[i]) + 1, qlen, int(pd[i]))
         elif modp:
-            total += qlen                    # leaf: c * q^d
-    return total
+            mul += qlen                      # leaf: c * q^d
+    return bfly, mul
 
 
 def run_compose(args):
@@ -476,9 +482,10 @@ def run_compose(args):
     torch.cuda.set_device(0)
     npairs, degp, degq = args.pairs, 512, 64
     res = {}
-    # the mod-p roofline: (a b + c) mod p as the library computes it, measured
-    # on this GPU (fp_measure_rates); FP64: 2 DFMA per clock per SM
-    modp_peak = fpl.fp_measure_rates()["modp_muladd"]
+    # the mod-p roofline: butterflies and multiplications mod p as the library
+    # computes them, measured on this GPU (fp_measure_rates); FP64: 2 DFMA per
+    # clock per SM
+    rates = fpl.fp_measure_rates()
     for dt in args.compose_dtypes.split(","):
         pc, qc = W.composition_case(npairs, degp, degq, 4000, dt)
         e = W.dense_univariate_exps(degp + 1)
@@ -495,16 +502,20 @@ def run_compose(args):
                                modp=dt == "modp")
             steps = args.steps if dt == "modp" else 1
             ms = _timed(lambda: fpl.fp_compose(t, dt, dq, pcoeffs=dp, out=out), steps, 1 if dt == "f64" else args.warmup)
-            work = compose_work(t, degq, dt == "modp") * npairs
-            rate = work / (ms * 1e-3) / 1e9
+            bfly, mul = compose_work(t, degq, dt == "modp")
+            if dt == "modp":
+                roof_ms = npairs * (bfly / rates["modp_butterfly"] + mul / rates["modp_muladd"]) / 1e6
+                roof = {"unit": "ms", "butterflies": bfly * npairs, "multiplications": mul * npairs,
+                        "butterfly_rate_G_per_s": rates["modp_butterfly"], "mulmod_rate_G_per_s": rates["modp_muladd"],
+                        "basis": "measured (fp_measure_rates)"}
+            else:
+                roof_ms = npairs * mul / FP64_DFMA_GPS / 1e6
+                roof = {"unit": "ms", "multiply_adds": mul * npairs, "dfma_rate_G_per_s": FP64_DFMA_GPS,
+                        "basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
+            roof.update({"time_roof": roof_ms, "time_measured": ms, "frac": roof_ms / ms})
             res["%s/%s" % (dt, s)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
                                       "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3),
-                                      "roofline": {"unit": "G mulmod/s" if dt == "modp" else "G DFMA/s",
-                                                   "algorithmic_ops": work, "achieved": rate,
-                                                   "peak": modp_peak if dt == "modp" else FP64_DFMA_GPS,
-                                                   "peak_basis": "measured (fp_measure_rates)" if dt == "modp" else
-                                                   "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
-                                                   "frac": rate / (modp_peak if dt == "modp" else FP64_DFMA_GPS)}}
+                                      "roofline": roof}
     line = {"metric": "compositions/s", "workload": "batched composition, %d pairs, deg p %d, deg q %d" %
             (npairs, degp, degq), "results": res, "n_gpus": 1, "data": "synthetic"}
     print(json.dumps(line))

@@ -353,6 +353,8 @@ int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, co
  *   FP_RATE_F32C_HORNER  the same with a coefficient added and x a point
  *                        (exact zero low parts dropped: a Horner step)
  *   FP_RATE_MODP_MULADD  (a b + c) mod p (one MODP node)
+ *   FP_RATE_MODP_BUTTERFLY  (a, b) -> (a + w b, a - w b) mod p (one radix-2
+ *                        butterfly of the number-theoretic transforms)
  * An interval node is 2 additions, 2 products and 2 additions with directed
  * rounding: its bound is FP_RATE_DADD_RD / 6 (the products issue at the same
  * rate as the additions). 
@@ -365,7 +367,8 @@ enum {
   FP_RATE_F32C_MAD = 4,
   FP_RATE_F32C_HORNER = 5,
   FP_RATE_MODP_MULADD = 6,
-  FP_RATE_COUNT = 7
+  FP_RATE_MODP_BUTTERFLY = 7,
+  FP_RATE_COUNT = 8
 };
 int fp_measure_rates(double* rates, int nrates, void* stream);
 

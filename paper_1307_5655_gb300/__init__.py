@@ -213,7 +213,7 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
     return out
 
 
-RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd")
+RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd", "modp_butterfly")
 
 
 def fp_measure_rates(stream=None):

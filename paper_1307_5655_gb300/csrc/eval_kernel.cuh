@@ -219,6 +219,44 @@ struct MODP {
         : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi), "r"((uint32_t)(hi >> 32)));
     return (uint64_t)r1 << 32 | r0;
   }
+  // (a + b) mod p for a, b < p: s = a + b (carry c); s + (2^32 - 1) carries
+  // out exactly when s >= p, and then equals s - p; with c set the true sum is
+  // s + 2^64, which is congruent to s + 2^32 - 1 < p.
+  static __device__ __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
+    uint32_t r0, r1;
+    asm("{\n\t"
+        ".reg .u32 s0, s1, t0, t1, c;\n\t"
+        ".reg .pred q;\n\t"
+        "add.cc.u32 s0, %2, %4;\n\t"
+        "addc.cc.u32 s1, %3, %5;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "add.cc.u32 t0, s0, 0xFFFFFFFF;\n\t"
+        "addc.cc.u32 t1, s1, 0;\n\t"
+        "addc.u32 c, c, 0;\n\t"
+        "setp.ne.u32 q, c, 0;\n\t"
+        "selp.u32 %0, t0, s0, q;\n\t"
+        "selp.u32 %1, t1, s1, q;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
+    return (uint64_t)r1 << 32 | r0;
+  }
+  // (a - b) mod p for a, b < p: on a borrow, d = a - b + 2^64 >= 2^32, and
+  // a - b + p = d - (2^32 - 1).
+  static __device__ __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
+    uint32_t r0, r1;
+    asm("{\n\t"
+        ".reg .u32 d0, d1, m;\n\t"
+        "sub.cc.u32 d0, %2, %4;\n\t"
+        "subc.cc.u32 d1, %3, %5;\n\t"
+        "subc.u32 m, 0, 0;\n\t"
+        "sub.cc.u32 %0, d0, m;\n\t"
+        "subc.u32 %1, d1, 0;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
+    return (uint64_t)r1 << 32 | r0;
+  }
   // (a b + c) mod p from the 128-bit product (a b + c < 2^128: no overflow)
   static __device__ __forceinline__ uint64_t mul_add(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t lo = a * b;

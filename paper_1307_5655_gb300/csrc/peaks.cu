@@ -62,6 +62,21 @@ struct OpF32cHorner {  // Horner's step: coefficient added, x a loaded FP32 poin
   }
   static __device__ double out(T a) { return (double)a.x + a.y; }
 };
+// one radix-2 butterfly mod p per step, on a pair: (a, b) -> (a + w b, a - w b)
+// (the transforms' arithmetic: MODP::reduce, MODP::add, MODP::sub)
+struct ModpPair {
+  uint64_t a, b;
+};
+struct OpModpButterfly {
+  using T = ModpPair;
+  static __device__ T init(const Params& q, int j) { return ModpPair{q.u[0] + j + threadIdx.x, q.u[0] + 7 * j}; }
+  static __device__ T step(const Params& q, T v) {
+    const uint64_t t = MODP::reduce(v.b * q.u[1], __umul64hi(v.b, q.u[1]));
+    return ModpPair{MODP::add(v.a, t), MODP::sub(v.a, t)};
+  }
+  static __device__ double out(T v) { return (double)(v.a ^ v.b); }
+};
+
 struct OpModpMulAdd {
   using T = uint64_t;
   static __device__ T init(const Params& q, int j) { return q.u[0] + j + threadIdx.x; }
@@ -144,6 +159,7 @@ extern "C" int fp_measure_rates(double* rates, int nrates, void* stream) {
       case FP_RATE_F32C_MAD: rc = time_rate<OpF32cMad>(prm, out, blocks, 8192, st, g); break;
       case FP_RATE_F32C_HORNER: rc = time_rate<OpF32cHorner>(prm, out, blocks, 8192, st, g); break;
       case FP_RATE_MODP_MULADD: rc = time_rate<OpModpMulAdd>(prm, out, blocks, 2048, st, g); break;
+      case FP_RATE_MODP_BUTTERFLY: rc = time_rate<OpModpButterfly>(prm, out, blocks, 2048, st, g); break;
       default: break;
     }
     rates[i] = g;
