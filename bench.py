@@ -759,7 +759,7 @@ def run_hybrid(args):
     d32 = torch.from_numpy(W.to_f32(x)).cuda()
     e, c, _ = W.univariate_case(k, 1, SEED + k)
     res = {}
-    variants = [("H", None), ("E", None), ("B", None)]
+    variants = [("H", None), ("E", None), ("B", None), ("D", None)]
     for k0 in (4, 8, 16, 32, 64, 128, 512):
         ft = np.ones(k + 1, dtype=np.int32)
         for n in range(1, k + 1):
@@ -771,7 +771,17 @@ def run_hybrid(args):
             fpl.fp_tune(t, dt, d[:, : 1 << 20].contiguous())
             ms = _timed(lambda: fpl.fp_eval(t, dt, d), 3, 1)
             res["%s/%s" % (dt, name)] = {"ms": ms, "G_term_evals_per_s": k * NPTS / (ms * 1e6)}
-    print(json.dumps({"metric": "G term-evals/s", "workload": "k = 10007, 2^24 points", "results": res}))
+    # the scheme autotuner (fp_tune_scheme) on a 2^20-point sample, then the
+    # chosen tree timed at full size
+    chosen = {}
+    for dt, d in (("f64", d64), ("f32c", d32)):
+        t, k0 = fpl.fp_tune_scheme(e, c, dt, d[:, : 1 << 20].contiguous())
+        ms = _timed(lambda: fpl.fp_eval(t, dt, d), 3, 1)
+        chosen[dt] = {"k0": k0, "meaning": "Balanced" if k0 == 0 else ("Horner" if k0 >= k else "Estrin above k0 terms"),
+                      "ms": ms, "G_term_evals_per_s": k * NPTS / (ms * 1e6)}
+        t.free()
+    print(json.dumps({"metric": "G term-evals/s", "workload": "k = 10007, 2^24 points", "results": res,
+                      "fp_tune_scheme": chosen}))
 
 
 def main():

@@ -130,10 +130,11 @@ int fp_eval(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, 
 /* Launch configuration for fp_eval_ex.
  *   kernel  0: automatic;
  *           1: grouped ops -- chains of single-child nodes run as a register
- *              loop and dense subtrees of <= 16 terms (univariate, schemes E
- *              and B) by a compiled template of the scheme's split; FP64,
- *              FP32C and MODP only, power table in shared memory (else
- *              FP_E_TOO_LARGE);
+ *              loop; under schemes E and B, dense runs of <= 16 terms of the
+ *              innermost variable (whole subtrees, or a node with its last
+ *              children) by a compiled template of the scheme's split (MODP:
+ *              Horner's rule over the run, the same residue); FP64, FP32C and
+ *              MODP only, power table in shared memory (else FP_E_TOO_LARGE);
  *           2: node by node (any tree and value type).
  * MODP results are identical for every configuration; FP64 and FP32C results
  * of configuration 1 may differ in the last bits (another summation order
@@ -159,6 +160,22 @@ int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npt
  * `stream`; writes the choice to *best when non-NULL. */
 int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
             fp_launch_cfg* best);
+
+/* fp_tune_scheme -- compile a polynomial under the function scheme that
+ * evaluates it fastest on the given points.  Candidates: the combined scheme
+ * of the Remark of Sec. 1.1 -- Estrin's split f(n) = 2^floor(log2 n) for runs
+ * of more than k0 terms, Horner's f(n) = 1 below -- for k0 = 1 (Estrin
+ * everywhere), 2, 4, ..., the first power of two >= nterms (Horner
+ * everywhere), and the Balanced scheme; each compiled and tuned as fp_tune
+ * does, the fastest kept and the others freed.
+ *   nvars ... coeff_type: as fp_compile.   dtype, points, npts, out, stream:
+ *   as fp_tune (`out` holds the winner's result).
+ *   k0_out (may be NULL): the chosen k0, 0 for the Balanced scheme.
+ *   tree_out: the chosen tree, compiled and tuned; the caller frees it.
+ * Synchronous.  Errors: those of fp_compile (invalid terms) and fp_tune. */
+int fp_tune_scheme(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
+                   fp_dtype coeff_type, fp_dtype dtype, const void* points, int64_t npts,
+                   void* out, void* stream, int64_t* k0_out, fp_tree** tree_out);
 
 /* fp_eval_host -- the same as fp_eval with host buffers: copies the points to
  * the device, evaluates, copies the result back and synchronises `stream`.

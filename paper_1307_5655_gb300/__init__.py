@@ -33,6 +33,7 @@ for _name, _args in {
     "fp_tree_info": [_P, _P, _P, _P, _P, _P],
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_measure_rates": [_P, ctypes.c_int, _P],
+    "fp_tune_scheme": [ctypes.c_int, _I64, _P, _P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _P, _P, _P],
     "fp_tree_schedule": [_P] * 12,
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
@@ -222,6 +223,27 @@ def fp_measure_rates(stream=None):
     rates = np.zeros(len(RATE_NAMES), dtype=np.float64)
     _check(_lib.fp_measure_rates(_ptr(rates), len(RATE_NAMES), _stream_handle(stream)), "fp_measure_rates")
     return dict(zip(RATE_NAMES, rates.tolist()))
+
+
+def fp_tune_scheme(exps, coeffs, dtype, points, out=None, stream=None, modp=False):
+    """Compile under the fastest combined Estrin/Horner threshold k0 (or the
+    Balanced scheme) for these points (fp_tune_scheme); returns (tree, k0),
+    k0 = 0 meaning Balanced."""
+    import torch
+    e = np.ascontiguousarray(exps, dtype=np.int32)
+    if e.ndim == 1:
+        e = e.reshape(-1, 1)
+    nterms, nvars = e.shape
+    c = np.ascontiguousarray(coeffs, dtype=np.uint64 if modp else np.float64)
+    npts = points.shape[-1]
+    if out is None:
+        out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    h = ctypes.c_void_p()
+    k0 = ctypes.c_int64()
+    _check(_lib.fp_tune_scheme(nvars, nterms, _ptr(e), _ptr(c), DTYPES["modp"] if modp else DTYPES["f64"],
+                               DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
+                               ctypes.byref(k0), ctypes.byref(h)), "fp_tune_scheme")
+    return Tree(h.value, nvars, "modp" if modp else "f64"), k0.value
 
 
 def fp_tune(tree, dtype, points, out=None, stream=None):

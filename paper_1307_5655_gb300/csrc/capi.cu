@@ -356,18 +356,20 @@ int fp_eval_ex(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npt
                      cfg ? cfg->points_per_thread : 0);
 }
 
-int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
-            fp_launch_cfg* best) {
-  if (!t || npts <= 0 || !points || !out) return FP_E_BAD_VALUE;
-  if (!dtype_ok(t, dtype)) return FP_E_DTYPE;
-  if (t->nnodes == 0) return FP_E_BAD_VALUE;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace fp {
+// Time every launch configuration of one tree on these points (3 runs each
+// after a warm-up); the fastest one's (kernel, points per thread, ms per run).
+int tune_device(const fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, cudaStream_t st,
+                int& bk, int& bp, float& best_ms) {
   const int kernels[2] = {1, 2};
   const int ppts[3] = {1, 2, 4};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { cudaGetLastError(); return FP_E_CUDA; }
-  float best_ms = 1e30f;
-  int bk = 0, bp = 0;
+  best_ms = 1e30f;
+  bk = 0;
+  bp = 0;
   for (int k : kernels) {
     if (k == 1 && dtype == FP_IV64) continue;
     for (int p : ppts) {
@@ -387,6 +389,23 @@ int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (bk == 0) return FP_E_CUDA;
+  best_ms /= 3;
+  return FP_OK;
+}
+}  // namespace fp
+
+extern "C" {
+
+int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream,
+            fp_launch_cfg* best) {
+  if (!t || npts <= 0 || !points || !out) return FP_E_BAD_VALUE;
+  if (!dtype_ok(t, dtype)) return FP_E_DTYPE;
+  if (t->nnodes == 0) return FP_E_BAD_VALUE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int bk = 0, bp = 0;
+  float best_ms = 0;
+  const int trc = tune_device(t, dtype, points, npts, out, st, bk, bp, best_ms);
+  if (trc != FP_OK) return trc;
   t->tuned_kernel[dtype] = bk;
   t->tuned_ppt[dtype] = bp;
   {
@@ -400,6 +419,84 @@ int fp_tune(fp_tree* t, fp_dtype dtype, const void* points, int64_t npts, void* 
     best->points_per_thread = bp;
   }
   return rc;
+}
+
+int fp_tune_scheme(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs, fp_dtype coeff_type,
+                   fp_dtype dtype, const void* points, int64_t npts, void* out, void* stream, int64_t* k0_out,
+                   fp_tree** tree_out) {
+  if (!tree_out || npts <= 0 || !points || !out || nterms < 1) return FP_E_BAD_VALUE;
+  if (nterms > FP_MAX_TERMS) return FP_E_TOO_LARGE;
+  cudaStream_t st = (cudaStream_t)stream;
+  // candidates: k0 = 1, 2, 4, ..., the first power of two >= nterms (Horner
+  // everywhere), then the Balanced scheme (k0 = 0)
+  std::vector<int64_t> k0s;
+  for (int64_t k0 = 1;; k0 <<= 1) {
+    k0s.push_back(k0);
+    if (k0 >= nterms) break;
+  }
+  k0s.push_back(0);
+  std::vector<int32_t> ft;
+  fp_tree* best = nullptr;
+  float best_ms = 1e30f;
+  int64_t best_k0 = -1;
+  int last_rc = FP_OK;
+  for (const int64_t k0 : k0s) {
+    fp_tree* t = nullptr;
+    int rc;
+    if (k0 == 0) {
+      rc = fp_compile(nvars, nterms, exps, coeffs, coeff_type, FP_SCHEME_B, nullptr, 0, &t);
+    } else {
+      // f(n) = 2^floor(log2 n) when the run has more than k0 terms (n + 1 > k0), else 1
+      try {
+        ft.assign((size_t)nterms, 1);
+      } catch (const std::bad_alloc&) {
+        return FP_E_NOMEM;
+      }
+      for (int64_t n = 1; n < nterms; ++n) {
+        int64_t f = 1;
+        if (n + 1 > k0)
+          while ((f << 1) <= n) f <<= 1;
+        ft[(size_t)n] = (int32_t)f;
+      }
+      rc = fp_compile(nvars, nterms, exps, coeffs, coeff_type, FP_SCHEME_CUSTOM, ft.data(), nterms, &t);
+    }
+    if (rc != FP_OK) {  // invalid terms fail every candidate alike
+      if (best) fp_free(best);
+      return rc;
+    }
+    int bk = 0, bp = 0;
+    float ms = 0;
+    rc = dtype_ok(t, dtype) ? (t->nnodes ? tune_device(t, dtype, points, npts, out, st, bk, bp, ms) : FP_OK)
+                            : FP_E_DTYPE;
+    if (rc != FP_OK) {
+      last_rc = rc;
+      fp_free(t);
+      if (rc == FP_E_DTYPE) break;
+      continue;
+    }
+    if (t->nnodes) {
+      t->tuned_kernel[dtype] = bk;
+      t->tuned_ppt[dtype] = bp;
+    }
+    if (!best || ms < best_ms) {
+      if (best) fp_free(best);
+      best = t;
+      best_ms = ms;
+      best_k0 = k0;
+    } else {
+      fp_free(t);
+    }
+  }
+  if (!best) return last_rc != FP_OK ? last_rc : FP_E_CUDA;
+  // the winner's result in `out`
+  const int rc = eval_device(best, dtype, points, npts, out, st);
+  if (rc != FP_OK) {
+    fp_free(best);
+    return rc;
+  }
+  if (k0_out) *k0_out = best_k0;
+  *tree_out = best;
+  return FP_OK;
 }
 
 int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts, void* out_host,

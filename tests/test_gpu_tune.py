@@ -7,6 +7,7 @@ import pytest
 import workloads as W
 import paper_1307_5655_gb300 as fpl
 from gpu_util import device_points
+from test_gpu_eval import check_f32c, check_f64, check_modp
 
 pytestmark = pytest.mark.gpu
 
@@ -60,3 +61,31 @@ def test_tune_choice_is_used(dtype):
     a2 = fpl.fp_eval(t2, dtype, d)
     b2 = fpl.fp_eval_ex(t2, dtype, d, kernel=kern, ppt=ppt)
     assert torch.equal(a2.view(torch.uint8), b2.view(torch.uint8))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32c", "modp"])
+def test_tune_scheme_picks_a_valid_tree(dtype):
+    """fp_tune_scheme returns a tuned tree of one of its candidates (k0 a power
+    of two up to the first one >= k, or 0 for Balanced) whose result, left in
+    `out` and from fp_eval, equals the oracle's (MODP) or meets the bound."""
+    import torch
+    k = 300
+    modp = dtype == "modp"
+    e, c, x = W.univariate_case(k, 4096 + 7, 77, "modp" if modp else "f64")
+    d = device_points(dtype, x)
+    out = torch.empty((4096 + 7,) if dtype != "f32c" else (2, 4096 + 7),
+                      dtype=torch.int64 if modp else (torch.float32 if dtype == "f32c" else torch.float64),
+                      device="cuda")
+    tree, k0 = fpl.fp_tune_scheme(e, c, dtype, d, out=out, modp=modp)
+    assert k0 == 0 or ((k0 & (k0 - 1)) == 0 and 1 <= k0 <= 512)
+    again = fpl.fp_eval(tree, dtype, d)
+    torch.cuda.synchronize()
+    assert torch.equal(out, again)
+    got = out.cpu().numpy()
+    if modp:
+        check_modp(e, c, x, got.view(np.uint64))
+    elif dtype == "f64":
+        check_f64(e, c, x, got)
+    else:
+        check_f32c(e, c, x, got)
+    tree.free()
