@@ -559,6 +559,25 @@ def run_eval_config(args):
             ms = _timed(lambda: fpl.fp_eval(tf, dt, d), 3, 1)
             res["trivariate_deg40_%s_%s_2^22" % (s, dt)] = {"ms": ms, "G_term_evals_per_s": len(ef) * npts / (ms * 1e6),
                                                            "launch": tune}
+    # sparse trivariate: a seeded 30 % of the degree-40 monomials, so groups
+    # miss their lowest terms and the tree carries zero-coefficient virtual
+    # roots (the multivariate reading of the Remark of Sec. 1.1)
+    full = W.total_degree_exps(3, 40)
+    keep = W.rng(303).random(len(full)) < 0.3
+    es = full[keep]
+    for s in ("E", "B"):
+        cs = W.uniform_f64(len(es), 304)
+        xs = W.points_f64(3, npts, 305)
+        ts = fpl.fp_compile(es, cs, s)
+        info = ts.info()
+        ds = torch.from_numpy(xs).cuda()
+        tune = fpl.fp_tune(ts, "f64", ds[:, : 1 << 20].contiguous()) if not args.no_tune else None
+        ms = _timed(lambda: fpl.fp_eval(ts, "f64", ds), 3, 1)
+        res["sparse_trivariate_30pct_%s_f64_2^22" % s] = {
+            "ms": ms, "terms": int(len(es)), "nodes": info["nnodes"],
+            "virtual_nodes": int(info["nnodes"] - len(es)),
+            "G_term_evals_per_s": len(es) * npts / (ms * 1e6),
+            "G_node_evals_per_s": info["nnodes"] * npts / (ms * 1e6), "launch": tune}
     print(json.dumps({"metric": "G term-evals/s", "results": res, "n_gpus": 1, "data": "synthetic"}))
 
 
@@ -744,6 +763,61 @@ def run_peaks(args):
                       "per_node": derived, "clocks": clocks, "n_gpus": 1}))
 
 
+def run_rns(args):
+    """Exact integer evaluation through residues (the paper's multi-precision
+    setting, Sec. 3): dense univariate integer polynomials with random signed
+    coefficients of cbits bits at 2^16 random signed points of xbits bits;
+    as many primes q = 2^64 - c as the values need; the walk modulo every
+    prime in one launch, then the Chinese remainder reconstruction.  The CPU
+    baseline is the oracle's exact integer sum (Python integers) on a sample."""
+    import time
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    from oracle import exact as X
+    torch.cuda.set_device(0)
+    npts = 1 << 16
+    res = {}
+    for deg, cbits, xbits in ((100, 256, 32), (60, 1024, 32), (30, 128, 100), (1000, 64, 3)):
+        k = deg + 1
+        r = W.rng(7000 + deg)
+        coeffs = [int(v) * (1 if r.random() < 0.5 else -1) for v in
+                  (int.from_bytes(r.bytes((cbits + 7) // 8), "little") >> (8 * ((cbits + 7) // 8) - cbits)
+                   for _ in range(k))]
+        xs = [int(v) - (1 << (xbits - 1)) for v in
+              (int.from_bytes(r.bytes((xbits + 7) // 8), "little") >> (8 * ((xbits + 7) // 8) - xbits)
+               for _ in range(npts))]
+        nq = (cbits + deg * xbits + k.bit_length() + 2 + 63) // 64 + 1
+        qs = [int(v) for v in fpl.fp_rns_primes(nq)]
+        e = W.dense_univariate_exps(k)
+        resid = np.array([[c % q for c in coeffs] for q in qs], dtype=np.uint64)
+        pts = np.array([[[x % q for x in xs]] for q in qs], dtype=np.uint64)
+        t = fpl.fp_compile_rns(e, resid, "E")
+        d = torch.from_numpy(pts.view(np.int64)).cuda()
+        out = torch.empty((nq, npts), dtype=torch.int64, device="cuda")
+        limbs = torch.empty((npts, nq), dtype=torch.int64, device="cuda")
+        ms_eval = _timed(lambda: fpl.fp_eval_rns(t, d, out=out), args.steps, args.warmup)
+        ms_crt = _timed(lambda: fpl.fp_crt(out, out=limbs), args.steps, args.warmup)
+        # spot check against the oracle
+        lim = limbs.cpu().numpy().view(np.uint64)
+        for j in (0, npts // 2, npts - 1):
+            assert fpl.limbs_to_int(lim[j]) == X.int_value(e.tolist(), coeffs, (xs[j],))
+        nsample = 64 if deg * xbits <= 4000 else 16
+        t0 = time.perf_counter()
+        for j in range(nsample):
+            X.int_value(e.tolist(), coeffs, (xs[j],))
+        cpu_s = (time.perf_counter() - t0) / nsample
+        total_ms = ms_eval + ms_crt
+        res["deg%d_c%db_x%db" % (deg, cbits, xbits)] = {
+            "primes": nq, "value_bits": nq * 64, "eval_ms": ms_eval, "crt_ms": ms_crt,
+            "bigint_evals_per_s": npts / (total_ms * 1e-3),
+            "G_modular_term_evals_per_s": nq * k * npts / (ms_eval * 1e6),
+            "cpu_oracle_bigint_evals_per_s_1core": 1.0 / cpu_s, "cpu_sample_points": nsample}
+        t.free()
+    print(json.dumps({"metric": "exact big-integer evaluations/s", "points": npts, "scheme": "E",
+                      "results": res, "n_gpus": 1, "data": "synthetic"}))
+
+
 def run_hybrid(args):
     """The paper's combined scheme (Remark of Sec. 1.1): Estrin above k0 terms,
     Horner below, against H, E and B, FP64 and compensated FP32, k = 10007 at
@@ -787,7 +861,7 @@ def run_hybrid(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve", "accuracy",
-                                                                "staircase", "hybrid", "peaks"],
+                                                                "staircase", "hybrid", "peaks", "rns"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=1000)
@@ -824,6 +898,8 @@ def main():
         run_hybrid(args)
     elif args.workload == "peaks":
         run_peaks(args)
+    elif args.workload == "rns":
+        run_rns(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -395,6 +395,43 @@ int fp_measure_rates(double* rates, int nrates, void* stream);
 int fp_eval_plain_f64(const double* coeffs, int64_t ncoeffs, const double* points, int64_t npts,
                       double* out, void* stream);
 
+/*
+ * Exact integer values through residues (a residue number system): the
+ * paper evaluates polynomials with multi-precision integer coefficients at
+ * multi-precision points (Sec. 3); here a value is represented by its
+ * residues modulo k primes q_i = 2^64 - c_i (the k largest primes of that
+ * form with c_i < 2^32, largest first), the walk runs once per prime, and
+ * the Chinese remainder theorem gives back the integer when it lies in
+ * (-Q/2, Q/2], Q = q_0 ... q_{k-1}.
+ */
+#define FP_RNS_MAX_PRIMES 64
+#define FP_RNS_COEFFS 100  /* coeff_type reported by fp_tree_info for such trees */
+
+/* fp_rns_primes -- the first k primes q_0 > q_1 > ... (k <= FP_RNS_MAX_PRIMES),
+ * host uint64 [k].  Errors: FP_E_BAD_VALUE. */
+int fp_rns_primes(int k, uint64_t* q);
+
+/* fp_compile_rns -- fp_compile for integer coefficients given by residues:
+ * residues host uint64 [k][nterms], residues[i][t] = c_t mod q_i (each < q_i,
+ * else FP_E_BAD_VALUE).  A term whose residues are all zero is dropped.  The
+ * tree serves fp_eval_rns only (fp_eval returns FP_E_DTYPE).  Other arguments
+ * and errors as fp_compile. */
+int fp_compile_rns(int nvars, int64_t nterms, const int32_t* exps, int k, const uint64_t* residues,
+                   fp_scheme scheme, const int32_t* f_table, int64_t f_table_len, fp_tree** out);
+
+/* fp_eval_rns -- the walk modulo each prime of the tree: points device uint64
+ * [k][nvars][npts] (residues of the points; values >= q_i are reduced), out
+ * device uint64 [k][npts], out[i][j] = p(x_j) mod q_i exactly.  One launch:
+ * blocks over points by primes.  Errors as fp_eval. */
+int fp_eval_rns(const fp_tree* t, const uint64_t* points, int64_t npts, uint64_t* out, void* stream);
+
+/* fp_crt -- integers from residues (Garner's mixed-radix algorithm):
+ * residues device uint64 [k][npts] (each < q_i), limbs device uint64
+ * [npts][k]: the value X in (-Q/2, Q/2] with X = residues[i][j] mod q_i,
+ * as k 64-bit limbs, least significant first, two's complement.  Work per
+ * value O(k^2).  Errors: FP_E_BAD_VALUE, FP_E_NOMEM, FP_E_CUDA. */
+int fp_crt(int k, const uint64_t* residues, int64_t npts, uint64_t* limbs, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* fp_strerror(int status);
 

@@ -91,6 +91,20 @@ def modp_value(exps, coeffs, point):
     return s
 
 
+def int_value(exps, coeffs, point):
+    """Exact p(point) over the integers (Python integers of any size):
+    sum_e c_e prod_v x_v^(e_v), the plain definition.  exps: exponent tuples,
+    coeffs and point: integers."""
+    s = 0
+    for e, c in zip(exps, coeffs):
+        t = int(c)
+        for v, xv in enumerate(point):
+            if e[v]:
+                t *= int(xv) ** int(e[v])
+        s += t
+    return s
+
+
 def round_down(q):
     """Largest double <= the Fraction q (q within the finite double range)."""
     f = float(q)  # round to nearest

@@ -34,6 +34,10 @@ for _name, _args in {
     "fp_tree_export": [_P, _P, _P, _P, _P, _P, _P],
     "fp_measure_rates": [_P, ctypes.c_int, _P],
     "fp_tune_scheme": [ctypes.c_int, _I64, _P, _P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _P, _P, _P],
+    "fp_rns_primes": [ctypes.c_int, _P],
+    "fp_compile_rns": [ctypes.c_int, _I64, _P, ctypes.c_int, _P, ctypes.c_int, _P, _I64, _P],
+    "fp_eval_rns": [_P, _P, _I64, _P, _P],
+    "fp_crt": [ctypes.c_int, _P, _I64, _P, _P],
     "fp_tree_schedule": [_P] * 12,
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
@@ -212,6 +216,70 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
     _check(_lib.fp_eval_ex(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
                            ctypes.byref(cfg)), "fp_eval_ex")
     return out
+
+
+RNS_MAX_PRIMES = 64
+
+
+def fp_rns_primes(k):
+    """The library's first k primes q_i = 2^64 - c_i (largest first), uint64."""
+    q = np.zeros(k, dtype=np.uint64)
+    _check(_lib.fp_rns_primes(k, _ptr(q)), "fp_rns_primes")
+    return q
+
+
+def fp_compile_rns(exps, residues, scheme="E", ftab=None):
+    """Compile integer coefficients given as residues [k][nterms] (uint64,
+    residues[i][t] = c_t mod q_i) for fp_eval_rns."""
+    e = np.ascontiguousarray(exps, dtype=np.int32)
+    if e.ndim == 1:
+        e = e.reshape(-1, 1)
+    nterms, nvars = e.shape
+    r = np.ascontiguousarray(residues, dtype=np.uint64)
+    if r.ndim != 2 or r.shape[1] != nterms:
+        raise ValueError("residues must be [k][nterms]")
+    ft = None if ftab is None else np.ascontiguousarray(ftab, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.fp_compile_rns(nvars, nterms, _ptr(e), r.shape[0], _ptr(r),
+                               SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+                               None if ft is None else _ptr(ft), 0 if ft is None else len(ft), ctypes.byref(h)),
+           "fp_compile_rns")
+    t = Tree(h.value, nvars, "rns")
+    t.rns_k = r.shape[0]
+    return t
+
+
+def fp_eval_rns(tree, points, out=None, stream=None):
+    """p(x) mod each prime: points device [k][nvars][npts] (int64 containers of
+    uint64 residues), out [k][npts]."""
+    import torch
+    if not points.is_cuda or not points.is_contiguous():
+        raise ValueError("points must be a contiguous CUDA tensor")
+    npts = points.shape[-1]
+    if out is None:
+        out = torch.empty((tree.rns_k, npts), dtype=torch.int64, device=points.device)
+    _check(_lib.fp_eval_rns(tree.handle, _ptr(points), npts, _ptr(out), _stream_handle(stream)), "fp_eval_rns")
+    return out
+
+
+def fp_crt(residues, out=None, stream=None):
+    """Integers from residues [k][npts] (device): limbs [npts][k], least
+    significant first, two's complement of the value in (-Q/2, Q/2]."""
+    import torch
+    k, npts = residues.shape
+    if out is None:
+        out = torch.empty((npts, k), dtype=torch.int64, device=residues.device)
+    _check(_lib.fp_crt(k, _ptr(residues), npts, _ptr(out), _stream_handle(stream)), "fp_crt")
+    return out
+
+
+def limbs_to_int(limbs):
+    """Python integer of k 64-bit limbs (least significant first, two's complement)."""
+    v = 0
+    for i, w in enumerate(np.asarray(limbs, dtype=np.uint64).tolist()):
+        v |= int(w) << (64 * i)
+    k = len(limbs)
+    return v - (1 << (64 * k)) if v >> (64 * k - 1) else v
 
 
 RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd", "modp_butterfly")

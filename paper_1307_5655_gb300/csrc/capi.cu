@@ -12,6 +12,10 @@
 #include "tree.hpp"
 
 namespace fp {
+uint64_t rns_offset(int i);
+int launch_eval_rns(const EvalArgs& a, const OpArgs& o, int scheme, int k, const int64_t* strides,
+                    const uint64_t* root_c, cudaStream_t st);
+
 namespace {
 
 template <class T>
@@ -25,7 +29,8 @@ int upload(const std::vector<T>& h, T** d) {
 void release(fp_tree* t) {
   DeviceSchedule& d = t->dev;
   void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64,
-                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64, d.ops_prog, d.ops_chain_pid};
+                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64, d.ops_prog, d.ops_chain_pid,
+                  d.ca_rns, d.cb_rns, d.ops_rns, d.st_rns, d.root_rns};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceSchedule{};
@@ -587,6 +592,131 @@ int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_
     layout[6] = t->ops_root_pid;
   }
   return FP_OK;
+}
+
+int fp_compile_rns(int nvars, int64_t nterms, const int32_t* exps, int k, const uint64_t* residues,
+                   fp_scheme scheme, const int32_t* f_table, int64_t f_table_len, fp_tree** out) {
+  if (!out || k < 1 || k > FP_RNS_MAX_PRIMES || nterms < 0) return FP_E_BAD_VALUE;
+  if (nterms > FP_MAX_TERMS) return FP_E_TOO_LARGE;
+  if (nterms > 0 && !residues) return FP_E_BAD_VALUE;
+  std::vector<uint64_t> present;
+  try {
+    present.assign((size_t)nterms, 0);
+  } catch (const std::bad_alloc&) {
+    return FP_E_NOMEM;
+  }
+  for (int i = 0; i < k; ++i) {
+    const uint64_t q = 0 - rns_offset(i);
+    for (int64_t t = 0; t < nterms; ++t) {
+      const uint64_t r = residues[(size_t)i * nterms + t];
+      if (r >= q) return FP_E_BAD_VALUE;
+      present[t] |= r != 0 ? 1u : 0u;
+    }
+  }
+  fp_tree* t = new (std::nothrow) fp_tree();
+  if (!t) return FP_E_NOMEM;
+  int rc;
+  try {
+    // the tree of the terms that are non-zero modulo some prime
+    rc = compile_host(nvars, nterms, exps, present.data(), FP_MODP, scheme, f_table, f_table_len, t);
+    if (rc == FP_OK) {
+      const int64_t N = t->nnodes;
+      t->rns_k = k;
+      t->c_rns.assign((size_t)k * N, 0);
+      for (int i = 0; i < k; ++i)
+        for (int64_t j = 0; j < N; ++j)
+          if (t->term_of_node[j] >= 0) t->c_rns[(size_t)i * N + j] = residues[(size_t)i * nterms + t->term_of_node[j]];
+    }
+  } catch (const std::bad_alloc&) {
+    rc = FP_E_NOMEM;
+  }
+  if (rc == FP_OK) rc = upload_schedule(t);
+  if (rc == FP_OK && t->nnodes > 0) {
+    // per-prime slices of the node coefficients, the op records and streams
+    const int64_t N = t->nnodes, S = N - 1;
+    DeviceSchedule& d = t->dev;
+    std::vector<uint64_t> a((size_t)k * S), b((size_t)k * S), root(k);
+    std::vector<OpRec<uint64_t>> recs_all;
+    std::vector<uint64_t> st_all;
+    int64_t pitch = 0;
+    for (int i = 0; i < k; ++i) {
+      std::vector<uint64_t> ci(t->c_rns.begin() + (size_t)i * N, t->c_rns.begin() + (size_t)(i + 1) * N);
+      for (int64_t j = 0; j < S; ++j) {
+        a[(size_t)i * S + j] = ci[j];
+        b[(size_t)i * S + j] = ((t->ctrl[j] >> kCtrlFirst) & 1u) ? ci[t->parent[j]] : 0;
+      }
+      root[i] = ci[N - 1];
+      std::vector<OpRec<uint64_t>> recs;
+      std::vector<uint64_t> st;
+      build_ops(t, ci, recs, st);
+      pitch = (int64_t)st.size();
+      recs_all.insert(recs_all.end(), recs.begin(), recs.end());
+      st_all.insert(st_all.end(), st.begin(), st.end());
+    }
+    d.st_rns_pitch = pitch;
+    rc = upload(a, &d.ca_rns);
+    if (rc == FP_OK) rc = upload(b, &d.cb_rns);
+    if (rc == FP_OK) rc = upload(recs_all, &d.ops_rns);
+    if (rc == FP_OK) rc = upload(st_all, &d.st_rns);
+    if (rc == FP_OK) rc = upload(root, &d.root_rns);
+  }
+  if (rc != FP_OK) {
+    release(t);
+    delete t;
+    return rc;
+  }
+  t->coeff_type = FP_RNS_COEFFS;
+  *out = t;
+  return FP_OK;
+}
+
+int fp_eval_rns(const fp_tree* t, const uint64_t* points, int64_t npts, uint64_t* out, void* stream) {
+  if (!t || t->rns_k < 1) return t ? FP_E_DTYPE : FP_E_BAD_VALUE;
+  if (npts < 0) return FP_E_BAD_VALUE;
+  if (npts == 0) return FP_OK;
+  if (!points || !out) return FP_E_BAD_VALUE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->dev.device) { cudaGetLastError(); return FP_E_BAD_VALUE; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int k = t->rns_k;
+  if (t->nnodes == 0) {  // the zero polynomial: k rows of zeros
+    const int64_t words = (int64_t)k * npts;
+    fill_zero_kernel<<<(unsigned)std::min<int64_t>((words + 255) / 256, 4096), 256, 0, st>>>(out, words);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
+  }
+  EvalArgs a{};
+  a.ctrl = t->dev.ctrl;
+  a.pow_prog = t->dev.pow_prog;
+  a.pow_dv = t->dev.pow_dv;
+  a.nsteps = t->nnodes - 1;
+  a.npow = (int)t->pow_prog.size();
+  a.nslot = t->max_lh + 1;
+  a.nvars = t->nvars;
+  a.root_leaf = t->root_leaf;
+  a.root_lh = t->root_lh;
+  a.root_pid = t->root_pid;
+  a.points = points;
+  a.npts = npts;
+  a.out = out;
+  a.ca = t->dev.ca_rns;
+  a.cb = t->dev.cb_rns;
+  OpArgs o{};
+  o.recs = t->dev.ops_rns;
+  o.stream = t->dev.st_rns;
+  o.nops = (int64_t)t->ops.size();
+  o.prog = t->dev.ops_prog;
+  o.chain_pid = t->dev.ops_chain_pid;
+  o.nprog = (int)t->ops_prog.size();
+  o.nlive = t->ops_nlive;
+  o.nslot = t->ops_nslot;
+  o.entries = t->ops_entries;
+  o.root_lh = t->ops_root_lh;
+  o.root_pid = t->ops_root_pid;
+  o.pos_x1 = t->ops_pos_x1;
+  for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
+  const int64_t strides[5] = {(int64_t)t->nvars * npts, npts, t->nnodes - 1, (int64_t)t->ops.size(),
+                              t->dev.st_rns_pitch};
+  return launch_eval_rns(a, o, t->block_scheme, k, strides, t->dev.root_rns, st);
 }
 
 int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,

@@ -73,6 +73,13 @@ struct DeviceSchedule {
   uint64_t* st_u64 = nullptr;
   uint2* ops_prog = nullptr;         // power program of the grouped-op kernel
   uint32_t* ops_chain_pid = nullptr;  // [nsteps]
+  // residues (fp_compile_rns), one slice per prime
+  uint64_t* ca_rns = nullptr;        // [k][nsteps]
+  uint64_t* cb_rns = nullptr;        // [k][nsteps]
+  OpRec<uint64_t>* ops_rns = nullptr;  // [k][nops]
+  uint64_t* st_rns = nullptr;        // [k][stream_pitch]
+  uint64_t* root_rns = nullptr;      // [k]
+  int64_t st_rns_pitch = 0;
 };
 
 }  // namespace fp
@@ -119,6 +126,11 @@ struct fp_tree {
   int ops_root_lh = 0, ops_root_pid = -1;
   int ops_pos_x1 = -1;  // position of x_b when the walk reads it
   int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_b^d for the block templates (-1: absent)
+
+  // residue number system (fp_compile_rns): coefficients modulo rns_k primes,
+  // [rns_k][nnodes]; coeff_type is then FP_RNS_COEFFS
+  int rns_k = 0;
+  std::vector<uint64_t> c_rns;
 
   // launch configuration chosen by fp_tune per value type (kernel, ppt; 0 = not tuned)
   int tuned_kernel[4] = {0, 0, 0, 0};
