@@ -506,26 +506,11 @@ __global__ void __launch_bounds__(kTPB) eval_kernel(const EvalArgs g) {
 
 
 // ---------------------------------------------------------------- grouped-op kernel
-// The walk grouped into ops (see kOpNode / kOpChain / kOpBlock): the fused
-// value types evaluate chains as a register loop and dense subtree blocks with
-// a compile-time template of the scheme's split, and dispatch once per op.
-
-template <class T>
-__device__ __forceinline__ T shfl_any(T v, int src) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
-  if constexpr (sizeof(T) == 4) {
-    uint32_t u;
-    memcpy(&u, &v, 4);
-    u = __shfl_sync(0xffffffffu, u, src);
-    memcpy(&v, &u, 4);
-  } else {
-    unsigned long long u;
-    memcpy(&u, &v, 8);
-    u = __shfl_sync(0xffffffffu, u, src);
-    memcpy(&v, &u, 8);
-  }
-  return v;
-}
+// The walk grouped into ops (kOpNode / kOpChain / kOpBlock / kOpPartial): the
+// fused value types evaluate chains as a register loop and dense runs (whole
+// subtrees, or a node with its last children) with a compile-time template
+// of the scheme's split -- Horner's rule over the run for exact types -- and
+// dispatch once per op.
 
 // The grouped-op kernel's table per point: entries of 8 bytes, the walk's
 // powers at [0, nlive), the slots at [nlive, nlive + nslot); the power
@@ -585,18 +570,6 @@ __device__ __forceinline__ typename A::val block_eval(const typename A::coef (&c
     constexpr bool b_coef = f == 1 && (!BASE || A::kSlotAtEnd);
     return A::template mad_k<a_coef, b_coef, f == 1>(a, xp[f], b);
   }
-}
-
-// powers a block template reads, closed under the power rule
-// (x^2k needs x^k; x^(2k+1) needs x^2k and x)
-template <int SCHEME>
-__host__ __device__ constexpr bool block_needs_power(int d) {
-  if (block_uses_power<SCHEME>(d)) return true;
-  for (int e = d + 1; e <= kMaxBlock; ++e) {
-    const bool dep = (e % 2 == 0) ? (e / 2 == d) : (e - 1 == d || d == 1);
-    if (dep && block_needs_power<SCHEME>(e)) return true;
-  }
-  return false;
 }
 
 // The value of the block's last node N is its coefficient; for a partial
