@@ -219,6 +219,7 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
 
 
 RNS_MAX_PRIMES = 64
+MAX_TERMS = 1 << 24  # FP_MAX_TERMS
 
 
 def fp_rns_primes(k):

@@ -119,6 +119,15 @@ def test_compile_errors(bad, code):
     assert ei.value.code == code
 
 
+def test_term_count_limit():
+    """One term above FP_MAX_TERMS is refused before any work."""
+    n = fpl.MAX_TERMS + 1
+    e = np.arange(n, dtype=np.int32).reshape(-1, 1)
+    with pytest.raises(fpl.FastPolyError) as ex:
+        fpl.fp_compile_host(e, np.ones(n), "E")
+    assert ex.value.code == -6
+
+
 def test_eval_on_host_only_tree_is_rejected():
     t = fpl.fp_compile_host(np.array([[1], [0]]), np.array([1.0, 2.0]), "E")
     rc = fpl._lib.fp_eval(t.handle, 0, None, 0, None, None)

@@ -367,6 +367,30 @@ def test_config2_exact_rational_bound():
         assert abs(Fraction(got[j]) - v) <= 4 * (k - 1) * Fraction(U) * s
 
 
+@pytest.mark.parametrize("scheme", ["E", "H"])
+def test_maximum_term_count(scheme):
+    """FP_MAX_TERMS = 2^24 terms (dense univariate, degree 2^24 - 1): the
+    grouped kernel at the size limit, checked at sampled points (MODP exact,
+    FP64 within the bound)."""
+    k = fpl.MAX_TERMS
+    npts = 1000 + 3
+    idx = _sample(npts, 6, 5)
+    e = W.dense_univariate_exps(k)
+    cm = W.residues(k, 91)
+    xm = W.points_modp(1, npts, 92)
+    tm = fpl.fp_compile(e, cm, scheme, modp=True)
+    assert tm.info()["nnodes"] == k
+    gm = run(tm, "modp", xm)
+    check_modp(e, cm, xm[:, idx], gm[idx])
+    tm.free()
+    c = W.uniform_f64(k, 93)
+    x = W.points_f64(1, npts, 94)
+    t = fpl.fp_compile(e, c, scheme)
+    g = run(t, "f64", x)
+    check_f64(e, c, x[:, idx], g[idx])
+    t.free()
+
+
 def test_config3_full_size_sampled():
     """Trivariate total degree 40 (12341 terms), 2^22 boxes and residues."""
     npts = 1 << 22
