@@ -177,9 +177,14 @@ int fp_tune_scheme(int nvars, int64_t nterms, const int32_t* exps, const void* c
                    fp_dtype coeff_type, fp_dtype dtype, const void* points, int64_t npts,
                    void* out, void* stream, int64_t* k0_out, fp_tree** tree_out);
 
-/* fp_eval_host -- the same as fp_eval with host buffers: copies the points to
- * the device, evaluates, copies the result back and synchronises `stream`.
- * Device buffers are allocated per call (stream-ordered). */
+/* fp_eval_host -- the same as fp_eval with host buffers (same layouts):
+ * copies the points to the device, evaluates, copies the result back and
+ * synchronises `stream`.  Above 2^22 points the work runs in up to 16 chunks
+ * as a pipeline -- the copy in of one chunk and the copy out of another
+ * overlap the evaluation of a third, on two copy streams of the library
+ * ordered after the work already on `stream` -- with pinned host buffers the
+ * copies then hide behind the evaluation.  Results are identical to fp_eval.
+ * Device buffers come from the library's stream-ordered pool. */
 int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts,
                  void* out_host, void* stream);
 
@@ -321,7 +326,8 @@ void fp_server_destroy(fp_server* s);
  *   q        device, [npairs][degq + 1], coefficient of y^i at index i.
  *   out      device, [npairs][deg(p) * degq + 1].
  * Work space (about (lazy height + 6) x npairs x deg(p) x degq x 8 bytes) is
- * allocated on `stream` with cudaMallocAsync and released before returning;
+ * allocated on `stream` from the library's stream-ordered pool (which keeps
+ * up to 4 GiB of freed device memory mapped for reuse) and released before returning;
  * the call synchronises `stream` while it uploads its tables.
  * Errors: FP_E_BAD_VALUE, FP_E_DTYPE, FP_E_TOO_LARGE (output longer than
  * 2^26), FP_E_NOMEM, FP_E_CUDA.

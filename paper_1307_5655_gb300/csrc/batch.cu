@@ -272,7 +272,7 @@ int fp_eval_batch(fp_dtype dtype, const fp_job* jobs, int64_t njobs, void* strea
   if (rc != FP_OK || b.jobs.empty()) return rc;
   BatchJob* d = nullptr;
   const size_t bytes = b.jobs.size() * sizeof(BatchJob);
-  if (cudaMallocAsync((void**)&d, bytes, st) != cudaSuccess) { cudaGetLastError(); return FP_E_NOMEM; }
+  if (pool_alloc((void**)&d, bytes, st) != cudaSuccess) { cudaGetLastError(); return FP_E_NOMEM; }
   // from pageable memory: the copy is staged before the call returns
   if (cudaMemcpyAsync(d, b.jobs.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = FP_E_CUDA;
   if (rc == FP_OK) rc = batch_launch(&b, d, st);

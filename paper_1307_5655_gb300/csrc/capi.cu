@@ -156,6 +156,15 @@ __global__ void plain_horner_kernel(const double* __restrict__ c, int64_t nc, co
 
 }  // namespace
 
+// Host buffers in, host buffers out: the points are cut into chunks that
+// run as a pipeline -- the copy in of chunk i + 1 and the copy out of chunk
+// i - 1 overlap the evaluation of chunk i -- on two copy streams of the
+// library and the caller's stream, ordered by events; two device buffers
+// per direction alternate.  Points and results are structure-of-arrays rows
+// ([rows][npts]), so a chunk is a strided 2D copy.  Synchronous.
+int eval_host_pipelined(const fp_tree* t, fp_dtype dtype, const void* points_host, int64_t npts, void* out_host,
+                        cudaStream_t st);
+
 // ---- autotuner cache: (value type, variables, block scheme, log2 nodes,
 // log2 points) -> (kernel, points per thread), filled by fp_tune
 struct TuneKey {
@@ -511,23 +520,7 @@ int fp_eval_host(const fp_tree* t, fp_dtype dtype, const void* points_host, int6
   if (npts < 0) return FP_E_BAD_VALUE;
   if (npts == 0) return FP_OK;
   if (!points_host || !out_host) return FP_E_BAD_VALUE;
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t in_bytes = point_bytes(dtype) * (size_t)t->nvars * (size_t)npts;
-  const size_t out_bytes = value_bytes_out(dtype) * (size_t)npts;
-  void *din = nullptr, *dout = nullptr;
-  if (cudaMallocAsync(&din, in_bytes, st) != cudaSuccess || cudaMallocAsync(&dout, out_bytes, st) != cudaSuccess) {
-    cudaGetLastError();
-    if (din) cudaFreeAsync(din, st);
-    return FP_E_NOMEM;
-  }
-  int rc = FP_OK;
-  if (cudaMemcpyAsync(din, points_host, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = FP_E_CUDA;
-  if (rc == FP_OK) rc = eval_device(t, dtype, din, npts, dout, st);
-  if (rc == FP_OK && cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = FP_E_CUDA;
-  cudaFreeAsync(din, st);
-  cudaFreeAsync(dout, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess && rc == FP_OK) rc = FP_E_CUDA;
-  return rc;
+  return eval_host_pipelined(t, dtype, points_host, npts, out_host, (cudaStream_t)stream);
 }
 
 int fp_tree_info(const fp_tree* t, int64_t* nnodes, int* nvars, int* max_lazy_height, int* npowers,

@@ -413,7 +413,7 @@ struct Composer {
       arena_used += sz;
       return p;
     }
-    if (cudaMallocAsync(&p, bytes < 16 ? 16 : bytes, st) != cudaSuccess) {
+    if (pool_alloc(&p, bytes < 16 ? 16 : bytes, st) != cudaSuccess) {
       cudaGetLastError();
       status = FP_E_NOMEM;
       return nullptr;

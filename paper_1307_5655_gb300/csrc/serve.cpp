@@ -138,8 +138,8 @@ struct fp_server {
     std::vector<fp_job> jobs;
     jobs.reserve(take.size());
     for (Request& r : take) {
-      if (cudaMallocAsync(&r.d_in, r.in_bytes ? r.in_bytes : 16, s.stream) != cudaSuccess ||
-          cudaMallocAsync(&r.d_out, r.out_bytes ? r.out_bytes : 16, s.stream) != cudaSuccess) {
+      if (fp::pool_alloc(&r.d_in, r.in_bytes ? r.in_bytes : 16, s.stream) != cudaSuccess ||
+          fp::pool_alloc(&r.d_out, r.out_bytes ? r.out_bytes : 16, s.stream) != cudaSuccess) {
         cudaGetLastError();
         status = FP_E_NOMEM;
         break;

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime.h>
 #include <vector_types.h>
 
 #include "../../include/fastpoly.h"
@@ -140,6 +141,10 @@ struct fp_tree {
 };
 
 namespace fp {
+// Stream-ordered work space from the library's device pool (freed with
+// cudaFreeAsync; the pool keeps freed memory mapped for reuse).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+
 // Build the tree and its schedule on the host (no CUDA calls).
 int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
                  fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,

@@ -216,6 +216,31 @@ def test_host_entry_point_matches_device():
     assert np.array_equal(fpl.fp_eval_host(t, "f64", x), run(t, "f64", x))
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32c", "iv64", "modp"])
+def test_host_entry_point_pipelined(dtype):
+    """Above 2^22 points fp_eval_host runs chunks as a copy/compute pipeline
+    (strided 2D copies of the structure-of-arrays rows, a ragged last chunk):
+    bit-identical to fp_eval on the same points, two variables."""
+    npts = 3 * (1 << 21) + 7
+    e = W.graded_prefix_exps(40, 2)
+    modp = dtype == "modp"
+    c = W.residues(len(e), 15) if modp else W.uniform_f64(len(e), 15)
+    t = fpl.fp_compile(e, c, "E", modp=modp)
+    if dtype == "iv64":
+        lo, hi = W.boxes(2, npts, 16)
+        pts = np.ascontiguousarray(np.stack([lo, hi], axis=1))
+        dev = (lo, hi)
+    elif modp:
+        pts = dev = W.points_modp(2, npts, 16)
+    else:
+        x = W.points_f64(2, npts, 16)
+        pts = W.to_f32(x) if dtype == "f32c" else x
+        dev = x
+    got = fpl.fp_eval_host(t, dtype, pts)
+    want = run(t, dtype, dev)
+    assert np.array_equal(np.asarray(got).view(np.uint8), np.asarray(want).view(np.uint8))
+
+
 def test_plain_baseline_kernel():
     import torch
     e, c, x = W.univariate_case(1024, 5000, 14)
