@@ -136,10 +136,13 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi samples every 200 ms while a region runs; the raw CSV goes to
+    $FASTPOLY_CLOCKS_CSV when set, else to a temporary file."""
+
     def __init__(self):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv"
+        self.path = os.environ.get("FASTPOLY_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), "bench_clocks.csv")
 
     def start(self):
         try:

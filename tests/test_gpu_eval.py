@@ -1,7 +1,7 @@
 """GPU parity: the CUDA evaluation path against the CPU oracle, element by
 element on seeded inputs, for every value type, scheme and edge case.
 
-Bars (derived in the design doc):
+Bars:
   MODP   bit-exact against the plain sum mod p.
   IV64   bit-exact (both bounds) against the oracle's directed-rounding walk
          on the oracle's own tree.
