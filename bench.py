@@ -640,32 +640,39 @@ def run_serve(args):
     total_evals = sum(x[4] for x in reqs)
 
     def serve(arrivals):
+        """Latencies (us) in request order, wall time, server statistics."""
         srv = fpl.Server(hbm_budget_bytes=args.hbm_budget << 20, max_batch_jobs=256, streams=4)
-        lat = []
+        done, tickets = {}, []
         t0 = time.perf_counter()
         for (tree, dt, pts, out, _), ta in zip(reqs, arrivals):
             if ta is not None:
                 while time.perf_counter() - t0 < ta:
                     pass
-            srv.submit(tree, dt, pts, out)
-            if len(lat) < len(reqs):
-                lat += [x[2] for x in srv.poll()]
+            tickets.append(srv.submit(tree, dt, pts, out))
+            done.update({x[0]: x[2] for x in srv.poll()})
         srv.drain(3600)
         wall = time.perf_counter() - t0
-        lat += [x[2] for x in srv.poll()]
+        done.update({x[0]: x[2] for x in srv.poll()})
         st = srv.stats()
         srv.close()
-        return wall, np.array(lat), st
+        return wall, np.array([done.get(tk, np.nan) for tk in tickets], dtype=np.float64), st
 
     serve([None] * 8)  # warm-up on a few requests is implicit in the first call's trees
     wall_sat, lat_sat, st_sat = serve([None] * len(reqs))
     rate = len(reqs) / wall_sat
     gaps = W.rng(5001).exponential(1.0 / (0.7 * rate), size=len(reqs))
     wall_open, lat_open, st_open = serve(list(np.cumsum(gaps)))
+    lat_open = np.where(np.isnan(lat_open), np.nanmax(lat_open), lat_open)
+    # each request alone, one launch: its isolated service time (the
+    # denominator of its slowdown under the Poisson stream)
+    iso = np.empty(len(reqs))
     t0 = time.perf_counter()
-    for tree, dt, pts, out, _ in reqs:
+    for i, (tree, dt, pts, out, _) in enumerate(reqs):
+        ti = time.perf_counter()
         fpl.fp_eval_host(tree, dt, pts)
+        iso[i] = (time.perf_counter() - ti) * 1e6
     wall_seq = time.perf_counter() - t0
+    slow = lat_open / iso
     line = {
         "metric": "p50/p99 serve latency and throughput",
         "workload": "%d requests, uni/bivariate, k log-uniform [8, 65536], points log-uniform [1, 2^20], "
@@ -676,6 +683,9 @@ def run_serve(args):
         "poisson_0.7": {"rate_per_s": 0.7 * rate, "wall_s": wall_open,
                         "p50_ms": float(np.percentile(lat_open, 50)) / 1e3,
                         "p99_ms": float(np.percentile(lat_open, 99)) / 1e3,
+                        "slowdown_p50": float(np.nanpercentile(slow, 50)),
+                        "slowdown_p99": float(np.nanpercentile(slow, 99)),
+                        "slowdown_note": "latency / the request's own run time alone (fp_eval_host)",
                         "G_term_evals_per_s": total_evals / wall_open / 1e9, "batches": st_open["batches"]},
         "one_launch_per_request": {"wall_s": wall_seq, "requests_per_s": len(reqs) / wall_seq,
                                    "G_term_evals_per_s": total_evals / wall_seq / 1e9},
