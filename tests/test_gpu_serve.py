@@ -116,3 +116,25 @@ def test_concurrent_submitters():
     for tree, dt, pts, out in reqs:
         assert np.array_equal(out.view(np.uint8), _alone(tree, dt, pts).view(np.uint8))
     srv.close()
+
+
+def test_drain_deadline_then_completion():
+    """The bounded wait: a drain whose deadline passes while a long request
+    runs returns FP_E_TIMEOUT (the server keeps working, nothing is lost);
+    a second drain then completes and the result equals the request alone."""
+    k = 1 << 15
+    e = W.dense_univariate_exps(k)
+    c = W.uniform_f64(k, 41)
+    tree = fpl.fp_compile(e, c, "E")
+    pts = _host_points("iv64", 1, 1 << 20, 42)  # about 0.4 s of interval work
+    out = _out("iv64", 1 << 20)
+    srv = fpl.Server(hbm_budget_bytes=1 << 30, max_batch_jobs=4, streams=1)
+    srv.submit(tree, "iv64", pts, out)
+    with pytest.raises(fpl.FastPolyError) as ex:
+        srv.drain(1e-3)
+    assert ex.value.code == -8
+    srv.drain(120)
+    done = srv.poll()
+    assert len(done) == 1 and done[0][1] == 0
+    srv.close()
+    assert np.array_equal(out, _alone(tree, "iv64", pts))
