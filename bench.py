@@ -774,7 +774,7 @@ def run_peaks(args):
         "f32c_node_roofline_G_per_s (general form)": rates["f32c_mad"],
         "f32c_horner_node_roofline_G_per_s": rates["f32c_horner"],
         "modp_node_roofline_G_per_s": rates["modp_muladd"],
-        "iv64_node_roofline_G_per_s (6 directed-rounding FP64 operations)": rates["dadd_rd"] / 6,
+        "iv64_node_roofline_G_per_s (4 directed-rounding FP64 operations)": rates["dadd_rd"] / 4,
     }
     print(json.dumps({"metric": "sustained G op/s per operation (roofline denominators)", "rates": rates,
                       "per_node": derived, "clocks": clocks, "n_gpus": 1}))

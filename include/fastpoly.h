@@ -378,9 +378,10 @@ int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, co
  *   FP_RATE_MODP_MULADD  (a b + c) mod p (one MODP node)
  *   FP_RATE_MODP_BUTTERFLY  (a, b) -> (a + w b, a - w b) mod p (one radix-2
  *                        butterfly of the number-theoretic transforms)
- * An interval node is 2 additions, 2 products and 2 additions with directed
- * rounding: its bound is FP_RATE_DADD_RD / 6 (the products issue at the same
- * rate as the additions). 
+ * An interval walk costs 4 directed-rounding operations per node (a product,
+ * 2, plus the coefficient's addition at a parent or the accumulation at a
+ * non-first child, 2): its bound is FP_RATE_DADD_RD / 4 (products issue at
+ * the additions' rate). 
  * Errors: FP_E_BAD_VALUE (NULL rates, negative nrates), FP_E_NOMEM, FP_E_CUDA. */
 enum {
   FP_RATE_DFMA = 0,
