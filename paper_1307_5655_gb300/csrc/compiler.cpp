@@ -386,7 +386,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
                  (uint32_t)pid.at({t->pd_var[i], t->pd[i]}) << kCtrlPid;
   }
   // a5': group the walk into ops (fused value types).  A block is a maximal
-  // subtree of at most kMaxBlock nodes over consecutive exponents of a
+  // subtree of at most kMaxBlock nodes (kMaxExactBlock for residues) over consecutive exponents of a
   // univariate polynomial under E or B: its shape is the scheme's own split
   // applied to a dense run, so a compile-time template evaluates it.  A
   // partial block is, for a node N with a larger subtree, N together with its
@@ -406,6 +406,9 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     // polynomials): its groups are univariate polynomials under the scheme
     const int bv = nvars - 1;
     const bool blocks = scheme == FP_SCHEME_E || scheme == FP_SCHEME_B;
+    // residues are exact, so their kernels run a block as one loop over its
+    // run (any length); the floating-point kernels use compiled templates
+    const int64_t max_block = coeff_type == FP_MODP ? kMaxExactBlock : kMaxBlock;
     // nodes j0..r have consecutive exponents of x_bv and equal exponents of the others
     auto dense_run = [&](int64_t j0, int64_t r) {
       const int32_t* er = &t->node_e[r * nvars];
@@ -422,29 +425,40 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     std::vector<int64_t> partial_len(N, 0);  // at the partial block's first node
     std::vector<uint8_t> in_partial(N, 0);   // node lies inside a partial block
     if (blocks) {
-      for (int64_t r = 0; r + 1 < N; ++r) {  // partial blocks (the root keeps its own path)
-        if (size[r] <= kMaxBlock) continue;
-        int64_t s = 1, pos = r - 1;
-        while (pos >= 0 && t->parent[pos] == r && s + size[pos] <= kMaxBlock) {
+      // qual: the subtree is a dense run of at most max_block nodes
+      std::vector<uint8_t> qual(N, 0), in_block(N, 0);
+      for (int64_t r = 0; r + 1 < N; ++r) {
+        const int64_t s = size[r];
+        qual[r] = s >= 2 && s <= max_block && r - s + 1 < (1ll << 32) && dense_run(r - s + 1, r);
+      }
+      // subtrees inside a maximal qualifying subtree (nodes in index order:
+      // a subtree is the contiguous range ending at its root)
+      for (int64_t r = N - 2; r >= 0; --r) {
+        const int64_t q = t->parent[r];
+        if (q != N - 1 && (in_block[q] || qual[q])) in_block[r] = 1;
+      }
+      // partial blocks: a node outside any block, with the longest suffix of
+      // its children that forms a dense run with it (in a multivariate tree
+      // the earlier children may be other groups); the root keeps its path
+      for (int64_t r = 0; r + 1 < N; ++r) {
+        if (qual[r] || in_block[r]) continue;
+        int64_t s = 1, best = 1, pos = r - 1;
+        while (pos >= 0 && t->parent[pos] == r && s + size[pos] <= max_block) {
           s += size[pos];
           pos -= size[pos];
+          if (dense_run(r - s + 1, r)) best = s;
+          else break;
         }
+        s = best;
         if (s < 2) continue;
         const int64_t j0 = r - s + 1;
-        if (!dense_run(j0, r)) continue;
         if (j0 >= (1ll << 32)) continue;
         partial_len[j0] = s;
         for (int64_t j = j0; j <= r; ++j) in_partial[j] = 1;
       }
-      for (int64_t r = 0; r + 1 < N; ++r) {
-        const int64_t s = size[r], q = t->parent[r];
-        if (s < 2 || s > kMaxBlock || in_partial[r]) continue;
-        if (q != N - 1 && size[q] <= kMaxBlock) continue;  // not maximal
-        const int64_t j0 = r - s + 1;
-        if (!dense_run(j0, r)) continue;
-        if (j0 >= (1ll << 32)) continue;
-        block_len[j0] = s;
-      }
+      // blocks: maximal qualifying subtrees not absorbed by a partial block
+      for (int64_t r = 0; r + 1 < N; ++r)
+        if (qual[r] && !in_block[r] && !in_partial[r]) block_len[r - size[r] + 1] = size[r];
     }
     auto pid_of = [&](int64_t i) { return (uint32_t)pid.at({t->pd_var[i], t->pd[i]}); };
     auto emit = [&](uint32_t kind, int64_t j0, int64_t j1) {

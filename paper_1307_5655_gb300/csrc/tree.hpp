@@ -48,6 +48,7 @@ constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 constexpr uint32_t kOpNode = 0, kOpChain = 1, kOpBlock = 2, kOpPartial = 3;
 constexpr uint32_t kOpS = 2, kOpD = 8, kOpLeaf = 14, kOpFirst = 15, kOpUniform = 16, kOpPid = 17;
 constexpr int kMaxChain = 64, kMaxBlock = 16, kStreamAlign = 4;
+constexpr int kMaxExactBlock = 64;  // blocks of mod-p trees (evaluated by a loop, not a template)
 
 template <class C>
 struct alignas(16) OpRec {

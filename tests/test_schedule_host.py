@@ -68,8 +68,8 @@ def _replay(t, coeffs, x, counts=None):
     for d, v in xp.items():
         assert v == pow(x1, d, P), d
 
-    def xpow(d):
-        return xp[d]
+    def xpow(d):  # a block longer than 16 (mod-p trees) splits with powers past the table's
+        return xp[d] if d in xp else pow(x1, d, P)
 
     def slot(s_):
         assert 0 <= s_ < sc["nslot"]
@@ -109,7 +109,8 @@ def _replay(t, coeffs, x, counts=None):
                 if uniform:
                     assert len(pids) == 1
             else:
-                assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 16
+                # mod-p trees run blocks as a loop: up to 64 nodes (templates: 16)
+                assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 64
                 run = ex["node_e"][j0:j1 + 1]
                 assert np.array_equal(run[:, -1], np.arange(run[0, -1], run[0, -1] - ln, -1))
                 assert (run[:, :-1] == run[-1, :-1]).all()
@@ -160,6 +161,11 @@ def test_large_univariate_schedules_use_partial_blocks():
         assert counts[3] > 0 and counts[2] > 0
         # a partial block absorbs the small children: far fewer ops than nodes
         assert sum(counts) * 6 < 10007, counts
+    # the floating-point trees keep blocks of at most 16 nodes
+    e, c, _ = W.univariate_case(3000, 1, 4243)
+    sc = fpl.fp_compile_host(e, c, "B").schedule()
+    lens = sc["op_words"][:, 1][(sc["op_words"][:, 0] & 3) >= 2] + 1
+    assert lens.max() <= 16
 
 
 def test_sparse_and_hybrid_schedules():
