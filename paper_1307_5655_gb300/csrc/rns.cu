@@ -75,14 +75,19 @@ uint64_t rns_offset(int i) { return prime_offsets()[i]; }
 
 // ------------------------------------------------------------ device arithmetic
 // hi 2^64 + lo mod q, q = 2^64 - c, c < 2^32: 2^64 = c (mod q), so
-//   hi 2^64 + lo = lo + hi c;  hi c = t1 2^64 + t0 with t1 < 2^32;
+//   hi 2^64 + lo = lo + hi c;  hi c = t1 2^64 + t0 with t1 < 2^32 (from
+//   two 32 x 32 -> 64 products);
 //   s = lo + t0 (carry k);  then s + (t1 + k) c, whose product is < 2^64;
 //   a carry out of that sum is worth c again (it cannot carry twice);
 //   one conditional subtraction of q leaves [0, q).
 __device__ __forceinline__ uint64_t modq_reduce(uint64_t lo, uint64_t hi, uint64_t c) {
-  const uint64_t t0 = hi * c, t1 = __umul64hi(hi, c);
+  // hi c from two 32 x 32 -> 64 products (c < 2^32): h0 c + (h1 c) 2^32
+  const uint32_t c32 = (uint32_t)c;
+  const uint64_t p0 = (uint64_t)(uint32_t)hi * c32, p1 = (uint64_t)(uint32_t)(hi >> 32) * c32;
+  const uint64_t t0 = p0 + (p1 << 32);
+  const uint64_t t1 = (p1 >> 32) + (t0 < p0 ? 1ull : 0ull);
   const uint64_t s = lo + t0;
-  const uint64_t u = (t1 + (s < t0 ? 1ull : 0ull)) * c;
+  const uint64_t u = (uint64_t)(uint32_t)t1 * c32 + (s < t0 ? c : 0ull);  // (t1 + carry) c < 2^64
   uint64_t r = s + u;
   if (r < u) r += c;
   const uint64_t q = 0 - c;
