@@ -276,7 +276,11 @@ void fp_batch_free(fp_batch* batch);
  * groups requests of one value type into one batched launch on one of
  * `streams` streams (copies in, fp_eval_batch, copies out), and retires
  * batches as they finish, so requests that arrive while batches run are
- * admitted as soon as a stream and memory free up.  Results equal fp_eval's.
+ * admitted as soon as a stream and memory free up.  A batch lasts as long as
+ * its largest request: small requests (estimated work below about 1.7 ms of
+ * FP64 evaluation) are batched apart from large ones and launched on
+ * streams of the highest priority, and with two or more streams the first
+ * takes small requests only.  Results equal fp_eval's.
  * Host buffers should be pinned (page-locked) for the copies to overlap; they
  * must stay valid until the request completes.  Trees must outlive the
  * requests that use them.

@@ -6,9 +6,13 @@
 //     their device memory returns to the budget);
 //   - admits pending requests, oldest first, while their device footprint
 //     (points + results) fits in the HBM budget, grouping requests of one
-//     value type into one batched launch (fp_eval_batch) on a free stream:
-//     host->device copies, the launch, device->host copies, release of the
-//     buffers, then an event -- all stream-ordered;
+//     value type and one size class into one batched launch (fp_eval_batch)
+//     on a free stream: host->device copies, the launch, device->host copies,
+//     release of the buffers, then an event -- all stream-ordered.  A batch
+//     lasts as long as its largest request, so small requests (estimated
+//     work below kSmallWork) are never batched with large ones and run on
+//     high-priority streams, and with two or more slots the first is kept
+//     for small requests (an express lane);
 //   - sleeps on a condition variable (bounded) when there is nothing to do.
 // Requests arriving while batches run are admitted as soon as a stream and
 // memory are free, so their work overlaps with the batches in flight.
@@ -42,6 +46,16 @@ size_t in_bytes_of(fp_dtype dt, int nvars, int64_t npts) {
 }
 size_t out_bytes_of(fp_dtype dt, int64_t npts) { return (dt == FP_IV64 ? 16 : 8) * (size_t)npts; }
 
+// Estimated work of a request in FP64 node-evaluations: nodes x points x the
+// value type's cost per node relative to FP64 (measured throughputs: FP32C
+// about 4x faster, intervals about 7.5x slower, residues about as fast).
+double work_of(const fp_tree* t, fp_dtype dt, int64_t npts) {
+  const double w = dt == FP_F32C ? 0.25 : (dt == FP_IV64 ? 7.5 : 1.0);
+  return w * (double)t->nnodes * (double)npts;
+}
+// below this a request is small: about 1.7 ms of FP64 work on the GPU
+constexpr double kSmallWork = 1.0e9;
+
 struct Request {
   int64_t ticket = 0;
   const fp_tree* tree = nullptr;
@@ -50,13 +64,15 @@ struct Request {
   void* out_host = nullptr;
   int64_t npts = 0;
   size_t in_bytes = 0, out_bytes = 0;
+  bool small = true;  // estimated work below kSmallWork
   Clock::time_point t_submit;
   void* d_in = nullptr;
   void* d_out = nullptr;
 };
 
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // large requests (default priority)
+  cudaStream_t stream_hi = nullptr;  // small requests (highest priority)
   cudaEvent_t done = nullptr;
   std::vector<Request> reqs;
   size_t bytes = 0;
@@ -117,15 +133,22 @@ struct fp_server {
     return any;
   }
 
-  // admit and launch one batch on slot s; returns true if launched
-  bool dispatch(Slot& s) {
-    if (pending.empty()) return false;
-    const fp_dtype dt = pending.front().dtype;
+  // admit and launch one batch on slot s; returns true if launched.  The
+  // batch takes the oldest pending request (the oldest small one on the
+  // express slot, so that small requests always have a slot) and others of
+  // its value type and size class.
+  bool dispatch(Slot& s, bool express) {
+    auto first = pending.begin();
+    if (express)
+      while (first != pending.end() && !first->small) ++first;
+    if (first == pending.end()) return false;
+    const fp_dtype dt = first->dtype;
+    const bool small = first->small;
     const int maxjobs = cfg.max_batch_jobs > 0 ? cfg.max_batch_jobs : 1024;
     std::vector<Request> take;
     size_t bytes = 0;
-    for (auto it = pending.begin(); it != pending.end() && (int)take.size() < maxjobs;) {
-      if (it->dtype != dt) { ++it; continue; }
+    for (auto it = first; it != pending.end() && (int)take.size() < maxjobs;) {
+      if (it->dtype != dt || it->small != small) { ++it; continue; }
       const size_t need = it->in_bytes + it->out_bytes;
       const bool alone = take.empty() && used_bytes == 0;  // larger than the budget: run it by itself
       if (used_bytes + bytes + need > cfg.hbm_budget_bytes && !alone) break;  // oldest first: no overtaking
@@ -134,20 +157,24 @@ struct fp_server {
       it = pending.erase(it);
     }
     if (take.empty()) return false;
+    // small batches run on the slot's high-priority stream: the block
+    // scheduler then runs their blocks ahead of those a large batch still has
+    // waiting on the other streams
+    const cudaStream_t st = small ? s.stream_hi : s.stream;
     int status = FP_OK;
     std::vector<fp_job> jobs;
     jobs.reserve(take.size());
     for (Request& r : take) {
-      if (fp::pool_alloc(&r.d_in, r.in_bytes ? r.in_bytes : 16, s.stream) != cudaSuccess ||
-          fp::pool_alloc(&r.d_out, r.out_bytes ? r.out_bytes : 16, s.stream) != cudaSuccess) {
+      if (fp::pool_alloc(&r.d_in, r.in_bytes ? r.in_bytes : 16, st) != cudaSuccess ||
+          fp::pool_alloc(&r.d_out, r.out_bytes ? r.out_bytes : 16, st) != cudaSuccess) {
         cudaGetLastError();
         status = FP_E_NOMEM;
         break;
       }
-      if (r.in_bytes && cudaMemcpyAsync(r.d_in, r.in_host, r.in_bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+      if (r.in_bytes && cudaMemcpyAsync(r.d_in, r.in_host, r.in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         status = FP_E_CUDA;
       if (r.tree->nnodes == 0) {  // the zero polynomial goes through fp_eval
-        if (fp::eval_device(r.tree, r.dtype, r.d_in, r.npts, r.d_out, s.stream, 0, 0) != FP_OK) status = FP_E_CUDA;
+        if (fp::eval_device(r.tree, r.dtype, r.d_in, r.npts, r.d_out, st, 0, 0) != FP_OK) status = FP_E_CUDA;
       } else {
         fp_job j;
         j.tree = r.tree;
@@ -157,15 +184,15 @@ struct fp_server {
         jobs.push_back(j);
       }
     }
-    if (status == FP_OK && !jobs.empty()) status = fp_eval_batch(dt, jobs.data(), (int64_t)jobs.size(), s.stream);
+    if (status == FP_OK && !jobs.empty()) status = fp_eval_batch(dt, jobs.data(), (int64_t)jobs.size(), st);
     for (Request& r : take) {
       if (status == FP_OK && r.out_bytes &&
-          cudaMemcpyAsync(r.out_host, r.d_out, r.out_bytes, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
+          cudaMemcpyAsync(r.out_host, r.d_out, r.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         status = FP_E_CUDA;
-      if (r.d_in) cudaFreeAsync(r.d_in, s.stream);
-      if (r.d_out) cudaFreeAsync(r.d_out, s.stream);
+      if (r.d_in) cudaFreeAsync(r.d_in, st);
+      if (r.d_out) cudaFreeAsync(r.d_out, st);
     }
-    cudaEventRecord(s.done, s.stream);
+    cudaEventRecord(s.done, st);
     s.reqs = std::move(take);
     s.bytes = bytes;
     s.status = status;
@@ -189,8 +216,8 @@ struct fp_server {
         stopping = stop;
       }
       bool progress = retire();
-      for (Slot& s : slots)
-        if (!s.busy && dispatch(s)) progress = true;
+      for (size_t i = 0; i < slots.size(); ++i)
+        if (!slots[i].busy && dispatch(slots[i], i == 0 && slots.size() > 1)) progress = true;
       bool busy = false;
       for (const Slot& s : slots) busy = busy || s.busy;
       if (stopping && !busy && pending.empty()) {
@@ -222,12 +249,21 @@ int fp_server_create(const fp_server_cfg* cfg, fp_server** out) {
   }
   const int ns = cfg->streams > 0 ? cfg->streams : 4;
   s->slots.resize(ns);
+  // per slot a default-priority stream (large batches) and a highest-priority
+  // one (small batches)
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+    cudaGetLastError();
+    prio_low = prio_high = 0;
+  }
   for (Slot& sl : s->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       for (Slot& x : s->slots) {
         if (x.stream) cudaStreamDestroy(x.stream);
+        if (x.stream_hi) cudaStreamDestroy(x.stream_hi);
         if (x.done) cudaEventDestroy(x.done);
       }
       delete s;
@@ -239,6 +275,7 @@ int fp_server_create(const fp_server_cfg* cfg, fp_server** out) {
   } catch (...) {
     for (Slot& x : s->slots) {
       cudaStreamDestroy(x.stream);
+      cudaStreamDestroy(x.stream_hi);
       cudaEventDestroy(x.done);
     }
     delete s;
@@ -262,6 +299,7 @@ int fp_server_submit(fp_server* s, const fp_tree* tree, fp_dtype dtype, const vo
   r.npts = npts;
   r.in_bytes = in_bytes_of(dtype, tree->nvars, npts);
   r.out_bytes = out_bytes_of(dtype, npts);
+  r.small = work_of(tree, dtype, npts) < kSmallWork;
   r.t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> g(s->mu);
@@ -322,7 +360,9 @@ void fp_server_destroy(fp_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (Slot& x : s->slots) {
     cudaStreamSynchronize(x.stream);
+    cudaStreamSynchronize(x.stream_hi);
     cudaStreamDestroy(x.stream);
+    cudaStreamDestroy(x.stream_hi);
     cudaEventDestroy(x.done);
   }
   delete s;
