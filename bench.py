@@ -596,8 +596,9 @@ def run_serve(args):
     (B when k is not a power of two).  Trees are compiled once and stay
     resident (a pool of 8 per value type and variable count).  Measured: the
     saturated throughput (all requests submitted at once), then Poisson
-    arrivals at 0.7 x that rate with p50/p99 latency, and the same requests
-    served one launch at a time (fp_eval_host per request)."""
+    arrivals at 0.7 x that rate with p50/p99 latency, an overload stream at
+    1.2 x, and the same requests served one launch at a time (fp_eval_host per
+    request)."""
     import torch
     import workloads as W
     import paper_1307_5655_gb300 as fpl
@@ -667,6 +668,10 @@ def run_serve(args):
     gaps = W.rng(5001).exponential(1.0 / (0.7 * rate), size=len(reqs))
     wall_open, lat_open, st_open = serve(list(np.cumsum(gaps)))
     lat_open = np.where(np.isnan(lat_open), np.nanmax(lat_open), lat_open)
+    # overload: arrivals at 1.2 x the saturated rate (the queue grows for the
+    # whole stream; the server must keep its throughput and admit by age)
+    wall_over, lat_over, st_over = serve(list(np.cumsum(gaps * (0.7 / 1.2))))
+    lat_over = np.where(np.isnan(lat_over), np.nanmax(lat_over), lat_over)
     # each request alone, one launch: its isolated service time (the
     # denominator of its slowdown under the Poisson stream)
     iso = np.empty(len(reqs))
@@ -691,6 +696,11 @@ def run_serve(args):
                         "slowdown_p99": float(np.nanpercentile(slow, 99)),
                         "slowdown_note": "latency / the request's own run time alone (fp_eval_host)",
                         "G_term_evals_per_s": total_evals / wall_open / 1e9, "batches": st_open["batches"]},
+        "overload_1.2": {"rate_per_s": 1.2 * rate, "wall_s": wall_over,
+                         "p50_ms": float(np.percentile(lat_over, 50)) / 1e3,
+                         "p99_ms": float(np.percentile(lat_over, 99)) / 1e3,
+                         "G_term_evals_per_s": total_evals / wall_over / 1e9, "batches": st_over["batches"],
+                         "peak_hbm_bytes": st_over["peak_bytes"]},
         "one_launch_per_request": {"wall_s": wall_seq, "requests_per_s": len(reqs) / wall_seq,
                                    "G_term_evals_per_s": total_evals / wall_seq / 1e9},
         "hbm_budget_MiB": args.hbm_budget, "n_gpus": 1, "data": "synthetic",

@@ -78,6 +78,7 @@ struct F64 {
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
   static constexpr bool kExact = false;
+  static constexpr bool kKindRuns = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return fma(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return fma(s, xd, init); }
@@ -148,6 +149,7 @@ struct F32C {
   }
   static constexpr bool kSlotAtEnd = true;
   static constexpr bool kExact = false;
+  static constexpr bool kKindRuns = false;
   // a + b with the rounding error of the leading sum (TwoSum) kept in lo
   static __device__ __forceinline__ val add(val a, val b) {
     float h, e;
@@ -280,6 +282,7 @@ struct MODP {
   static __device__ __forceinline__ val from_coef(coef c) { return c; }
   static constexpr bool kSlotAtEnd = false;
   static constexpr bool kExact = true;  // any evaluation order gives the same residue
+  static constexpr bool kKindRuns = false;
   static __device__ __forceinline__ val mad(val s, pw xd, val init) { return mul_add(s, xd, init); }
   template <bool SC, bool IC, bool X1>
   static __device__ __forceinline__ val mad_k(val s, pw xd, val init) { return mul_add(s, xd, init); }
@@ -302,20 +305,38 @@ struct IV64 {
   using coef = double;
   using val = IV;
   using pw = IV;
+  // the node walk runs nodes of one kind as a loop (walk_run): a leaf skips
+  // the coefficient's additions and a first child the accumulation's
+  static constexpr bool kKindRuns = true;
   static __device__ __forceinline__ coef coef_from_bits(uint64_t b) { return __longlong_as_double((long long)b); }
   // Sign tests on the bit patterns (integer pipe; double compares would use
   // the reduced-rate FP64 pipe): x >= 0.0 holds for sign bit clear or -0.0,
-  // x <= 0.0 for sign bit set or +0.0 (NaN bounds do not occur).
-  static __device__ __forceinline__ bool ge0(double x) {
+  // x <= 0.0 for sign bit set or +0.0 (NaN bounds do not occur).  Bitwise
+  // rather than short-circuit logic, so no branches.
+  static __device__ __forceinline__ int ge0(double x) {
     const long long b = __double_as_longlong(x);
-    return b >= 0 || b == (long long)0x8000000000000000ull;
+    return (b >= 0) | (b == (long long)0x8000000000000000ull);
   }
-  static __device__ __forceinline__ bool le0(double x) {
-    const long long b = __double_as_longlong(x);
-    return b <= 0;  // sign bit set, or +0.0
-  }
-  static __device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+  static __device__ __forceinline__ int le0(double x) { return __double_as_longlong(x) <= 0; }
   static __device__ __forceinline__ int cls(const IV& a) { return ge0(a.lo) ? 0 : (le0(a.hi) ? 1 : 2); }
+  // p ? a : b as an integer select.  The FP64 pipe is the walk's bound: as a
+  // plain conditional the compiler may instead issue each product twice
+  // under complementary predicates, which doubles its FP64 issue slots.
+  static __device__ __forceinline__ double sel(int p, double a, double b) {
+    double r;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %3, 0;\n\tselp.f64 %0, %1, %2, q;\n\t}"
+        : "=d"(r)
+        : "d"(a), "d"(b), "r"(p));
+    return r;
+  }
+  // -0.0 -> +0.0, anything else unchanged (integer compare and select)
+  static __device__ __forceinline__ double pos_zero(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    asm("{\n\t.reg .pred z;\n\tsetp.eq.u64 z, %1, 0x8000000000000000;\n\tselp.b64 %0, 0, %1, z;\n\t}"
+        : "=l"(b)
+        : "l"(b));
+    return __longlong_as_double((long long)b);
+  }
   // Moore's nine sign cases: each bound is the directed rounding of the exact
   // extreme product.  The operands of the two products are selected per lane
   // (lanes hold points of different signs, so branching per case would run
@@ -331,15 +352,18 @@ struct IV64 {
   //   M x P  a.lo b.hi            a.hi b.hi
   //   M x N  a.hi b.lo            a.lo b.lo
   //   M x M  min(a.lo b.hi, a.hi b.lo)   max(a.lo b.lo, a.hi b.hi)
+  // The four operand choices of case 3 ca + cb, as bits (lower a, lower b,
+  // upper a, upper b; 1 = the other bound) of a 4-bit field of kSel.
+  static constexpr unsigned long long kSel =
+      (0x0ull << 0) | (0x5ull << 4) | (0x1ull << 8) |    // P x P, P x N, P x M
+      (0xAull << 12) | (0xFull << 16) | (0xEull << 20) |  // N x P, N x N, N x M
+      (0x2ull << 24) | (0xDull << 28) | (0xEull << 32);   // M x P, M x N, M x M
   static __device__ __forceinline__ IV mul(const IV& a, const IV& b) {
     const int ca = cls(a), cb = cls(b);
-    const bool la_hi = (ca == 0 && cb != 0) || (cb == 1 && ca != 0);
-    const bool lb_hi = ca == 1 || (ca == 2 && cb != 1);
-    const bool ha_lo = (ca == 0 && cb == 1) || (ca != 0 && cb != 0);
-    const bool hb_lo = ca == 1 || (ca == 2 && cb != 0);
+    const int m = (int)(kSel >> (4 * (3 * ca + cb))) & 0xF;
     IV r;
-    r.lo = __dmul_rd(la_hi ? a.hi : a.lo, lb_hi ? b.hi : b.lo);
-    r.hi = __dmul_ru(ha_lo ? a.lo : a.hi, hb_lo ? b.lo : b.hi);
+    r.lo = __dmul_rd(sel(m & 1, a.hi, a.lo), sel(m & 2, b.hi, b.lo));
+    r.hi = __dmul_ru(sel(m & 4, a.lo, a.hi), sel(m & 8, b.lo, b.hi));
     if (ca == 2 && cb == 2) {
       const double l2 = __dmul_rd(a.hi, b.lo), h2 = __dmul_ru(a.hi, b.hi);
       r.lo = r.lo < l2 ? r.lo : l2;
@@ -360,8 +384,9 @@ struct IV64 {
   static __device__ __forceinline__ pw square(pw a) {
     IV r;
     const int c = cls(a);
-    r.lo = __dmul_rd(c == 1 ? a.hi : a.lo, c == 1 ? a.hi : a.lo);
-    r.hi = __dmul_ru(c == 1 ? a.lo : a.hi, c == 1 ? a.lo : a.hi);
+    const double l = sel(c == 1, a.hi, a.lo), h = sel(c == 1, a.lo, a.hi);
+    r.lo = __dmul_rd(l, l);
+    r.hi = __dmul_ru(h, h);
     if (c == 2) {
       const double h1 = __dmul_ru(a.lo, a.lo);
       r.lo = 0.0;
@@ -378,7 +403,7 @@ struct IV64 {
     if (first) {
       IV r;
       r.lo = p.lo;
-      r.hi = is_zero(p.hi) ? 0.0 : p.hi;
+      r.hi = pos_zero(p.hi);  // RU(+0 + p.hi): an exact zero sum is +0
       *dst = r;
     } else {
       const IV m = *dst;
@@ -412,6 +437,70 @@ __device__ __forceinline__ typename A::pw binexp(typename A::pw x, uint32_t d) {
     if ((d >> b) & 1u) r = A::mulx(r, x);
   }
   return r;
+}
+
+// The node walk's cursor: the next step's control word and coefficients are
+// loaded one step ahead.
+template <class C>
+struct WalkState {
+  int64_t i;
+  uint32_t c_next;
+  C a_next, b_next;
+};
+
+// bit 0: leaf, bit 1: first child
+__device__ __forceinline__ int node_kind(uint32_t c) {
+  return (int)(((c >> kCtrlLeaf) & 1u) | (((c >> kCtrlFirst) & 1u) << 1));
+}
+
+// One node of the walk (at w.i), of kind (leaf, first) -- compile-time
+// constants when called from walk_run.
+template <class A, int PPT, bool TABLE>
+__device__ __forceinline__ void walk_step(const EvalArgs& g, WalkState<typename A::coef>& w, typename A::val* acc,
+                                          typename A::pw* pw, int tid, bool leaf, bool first) {
+  using W = typename A::pw;
+  using C = typename A::coef;
+  const C* ca = reinterpret_cast<const C*>(g.ca);
+  const C* cb = reinterpret_cast<const C*>(g.cb);
+  const uint32_t c = w.c_next;
+  const C va = w.a_next, vb = w.b_next;
+  ++w.i;
+  if (w.i < g.nsteps) {
+    w.c_next = __ldg(g.ctrl + w.i);
+    w.a_next = ca[w.i];
+    w.b_next = cb[w.i];
+  }
+  const int S = (int)((c >> kCtrlS) & 63u), D = (int)((c >> kCtrlD) & 63u);
+  const int pid = (int)(c >> kCtrlPid);
+  uint32_t dv = 0, dd = 0;
+  if (!TABLE) {
+    const uint2 q = __ldg(g.pow_dv + pid);
+    dv = q.x;
+    dd = q.y;
+  }
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const W xd = TABLE ? pw[(pid * PPT + p) * kTPB + tid] : binexp<A>(pw[(dv * PPT + p) * kTPB + tid], dd);
+    A::node(leaf, first, va, vb, &acc[(S * PPT + p) * kTPB + tid], &acc[(D * PPT + p) * kTPB + tid], xd);
+  }
+}
+
+// the node at w.i, its kind read from its control word
+template <class A, int PPT, bool TABLE>
+__device__ __forceinline__ void walk_node(const EvalArgs& g, WalkState<typename A::coef>& w, typename A::val* acc,
+                                          typename A::pw* pw, int tid) {
+  const int k = node_kind(w.c_next);
+  walk_step<A, PPT, TABLE>(g, w, acc, pw, tid, k & 1, k & 2);
+}
+
+// the nodes from w.i on while they are of kind (LEAF, FIRST); at least one
+template <class A, int PPT, bool TABLE, bool LEAF, bool FIRST>
+__device__ __forceinline__ void walk_run(const EvalArgs& g, WalkState<typename A::coef>& w, typename A::val* acc,
+                                         typename A::pw* pw, int tid) {
+  constexpr int kKind = (LEAF ? 1 : 0) | (FIRST ? 2 : 0);
+  do {
+    walk_step<A, PPT, TABLE>(g, w, acc, pw, tid, LEAF, FIRST);
+  } while (w.i < g.nsteps && node_kind(w.c_next) == kKind);
 }
 
 // TABLE = true: pw holds the full power table [npow][PPT][TPB] (Sec. 2.2).
@@ -455,31 +544,28 @@ __device__ __forceinline__ void node_tile(const EvalArgs& g, int64_t base, unsig
   // coefficient walk (Sec. 2.1) over the non-root nodes
   const C* ca = reinterpret_cast<const C*>(g.ca);
   const C* cb = reinterpret_cast<const C*>(g.cb);
-  uint32_t c_next = g.nsteps > 0 ? __ldg(g.ctrl) : 0u;
-  C a_next = g.nsteps > 0 ? ca[0] : C(0);
-  C b_next = g.nsteps > 0 ? cb[0] : C(0);
-  for (int64_t i = 0; i < g.nsteps; ++i) {
-    const uint32_t c = c_next;
-    const C va = a_next, vb = b_next;
-    if (i + 1 < g.nsteps) {
-      c_next = __ldg(g.ctrl + i + 1);
-      a_next = ca[i + 1];
-      b_next = cb[i + 1];
+  WalkState<C> w;
+  w.i = 0;
+  w.c_next = g.nsteps > 0 ? __ldg(g.ctrl) : 0u;
+  w.a_next = g.nsteps > 0 ? ca[0] : C(0);
+  w.b_next = g.nsteps > 0 ? cb[0] : C(0);
+  if constexpr (A::kKindRuns) {
+    // in runs of nodes of one kind (leaf or not, first child or not): each
+    // run is a loop whose body is compiled for its kind, so a kind's missing
+    // operations are skipped by a branch rather than issued under a false
+    // predicate (which still takes their FP64 pipe slots)
+    while (w.i < g.nsteps) {
+      switch (node_kind(w.c_next)) {
+        case 0: walk_run<A, PPT, TABLE, false, false>(g, w, acc, pw, tid); break;
+        case 1: walk_run<A, PPT, TABLE, true, false>(g, w, acc, pw, tid); break;
+        case 2: walk_run<A, PPT, TABLE, false, true>(g, w, acc, pw, tid); break;
+        default: walk_run<A, PPT, TABLE, true, true>(g, w, acc, pw, tid); break;
+      }
     }
-    const int S = (int)((c >> kCtrlS) & 63u), D = (int)((c >> kCtrlD) & 63u);
-    const bool leaf = (c >> kCtrlLeaf) & 1u, first = (c >> kCtrlFirst) & 1u;
-    const int pid = (int)(c >> kCtrlPid);
-    uint32_t dv = 0, dd = 0;
-    if (!TABLE) {
-      const uint2 q = __ldg(g.pow_dv + pid);
-      dv = q.x;
-      dd = q.y;
-    }
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      const W xd = TABLE ? pw[(pid * PPT + p) * kTPB + tid] : binexp<A>(pw[(dv * PPT + p) * kTPB + tid], dd);
-      A::node(leaf, first, va, vb, &acc[(S * PPT + p) * kTPB + tid], &acc[(D * PPT + p) * kTPB + tid], xd);
-    }
+  } else {
+    // one multiply-add per node whatever its kind: the kind only selects
+    // operands
+    while (w.i < g.nsteps) walk_node<A, PPT, TABLE>(g, w, acc, pw, tid);
   }
 
   // root

@@ -113,6 +113,7 @@ struct MODQ {
   using pw = uint64_t;
   static constexpr bool kSlotAtEnd = false;
   static constexpr bool kExact = true;
+  static constexpr bool kKindRuns = false;
   static __device__ __forceinline__ uint64_t c() { return g_rns_c[blockIdx.y]; }
   static __device__ __forceinline__ coef coef_from_bits(uint64_t b) { return b; }
   static __device__ __forceinline__ uint64_t mul_add(uint64_t a, uint64_t b, uint64_t d) {

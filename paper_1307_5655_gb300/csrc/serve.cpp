@@ -48,9 +48,9 @@ size_t out_bytes_of(fp_dtype dt, int64_t npts) { return (dt == FP_IV64 ? 16 : 8)
 
 // Estimated work of a request in FP64 node-evaluations: nodes x points x the
 // value type's cost per node relative to FP64 (measured throughputs: FP32C
-// about 4x faster, intervals about 7.5x slower, residues about as fast).
+// about 4x faster, intervals about 4.7x slower, residues about as fast).
 double work_of(const fp_tree* t, fp_dtype dt, int64_t npts) {
-  const double w = dt == FP_F32C ? 0.25 : (dt == FP_IV64 ? 7.5 : 1.0);
+  const double w = dt == FP_F32C ? 0.25 : (dt == FP_IV64 ? 4.7 : 1.0);
   return w * (double)t->nnodes * (double)npts;
 }
 // below this a request is small: about 1.7 ms of FP64 work on the GPU
