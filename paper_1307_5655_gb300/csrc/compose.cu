@@ -383,8 +383,11 @@ struct Composer {
   int sms = 0;  // multiprocessors of the current device
 
   // vectors of length n <= 4096 per block of an in-shared-memory transform:
-  // as many as fill 4096 elements, fewer when that would leave the device
-  // with under two blocks per multiprocessor (short transforms of few pairs)
+  // as many as fill 1024 elements (256 threads, one radix-4 butterfly each
+  // per stage: the transforms of one product are a single partial wave, so
+  // threads rather than work per thread hide the latencies), fewer when that
+  // would leave the device with under two blocks per multiprocessor (short
+  // transforms of few pairs)
   int small_vpb(int n) {
     if (sms == 0) {
       int dev = 0;
@@ -393,7 +396,7 @@ struct Composer {
         sms = 1;
       }
     }
-    int vpb = kNttSmemMax / n;
+    int vpb = std::max(1, 1024 / n);
     while (vpb > 1 && (npairs + vpb - 1) / vpb < 2 * (int64_t)sms) vpb >>= 1;
     return vpb;
   }
