@@ -127,8 +127,6 @@ __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw, int s
   __syncthreads();
 }
 
-__device__ __forceinline__ int bitrev(int x, int logn) { return logn == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - logn)); }
-
 // ------------------------------------------------------------ MODP kernels
 // The first outlen coefficients of cnt inverse transforms in sh (vectors of
 // length n), scaled by 1/n: written (mode 0), added into out (mode 1), or
@@ -214,26 +212,24 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
 // Four-step transform of length n = R * C (R, C <= 4096), vector x[C n1 + n2].
 // Column pass: a tile of TC columns (length R, stride C) per block, all
 // transformed together; forward multiplies by w_n^(k1 n2) afterwards,
-// inverse divides before.  Row pass: rows of length C, contiguous.
+// inverse divides before.  Row pass: rows of length C, contiguous.  Position
+// r of a transformed column holds k1 = bitrev(r), so the twiddle of element
+// r C + n2 is tw4[r C + n2] = w_n^(+-bitrev(r) n2): a table in the layout of
+// the data, read with the same coalesced pattern as the data.
 __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch, int R,
-                           int C, int TC, int logR, const uint64_t* twR, const uint64_t* twn, int inverse,
-                           uint64_t scale, int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
+                           int C, int TC, const uint64_t* twR, const uint64_t* tw4, int inverse, uint64_t scale,
+                           int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
   extern __shared__ uint64_t sh[];  // [TC][R + 1]: the padding spreads a transposed row over the banks
   const int RS = R + 1;
   const int tiles = C / TC;
   const int64_t pr = blockIdx.x / tiles;
-  const int c0 = (blockIdx.x % tiles) * TC;
-  const int n = R * C, mask = n - 1;  // n, R, C, TC: powers of two
+  const int c0 = (blockIdx.x % tiles) * TC;  // R, C, TC: powers of two
   const int lTC = ilog2_dev(TC);
   for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
     const int r = e >> lTC, c = e & (TC - 1);
     const int idx = r * C + c0 + c;
     uint64_t v = idx < len ? src[pr * src_pitch + idx] : 0;
-    if (inverse) {
-      // position r holds k1 = bitrev(r); undo the twiddle w^(k1 n2)
-      const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
-      v = d_mul(v, __ldg(twn + ((n - ex) & mask)));
-    }
+    if (inverse) v = d_mul(v, __ldg(tw4 + idx));  // undo w^(k1 n2)
     sh[c * RS + r] = v;
   }
   if (inverse) ntt_dit(sh, R, TC, twR, RS);
@@ -243,8 +239,7 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
     const int idx = r * C + c0 + c;
     uint64_t v = sh[c * RS + r];
     if (!inverse) {
-      const int ex = (int)(((int64_t)bitrev(r, logR) * (c0 + c)) & mask);
-      dst[pr * dst_pitch + idx] = d_mul(v, __ldg(twn + ex));
+      dst[pr * dst_pitch + idx] = d_mul(v, __ldg(tw4 + idx));
     } else if (idx < outlen) {
       v = d_mul(v, scale);
       uint64_t* o = dst + pr * dst_pitch + idx;
@@ -376,6 +371,8 @@ struct Composer {
   std::vector<void*> owned;
   // twiddles (MODP): forward/inverse powers of w_n for every length n used
   std::map<int, std::pair<uint64_t*, uint64_t*>> tw;
+  // four-step twiddle tables (forward, inverse) per length n > 4096, n entries each
+  std::map<int, std::pair<uint64_t*, uint64_t*>> tw4;
   // when set, work space is carved from this caller-provided region instead
   // of being allocated (fp_compose_noalloc)
   unsigned char* arena = nullptr;
@@ -457,6 +454,41 @@ struct Composer {
     return tw[n];
   }
 
+  // the four-step twiddles of length n = R C in the layout of the data:
+  // forward [r C + n2] = w^(bitrev(r) n2), inverse the same with w^-1
+  std::pair<uint64_t*, uint64_t*> four_step_twiddles(int n) {
+    auto it = tw4.find(n);
+    if (it != tw4.end()) return it->second;
+    int R, C;
+    split(n, R, C);
+    int logR = 0;
+    while ((1 << logR) < R) ++logR;
+    std::vector<uint64_t> f(n), b(n);
+    const uint64_t w = h_pow(7, (kP - 1) / (uint64_t)n);
+    const uint64_t wi = h_pow(w, kP - 2);
+    for (int r = 0; r < R; ++r) {
+      int k1 = 0;  // bitrev(r) over logR bits
+      for (int j = 0; j < logR; ++j) k1 |= ((r >> j) & 1) << (logR - 1 - j);
+      const uint64_t uf = h_pow(w, (uint64_t)k1), ub = h_pow(wi, (uint64_t)k1);
+      uint64_t x = 1, y = 1;
+      for (int c = 0; c < C; ++c) {
+        f[(size_t)r * C + c] = x;
+        b[(size_t)r * C + c] = y;
+        x = h_mul(x, uf);
+        y = h_mul(y, ub);
+      }
+    }
+    uint64_t* df = (uint64_t*)alloc(n * 8);
+    uint64_t* db = (uint64_t*)alloc(n * 8);
+    if (status == FP_OK) {
+      cudaMemcpyAsync(df, f.data(), n * 8, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(db, b.data(), n * 8, cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);  // the host vectors must outlive the copies
+    }
+    tw4[n] = {df, db};
+    return tw4[n];
+  }
+
   static void split(int n, int& R, int& C) {
     int lg = 0;
     while ((1 << lg) < n) ++lg;
@@ -478,10 +510,10 @@ struct Composer {
       const int TC = kNttSmemMax / R;
       auto wR = twiddles(R);
       auto wC = twiddles(C);
-      auto wn = twiddles(n);
+      auto w4 = four_step_twiddles(n);
       k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
-          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, ilog2(R), wR.first,
-          wn.first, 0, 1, 0, 0, nullptr, 0);
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, wR.first, w4.first, 0,
+          1, 0, 0, nullptr, 0);
       const int vpb = kNttSmemMax / C;
       k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
           (uint64_t*)dst.ptr, dst.pitch, R, C, vpb, wC.first, 0, nullptr, 0);
@@ -507,13 +539,13 @@ struct Composer {
       const int TC = kNttSmemMax / R;
       auto wR = twiddles(R);
       auto wC = twiddles(C);
-      auto wn = twiddles(n);
+      auto w4 = four_step_twiddles(n);
       const int vpb = kNttSmemMax / C;
       k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
           (uint64_t*)fa.ptr, fa.pitch, R, C, vpb, wC.second, 1, (const uint64_t*)fbuf.ptr, fbuf.pitch);
       k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
-          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, ilog2(R), wR.second,
-          wn.first, 1, ninv, outlen, mode, init, init_pitch);
+          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, wR.second, w4.second, 1,
+          ninv, outlen, mode, init, init_pitch);
     }
     check();
   }
@@ -767,7 +799,7 @@ size_t compose_workspace_bytes(const fp_tree* t, bool modp, bool shared_coeffs, 
   auto use = [&](int64_t rl, int bk) {
     const int64_t n = next_pow2(rl);
     if (n <= kNttSmemMax) tw[n] = 1;
-    else {
+    else {  // tables of R, C and the four-step table of n (all 2 x length entries)
       int lg = 0;
       while ((1ll << lg) < n) ++lg;
       const int64_t C = 1ll << ((lg + 1) / 2);
