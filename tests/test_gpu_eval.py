@@ -176,6 +176,44 @@ def test_sparse_root_degree_and_gaps():
         check_iv64(e, c, lo, hi, s, run(t, "iv64", (lo, hi)))
 
 
+def _wide_boxes(nvars, npts, seed):
+    """Boxes of every sign class (non-negative, non-positive, straddling 0):
+    centres U[-1, 1], widths from {0.3, 1, 1.5}, and a few with a bound that
+    is exactly zero or a degenerate [0, 0]."""
+    c = W.points_f64(nvars, npts, seed)
+    w = np.array([0.3, 1.0, 1.5])[W.rng(seed + 1).integers(0, 3, size=c.shape)]
+    lo, hi = c - w / 2, c + w / 2
+    lo[:, 0], hi[:, 0] = 0.0, 0.5
+    lo[:, 1], hi[:, 1] = -0.5, 0.0
+    lo[:, 2], hi[:, 2] = 0.0, 0.0
+    lo[:, 3], hi[:, 3] = -0.7, 0.7
+    return lo, hi
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("k", [5, 64, 300])
+def test_iv64_wide_boxes_every_sign_case(k, scheme):
+    """Interval products in all nine sign cases (Moore's table): boxes wide
+    enough that points and partial sums straddle zero, bit-exact against the
+    oracle's walk, whose product takes the min and max of all four products."""
+    e = W.dense_univariate_exps(k)
+    c = W.uniform_f64(k, 70 + k)
+    lo, hi = _wide_boxes(1, 1000 + 9, 71 + k)
+    cls = np.where(lo >= 0, 0, np.where(hi <= 0, 1, 2))
+    assert set(np.unique(cls)) == {0, 1, 2}
+    t = fpl.fp_compile(e, c, scheme)
+    check_iv64(e, c, lo, hi, scheme, run(t, "iv64", (lo, hi)))
+
+
+def test_iv64_wide_boxes_bivariate():
+    e = _multi(2, "total", 12, 72)
+    c = W.uniform_f64(len(e), 73)
+    lo, hi = _wide_boxes(2, 700 + 5, 74)
+    for s in SCHEMES:
+        t = fpl.fp_compile(e, c, s)
+        check_iv64(e, c, lo, hi, s, run(t, "iv64", (lo, hi)))
+
+
 def test_deep_lazy_height_custom_scheme():
     """Random function schemes give lazy heights well above E/B's."""
     k = 3000
