@@ -382,6 +382,9 @@ int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, co
  *   FP_RATE_MODP_MULADD  (a b + c) mod p (one MODP node)
  *   FP_RATE_MODP_BUTTERFLY  (a, b) -> (a + w b, a - w b) mod p (one radix-2
  *                        butterfly of the number-theoretic transforms)
+ *   FP_RATE_IMAD         32-bit integer multiply-add, a b + c mod 2^32
+ *   FP_RATE_IMAD_WIDE    32 x 32 -> 64-bit product plus a 64-bit addend (the
+ *                        partial products of the 64-bit arithmetic mod p)
  * An interval walk costs 4 directed-rounding operations per node (a product,
  * 2, plus the coefficient's addition at a parent or the accumulation at a
  * non-first child, 2): its bound is FP_RATE_DADD_RD / 4 (products issue at
@@ -396,7 +399,9 @@ enum {
   FP_RATE_F32C_HORNER = 5,
   FP_RATE_MODP_MULADD = 6,
   FP_RATE_MODP_BUTTERFLY = 7,
-  FP_RATE_COUNT = 8
+  FP_RATE_IMAD = 8,
+  FP_RATE_IMAD_WIDE = 9,
+  FP_RATE_COUNT = 10
 };
 int fp_measure_rates(double* rates, int nrates, void* stream);
 

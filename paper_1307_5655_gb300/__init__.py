@@ -283,7 +283,8 @@ def limbs_to_int(limbs):
     return v - (1 << (64 * k)) if v >> (64 * k - 1) else v
 
 
-RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd", "modp_butterfly")
+RATE_NAMES = ("dfma", "dadd_rd", "dmul_ru", "ffma", "f32c_mad", "f32c_horner", "modp_muladd", "modp_butterfly",
+              "imad", "imad_wide")
 
 
 def fp_measure_rates(stream=None):

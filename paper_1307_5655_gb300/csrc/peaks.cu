@@ -20,6 +20,7 @@ struct Params {
   double d[4];
   float f[4];
   uint64_t u[2];
+  uint32_t w[2];
 };
 
 struct OpDfma {
@@ -83,6 +84,19 @@ struct OpModpMulAdd {
   static __device__ T step(const Params& q, T a) { return MODP::mul_add(a, q.u[1], q.u[0]); }
   static __device__ double out(T a) { return (double)a; }
 };
+struct OpImad {
+  using T = uint32_t;
+  static __device__ T init(const Params& q, int j) { return q.w[0] + j + threadIdx.x; }
+  static __device__ T step(const Params& q, T a) { return a * q.w[0] + q.w[1]; }
+  static __device__ double out(T a) { return (double)a; }
+};
+struct OpImadWide {  // the low half of the previous value times a 32-bit word, plus a 64-bit addend
+  using T = uint64_t;
+  static __device__ T init(const Params& q, int j) { return q.u[0] + j + threadIdx.x; }
+  static __device__ T step(const Params& q, T a) { return (uint64_t)(uint32_t)a * q.w[0] + q.u[1]; }
+  static __device__ double out(T a) { return (double)a; }
+};
+
 template <class Op>
 __global__ void __launch_bounds__(kThreads) k_rate(const Params* prm, double* out, int iters) {
   const Params q = *prm;
@@ -148,6 +162,7 @@ extern "C" int fp_measure_rates(double* rates, int nrates, void* stream) {
   h.d[0] = 0.5; h.d[1] = 0.999999; h.d[2] = 1e-7; h.d[3] = 1e-12;
   h.f[0] = 0.5f; h.f[1] = 0.9999f; h.f[2] = 1e-4f; h.f[3] = 1e-9f;
   h.u[0] = 0x9E3779B97F4A7C15ull % 0xFFFFFFFF00000001ull; h.u[1] = 0x1234567890ABCDEull;
+  h.w[0] = 0x9E3779B1u; h.w[1] = 0x7F4A7C15u;
   int rc = cudaMemcpy(prm, &h, sizeof(Params), cudaMemcpyHostToDevice) == cudaSuccess ? FP_OK : FP_E_CUDA;
   for (int i = 0; i < nrates && rc == FP_OK; ++i) {
     double g = 0;
@@ -160,6 +175,8 @@ extern "C" int fp_measure_rates(double* rates, int nrates, void* stream) {
       case FP_RATE_F32C_HORNER: rc = time_rate<OpF32cHorner>(prm, out, blocks, 8192, st, g); break;
       case FP_RATE_MODP_MULADD: rc = time_rate<OpModpMulAdd>(prm, out, blocks, 2048, st, g); break;
       case FP_RATE_MODP_BUTTERFLY: rc = time_rate<OpModpButterfly>(prm, out, blocks, 2048, st, g); break;
+      case FP_RATE_IMAD: rc = time_rate<OpImad>(prm, out, blocks, 16384, st, g); break;
+      case FP_RATE_IMAD_WIDE: rc = time_rate<OpImadWide>(prm, out, blocks, 16384, st, g); break;
       default: break;
     }
     rates[i] = g;

@@ -15,3 +15,7 @@ def test_measure_rates():
     assert r["ffma"] > 10 * r["dfma"]
     assert r["f32c_mad"] < r["ffma"] / 6
     assert r["f32c_mad"] < r["f32c_horner"] < r["ffma"] / 6
+    # integer multiply-adds: GB300's FP64 rate is far below its integer one,
+    # and a 64-bit product mod p takes several 32 x 32 partial products
+    assert r["imad"] > 4 * r["dfma"]
+    assert r["imad_wide"] > r["modp_muladd"]
