@@ -768,6 +768,108 @@ def run_staircase(args):
                       "results": res}))
 
 
+def run_batched(args):
+    """Many FP64 univariate polynomials of uneven size -- the FP64 univariate
+    part of the serving mix: k log-uniform in [8, 65536] dense terms, points
+    log-uniform in [1, 2^20], coefficients and points uniform[-1, 1], scheme E
+    (B when k is not a power of two) -- the batched and served forms against
+    the plain one-launch-per-polynomial FP64 kernel (one thread per point,
+    Horner) on the same inputs.  Device-resident: one fp_eval_batch call (it
+    plans the batch every call), a planned batch (fp_batch_create once,
+    launch only), and the plain kernel once per polynomial back to back on
+    one stream.  Host buffers (pinned): the server (submit all, drain) and the
+    plain kernel once per polynomial with its copy in and copy out on one
+    stream.  Wall time around each pass (synchronized), median of 3 after a
+    warm-up pass; every result is checked against the plain kernel's within
+    8 k u S (S = sum |c_e| |x|^e, both are FP64 evaluations within 4 k u S)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    r = W.rng(6000)
+    n = args.batch_polys
+    polys = []
+    for i in range(n):
+        k = int(np.exp(r.uniform(np.log(8), np.log(65536))))
+        npts = int(np.exp(r.uniform(0, np.log(1 << 20))))
+        e, c, x = W.univariate_case(k, npts, 6100 + i)
+        t = fpl.fp_compile(e, c, "E" if (k & (k - 1)) == 0 else "B")
+        polys.append((k, npts, t, c, x))
+    evals = sum(k * m for k, m, _, _, _ in polys)
+    dev = torch.device("cuda")
+    coef_d = [torch.from_numpy(c[::-1].copy()).to(dev) for _, _, _, c, _ in polys]
+    pts_d = [torch.from_numpy(x).to(dev) for _, _, _, _, x in polys]
+    out_plain = [torch.empty(m, dtype=torch.float64, device=dev) for _, m, _, _, _ in polys]
+    out_batch = [torch.empty((1, m), dtype=torch.float64, device=dev) for _, m, _, _, _ in polys]
+    jobs = [(t, pts_d[i], out_batch[i]) for i, (_, _, t, _, _) in enumerate(polys)]
+    pts_h = [torch.from_numpy(x).pin_memory() for _, _, _, _, x in polys]
+    out_h = [torch.empty(m, dtype=torch.float64).pin_memory() for _, m, _, _, _ in polys]
+    out_srv = [torch.empty((1, m), dtype=torch.float64).pin_memory().numpy() for _, m, _, _, _ in polys]
+
+    def wall(fn):
+        ts = []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            if rep:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts))
+
+    def plain_device():
+        for i in range(n):
+            fpl.fp_eval_plain_f64(coef_d[i], pts_d[i], out=out_plain[i])
+
+    def batch_call():
+        fpl.fp_eval_batch("f64", jobs)
+
+    planned = fpl.Batch("f64", jobs)
+
+    def plain_host():
+        for i in range(n):
+            d = pts_h[i].to(dev, non_blocking=True)
+            o = fpl.fp_eval_plain_f64(coef_d[i], d)
+            out_h[i].copy_(o, non_blocking=True)
+
+    srv = fpl.Server(hbm_budget_bytes=args.hbm_budget << 20, max_batch_jobs=256, streams=4)
+    pts_srv = [p.numpy() for p in pts_h]
+
+    def served():
+        for i, (_, _, t, _, _) in enumerate(polys):
+            srv.submit(t, "f64", pts_srv[i], out_srv[i])
+        srv.drain(3600)
+        done = srv.poll()
+        assert len(done) == n and all(st == 0 for _, st, _ in done), "server requests failed"
+
+    res = {"plain_one_launch_per_poly_ms": wall(plain_device), "fp_eval_batch_ms": wall(batch_call),
+           "planned_batch_launch_ms": wall(planned.launch)}
+    res["speedup_fp_eval_batch"] = res["plain_one_launch_per_poly_ms"] / res["fp_eval_batch_ms"]
+    res["speedup_planned_batch"] = res["plain_one_launch_per_poly_ms"] / res["planned_batch_launch_ms"]
+    host = {"plain_with_copies_ms": wall(plain_host), "server_ms": wall(served)}
+    host["speedup_server"] = host["plain_with_copies_ms"] / host["server_ms"]
+    # the results agree within the FP64 bound
+    worst = 0.0
+    for i, (k, m, _, c, x) in enumerate(polys):
+        S = fpl.fp_eval_plain_f64(coef_d[i].abs(), pts_d[i].abs()).cpu().numpy()
+        ref = out_plain[i].cpu().numpy()
+        for got in (out_batch[i][0].cpu().numpy(), out_h[i].numpy(), out_srv[i][0]):
+            worst = max(worst, float(np.max(np.abs(got - ref) / (8 * k * 2.0 ** -53 * S + 1e-300))))
+    planned.free()
+    srv.close()
+    line = {"metric": "ms per batch of %d FP64 polynomials of uneven size" % n,
+            "workload": "univariate dense, k log-uniform [8, 65536], points log-uniform [1, 2^20], "
+                        "E (B for k not a power of two), uniform[-1, 1]",
+            "term_evals": int(evals), "device_resident": res, "host_buffers": host,
+            "G_term_evals_per_s": {"plain": evals / res["plain_one_launch_per_poly_ms"] / 1e6,
+                                   "fp_eval_batch": evals / res["fp_eval_batch_ms"] / 1e6,
+                                   "planned_batch": evals / res["planned_batch_launch_ms"] / 1e6,
+                                   "server_host_buffers": evals / host["server_ms"] / 1e6,
+                                   "plain_host_buffers": evals / host["plain_with_copies_ms"] / 1e6},
+            "max_error_over_8kuS": worst, "n_gpus": 1, "data": "synthetic"}
+    print(json.dumps(line))
+
+
 def run_peaks(args):
     """Roofline denominators measured with the library's own arithmetic
     (fp_measure_rates), with the SM clock sampled while they run."""
@@ -888,10 +990,11 @@ def run_hybrid(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve", "accuracy",
-                                                                "staircase", "hybrid", "peaks", "rns"],
+                                                                "staircase", "hybrid", "peaks", "rns", "batched"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--batch-polys", type=int, default=256, help="polynomials of --workload batched")
     ap.add_argument("--hbm-budget", type=int, default=8192, help="MiB of device memory for requests in flight")
     ap.add_argument("--profile-case", action="store_true",
                     help="run two launches of one evaluation (for ncu) and exit")
@@ -925,6 +1028,8 @@ def main():
         run_hybrid(args)
     elif args.workload == "peaks":
         run_peaks(args)
+    elif args.workload == "batched":
+        run_batched(args)
     elif args.workload == "rns":
         run_rns(args)
     elif args.impl == "reference":
