@@ -415,8 +415,10 @@ def compose_work(t, degq, modp):
     the walk's products as the library sizes them.  MODP: (butterflies,
     multiplications) -- a transform of length n is (n/2) log2 n radix-2
     butterflies (one multiplication, one addition, one subtraction each);
-    pointwise products, scaling by 1/n, four-step twiddles and leaf scalings
-    are single multiplications.  FP64: (0, multiply-adds of the direct
+    pointwise products, four-step twiddles and leaf scalings are single
+    multiplications (the inverse transform's 1/n rides on the inverse
+    four-step twiddles, or on the cached transform of q^d for n <= 4096,
+    scaled once when cached).  FP64: (0, multiply-adds of the direct
     convolutions)."""
     import math
     ex = t.export()
@@ -461,7 +463,9 @@ def compose_work(t, degq, modp):
         if (bkey, n) not in cached:          # transform of q^d, once per length
             cached.add((bkey, n))
             ntt(n)
-        mul += n + rl                        # pointwise, scaling
+            if n <= 4096:
+                mul += n                     # scaled by 1/n once
+        mul += n                             # pointwise
         ntt(n)                               # inverse
 
     for d in sorted(need):

@@ -129,8 +129,10 @@ __device__ void ntt_dit(uint64_t* a, int n, int count, const uint64_t* tw, int s
 
 // ------------------------------------------------------------ MODP kernels
 // The first outlen coefficients of cnt inverse transforms in sh (vectors of
-// length n), scaled by 1/n: written (mode 0), added into out (mode 1), or
-// written with init[pair] added at degree 0 (mode 2).
+// length n), scaled by 1/n (SCALE; else the scale is already in them):
+// written (mode 0), added into out (mode 1), or written with init[pair] added
+// at degree 0 (mode 2).
+template <bool SCALE>
 __device__ __forceinline__ void store_product(const uint64_t* sh, int n, int cnt, int64_t p0, uint64_t ninv,
                                               uint64_t* out, int64_t out_pitch, int outlen, int mode,
                                               const uint64_t* init, int64_t init_pitch) {
@@ -139,7 +141,7 @@ __device__ __forceinline__ void store_product(const uint64_t* sh, int n, int cnt
     const int v = e >> logn, i = e & (n - 1);
     if (i >= outlen) continue;
     uint64_t* o = out + (p0 + v) * out_pitch + i;
-    uint64_t val = d_mul(sh[e], ninv);
+    uint64_t val = SCALE ? d_mul(sh[e], ninv) : sh[e];
     if (mode == 1) val = d_add(*o, val);
     else if (mode == 2 && i == 0) val = d_add(val, init[(p0 + v) * init_pitch]);
     *o = val;
@@ -147,9 +149,9 @@ __device__ __forceinline__ void store_product(const uint64_t* sh, int n, int cnt
 }
 
 // Forward transform of length n <= 4096 of src[pair][0..len) zero-padded,
-// into dst[pair][0..n); vpb pairs per block.
+// times `scale`, into dst[pair][0..n); vpb pairs per block.
 __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch,
-                                int n, int vpb, int64_t npairs, const uint64_t* tw) {
+                                int n, int vpb, int64_t npairs, const uint64_t* tw, uint64_t scale) {
   extern __shared__ uint64_t sh[];
   const int64_t p0 = (int64_t)blockIdx.x * vpb;
   const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
@@ -161,7 +163,7 @@ __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len,
   ntt_dif(sh, n, vpb, tw, n);
   for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
     const int v = e >> logn, i = e & (n - 1);
-    dst[(p0 + v) * dst_pitch + i] = sh[e];
+    dst[(p0 + v) * dst_pitch + i] = scale == 1 ? sh[e] : d_mul(sh[e], scale);
   }
 }
 
@@ -181,17 +183,18 @@ __global__ void k_ntt_mul_inv_small(const uint64_t* prod, int64_t pitch, const u
     sh[e] = v < cnt ? d_mul(prod[(p0 + v) * pitch + i], fb[(p0 + v) * fb_pitch + i]) : 0;
   }
   ntt_dit(sh, n, vpb, twi, n);
-  store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
+  store_product<true>(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
 // A whole product for n <= 4096, one launch: transform of src (first len
-// coefficients, zero-padded), times the cached transform fb, inverse, scaled
-// by 1/n, written per mode as in k_ntt_mul_inv_small.  src may be the
-// destination: a block reads its rows completely before writing them.
+// coefficients, zero-padded), times the cached transform fb (which carries
+// the 1/n of the inverse), inverse, written per mode as in
+// k_ntt_mul_inv_small.  src may be the destination: a block reads its rows
+// completely before writing them.
 __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int len, const uint64_t* fb,
                                     int64_t fb_pitch, int n, int vpb, int64_t npairs, const uint64_t* tw,
-                                    const uint64_t* twi, uint64_t ninv, uint64_t* out, int64_t out_pitch, int outlen,
-                                    int mode, const uint64_t* init, int64_t init_pitch) {
+                                    const uint64_t* twi, uint64_t* out, int64_t out_pitch, int outlen, int mode,
+                                    const uint64_t* init, int64_t init_pitch) {
   extern __shared__ uint64_t sh[];
   const int64_t p0 = (int64_t)blockIdx.x * vpb;
   const int cnt = (int)(npairs - p0 < vpb ? npairs - p0 : vpb);
@@ -206,7 +209,7 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
     if (v < cnt) sh[e] = d_mul(sh[e], fb[(p0 + v) * fb_pitch + i]);
   }
   ntt_dit(sh, n, vpb, twi, n);
-  store_product(sh, n, cnt, p0, ninv, out, out_pitch, outlen, mode, init, init_pitch);
+  store_product<false>(sh, n, cnt, p0, 1, out, out_pitch, outlen, mode, init, init_pitch);
 }
 
 // Four-step transform of length n = R * C (R, C <= 4096), vector x[C n1 + n2].
@@ -215,10 +218,11 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
 // inverse divides before.  Row pass: rows of length C, contiguous.  Position
 // r of a transformed column holds k1 = bitrev(r), so the twiddle of element
 // r C + n2 is tw4[r C + n2] = w_n^(+-bitrev(r) n2): a table in the layout of
-// the data, read with the same coalesced pattern as the data.
+// the data, read with the same coalesced pattern as the data (the inverse
+// table also carries the 1/n of the inverse transform).
 __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint64_t* dst, int64_t dst_pitch, int R,
-                           int C, int TC, const uint64_t* twR, const uint64_t* tw4, int inverse, uint64_t scale,
-                           int outlen, int mode, const uint64_t* init, int64_t init_pitch) {
+                           int C, int TC, const uint64_t* twR, const uint64_t* tw4, int inverse, int outlen, int mode,
+                           const uint64_t* init, int64_t init_pitch) {
   extern __shared__ uint64_t sh[];  // [TC][R + 1]: the padding spreads a transposed row over the banks
   const int RS = R + 1;
   const int tiles = C / TC;
@@ -241,7 +245,6 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
     if (!inverse) {
       dst[pr * dst_pitch + idx] = d_mul(v, __ldg(tw4 + idx));
     } else if (idx < outlen) {
-      v = d_mul(v, scale);
       uint64_t* o = dst + pr * dst_pitch + idx;
       if (mode == 1) v = d_add(*o, v);
       else if (mode == 2 && idx == 0) v = d_add(v, init[pr * init_pitch]);
@@ -455,7 +458,8 @@ struct Composer {
   }
 
   // the four-step twiddles of length n = R C in the layout of the data:
-  // forward [r C + n2] = w^(bitrev(r) n2), inverse the same with w^-1
+  // forward [r C + n2] = w^(bitrev(r) n2), inverse w^-(bitrev(r) n2) / n (the
+  // inverse transform's scaling rides on its twiddle)
   std::pair<uint64_t*, uint64_t*> four_step_twiddles(int n) {
     auto it = tw4.find(n);
     if (it != tw4.end()) return it->second;
@@ -465,12 +469,12 @@ struct Composer {
     while ((1 << logR) < R) ++logR;
     std::vector<uint64_t> f(n), b(n);
     const uint64_t w = h_pow(7, (kP - 1) / (uint64_t)n);
-    const uint64_t wi = h_pow(w, kP - 2);
+    const uint64_t wi = h_pow(w, kP - 2), ninv = h_pow((uint64_t)n, kP - 2);
     for (int r = 0; r < R; ++r) {
       int k1 = 0;  // bitrev(r) over logR bits
       for (int j = 0; j < logR; ++j) k1 |= ((r >> j) & 1) << (logR - 1 - j);
       const uint64_t uf = h_pow(w, (uint64_t)k1), ub = h_pow(wi, (uint64_t)k1);
-      uint64_t x = 1, y = 1;
+      uint64_t x = 1, y = ninv;
       for (int c = 0; c < C; ++c) {
         f[(size_t)r * C + c] = x;
         b[(size_t)r * C + c] = y;
@@ -496,14 +500,15 @@ struct Composer {
     R = n / C;
   }
 
-  // forward transform of length n of src (first len coefficients) into dst
-  void fwd(const Buf& src, int len, const Buf& dst, int n) {
+  // forward transform of length n of src (first len coefficients) into dst;
+  // for n <= 4096 times `scale`
+  void fwd(const Buf& src, int len, const Buf& dst, int n, uint64_t scale = 1) {
     if (status != FP_OK) return;
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
       const int vpb = small_vpb(n);
       k_ntt_fwd_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
-          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, n, vpb, npairs, w.first);
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, n, vpb, npairs, w.first, scale);
     } else {
       int R, C;
       split(n, R, C);
@@ -512,8 +517,8 @@ struct Composer {
       auto wC = twiddles(C);
       auto w4 = four_step_twiddles(n);
       k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
-          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, wR.first, w4.first, 0,
-          1, 0, 0, nullptr, 0);
+          (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, wR.first, w4.first, 0, 0,
+          0, nullptr, 0);
       const int vpb = kNttSmemMax / C;
       k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
           (uint64_t*)dst.ptr, dst.pitch, R, C, vpb, wC.first, 0, nullptr, 0);
@@ -545,7 +550,7 @@ struct Composer {
           (uint64_t*)fa.ptr, fa.pitch, R, C, vpb, wC.second, 1, (const uint64_t*)fbuf.ptr, fbuf.pitch);
       k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
           (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, wR.second, w4.second, 1,
-          ninv, outlen, mode, init, init_pitch);
+          outlen, mode, init, init_pitch);
     }
     check();
   }
@@ -629,14 +634,16 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
   Buf ta{cm.alloc(npairs * Lmax * esz), Lmax}, tb{cm.alloc(npairs * Lmax * esz), Lmax};
   if (cm.status != FP_OK) { cm.release(); return cm.status; }
-  // transforms of the powers q^d at the lengths they are used at
+  // transforms of the powers q^d at the lengths they are used at; for
+  // n <= 4096 (used only by the fused product kernel) times 1/n, the scaling
+  // of the products' inverse transforms
   std::map<std::pair<int, int64_t>, Buf> qhat;
   auto qhat_of = [&](int k, int64_t n) -> Buf {
     auto key = std::make_pair(k, n);
     auto it = qhat.find(key);
     if (it != qhat.end()) return it->second;
     Buf b{cm.alloc(npairs * n * esz), n};
-    cm.fwd(qp[k], (int)qp[k].pitch, b, (int)n);
+    cm.fwd(qp[k], (int)qp[k].pitch, b, (int)n, n <= kNttSmemMax ? h_pow((uint64_t)n, kP - 2) : 1);
     qhat[key] = b;
     return b;
   };
@@ -651,10 +658,9 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
         if (cm.status != FP_OK) return;
         auto w = cm.twiddles(n);
         const int vpb = cm.small_vpb(n);
-        const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
         k_ntt_product_small<<<(unsigned)((npairs + vpb - 1) / vpb), cm.small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
             (const uint64_t*)A.ptr, A.pitch, (int)alen, (const uint64_t*)fb.ptr, fb.pitch, n, vpb, npairs, w.first,
-            w.second, ninv, (uint64_t*)dst.ptr, dst.pitch, (int)rl, mode, (const uint64_t*)init, init_pitch);
+            w.second, (uint64_t*)dst.ptr, dst.pitch, (int)rl, mode, (const uint64_t*)init, init_pitch);
         cm.check();
         return;
       }
