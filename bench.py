@@ -109,6 +109,13 @@ def cpu_oracle_rate(npoints=CPU_SAMPLE_POINTS):
     return evals / wall, cores, wall
 
 
+def cpu_oracle_rate_single(npoints=1 << 13):
+    """The same oracle in this process, one core: term-evals per second over
+    npoints points of every (k, value type)."""
+    wall = sum(_oracle_chunk((k, 0, npoints, SEED + k)) for k in KS)
+    return sum(KS) * npoints * len(DTYPES) / wall
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -324,7 +331,9 @@ def run_ours(args):
             rate, cores, wall = cpu_oracle_rate()
             cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "2^18 points per (k, value type) of the same workload; the plain-sum oracle does not "
-                             "depend on the scheme (%.1f s wall)" % wall}
+                             "depend on the scheme (%.1f s wall)" % wall,
+                   "single_thread": {"value": cpu_oracle_rate_single() / 1e9, "unit": UNIT, "cores": 1,
+                                     "sample": "2^13 points per (k, value type), in this process"}}
         traffic = None
         tf = os.path.join(ROOT, "profiles", "eval_f64_traffic.txt")
         if os.path.exists(tf):
