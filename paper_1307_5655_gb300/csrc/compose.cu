@@ -253,19 +253,34 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
   }
 }
 
-// rows (length C) of data[pair][R][C], vpb rows per block; the inverse pass
-// first multiplies by the matching rows of fb
-__global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, int vpb, const uint64_t* twC, int inverse,
-                           const uint64_t* fb, int64_t fb_pitch) {
+// forward row pass: rows (length C) of data[pair][R][C], vpb rows per block
+__global__ void k_ntt_rows(uint64_t* data, int64_t pitch, int R, int C, int vpb, const uint64_t* twC) {
   extern __shared__ uint64_t sh[];
   const int per_pair = R / vpb;
   const int64_t pr = blockIdx.x / per_pair;
   const int r0 = (blockIdx.x % per_pair) * vpb;
   uint64_t* rows = data + pr * pitch + (int64_t)r0 * C;
-  const uint64_t* frows = fb ? fb + pr * fb_pitch + (int64_t)r0 * C : nullptr;
-  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = frows ? d_mul(rows[e], frows[e]) : rows[e];
-  if (inverse) ntt_dit(sh, C, vpb, twC, C);
-  else ntt_dif(sh, C, vpb, twC, C);
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = rows[e];
+  ntt_dif(sh, C, vpb, twC, C);
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) rows[e] = sh[e];
+}
+
+// The row pass of a whole product: rows of the column-transformed A
+// (data[pair][R][C], vpb rows per block) are transformed forward, multiplied
+// by the matching rows of the transform fb, and transformed back, in shared
+// memory: one pass over the data instead of a forward and an inverse pass.
+__global__ void k_ntt_rows_product(uint64_t* data, int64_t pitch, int R, int C, int vpb, const uint64_t* twC,
+                                   const uint64_t* twCi, const uint64_t* fb, int64_t fb_pitch) {
+  extern __shared__ uint64_t sh[];
+  const int per_pair = R / vpb;
+  const int64_t pr = blockIdx.x / per_pair;
+  const int r0 = (blockIdx.x % per_pair) * vpb;
+  uint64_t* rows = data + pr * pitch + (int64_t)r0 * C;
+  const uint64_t* frows = fb + pr * fb_pitch + (int64_t)r0 * C;
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = rows[e];
+  ntt_dif(sh, C, vpb, twC, C);
+  for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) sh[e] = d_mul(sh[e], frows[e]);
+  ntt_dit(sh, C, vpb, twCi, C);
   for (int e = threadIdx.x; e < vpb * C; e += blockDim.x) rows[e] = sh[e];
 }
 
@@ -521,37 +536,46 @@ struct Composer {
           0, nullptr, 0);
       const int vpb = kNttSmemMax / C;
       k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
-          (uint64_t*)dst.ptr, dst.pitch, R, C, vpb, wC.first, 0, nullptr, 0);
+          (uint64_t*)dst.ptr, dst.pitch, R, C, vpb, wC.first);
     }
     check();
   }
 
-  // out = first outlen coefficients of inverse(F(A) * F(B)), per mode;
-  // fa is overwritten
+  // out = first outlen coefficients of A * B for n > 4096, per mode, given
+  // fb = F(B): column pass of A into work, one row pass for the forward
+  // transform, the product and the inverse, inverse column pass into out
+  void product_large(const Buf& a, int len, const Buf& fbuf, const Buf& work, int n, const Buf& out, int outlen,
+                     int mode, const uint64_t* init, int64_t init_pitch) {
+    if (status != FP_OK) return;
+    int R, C;
+    split(n, R, C);
+    const int TC = kNttSmemMax / R;
+    auto wR = twiddles(R);
+    auto wC = twiddles(C);
+    auto w4 = four_step_twiddles(n);
+    k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
+        (const uint64_t*)a.ptr, a.pitch, len, (uint64_t*)work.ptr, work.pitch, R, C, TC, wR.first, w4.first, 0, 0, 0,
+        nullptr, 0);
+    const int vpb = kNttSmemMax / C;
+    k_ntt_rows_product<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
+        (uint64_t*)work.ptr, work.pitch, R, C, vpb, wC.first, wC.second, (const uint64_t*)fbuf.ptr, fbuf.pitch);
+    k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
+        (const uint64_t*)work.ptr, work.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, wR.second, w4.second, 1,
+        outlen, mode, init, init_pitch);
+    check();
+  }
+
+  // out = first outlen coefficients of inverse(F(A) * F(B)) for n <= 4096,
+  // per mode (longer products go through product_large)
   void mul_inv(const Buf& fa, const Buf& fbuf, int n, const Buf& out, int outlen, int mode, const uint64_t* init,
                int64_t init_pitch) {
     if (status != FP_OK) return;
     const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
-    if (n <= kNttSmemMax) {
-      auto w = twiddles(n);
-      const int vpb = small_vpb(n);
-      k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
-          (const uint64_t*)fa.ptr, fa.pitch, (const uint64_t*)fbuf.ptr, fbuf.pitch, n, vpb, npairs, w.second, ninv,
-          (uint64_t*)out.ptr, out.pitch, outlen, mode, init, init_pitch);
-    } else {
-      int R, C;
-      split(n, R, C);
-      const int TC = kNttSmemMax / R;
-      auto wR = twiddles(R);
-      auto wC = twiddles(C);
-      auto w4 = four_step_twiddles(n);
-      const int vpb = kNttSmemMax / C;
-      k_ntt_rows<<<(unsigned)(npairs * (R / vpb)), 256, (size_t)vpb * C * 8, st>>>(
-          (uint64_t*)fa.ptr, fa.pitch, R, C, vpb, wC.second, 1, (const uint64_t*)fbuf.ptr, fbuf.pitch);
-      k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
-          (const uint64_t*)fa.ptr, fa.pitch, n, (uint64_t*)out.ptr, out.pitch, R, C, TC, wR.second, w4.second, 1,
-          outlen, mode, init, init_pitch);
-    }
+    auto w = twiddles(n);
+    const int vpb = small_vpb(n);
+    k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
+        (const uint64_t*)fa.ptr, fa.pitch, (const uint64_t*)fbuf.ptr, fbuf.pitch, n, vpb, npairs, w.second, ninv,
+        (uint64_t*)out.ptr, out.pitch, outlen, mode, init, init_pitch);
     check();
   }
 };
@@ -662,6 +686,14 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
             (const uint64_t*)A.ptr, A.pitch, (int)alen, (const uint64_t*)fb.ptr, fb.pitch, n, vpb, npairs, w.first,
             w.second, (uint64_t*)dst.ptr, dst.pitch, (int)rl, mode, (const uint64_t*)init, init_pitch);
         cm.check();
+        return;
+      }
+      if (n > kNttSmemMax) {
+        Buf fb = tb;
+        if (bk >= 0) fb = qhat_of(bk, n);
+        else cm.fwd(B, (int)blen, tb, n);
+        if (cm.status != FP_OK) return;
+        cm.product_large(A, (int)alen, fb, ta, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
         return;
       }
       cm.fwd(A, (int)alen, ta, n);
