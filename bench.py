@@ -423,8 +423,10 @@ def compose_work(t, degq, modp):
     """Algorithmic operations of one batched composition per pair, following
     the walk's products as the library sizes them.  MODP: (butterflies,
     multiplications) -- a transform of length n is (n/2) log2 n radix-2
-    butterflies (one multiplication, one addition, one subtraction each);
-    pointwise products, four-step twiddles and leaf scalings are single
+    butterflies (one multiplication, one addition, one subtraction each),
+    except that the first stage of a zero-padded operand (length <= n/2) is
+    n/2 single multiplications; pointwise products, four-step twiddles and
+    leaf scalings are single
     multiplications (the inverse transform's 1/n rides on the inverse
     four-step twiddles, or on the cached transform of q^d for n <= 4096,
     scaled once when cached).  FP64: (0, multiply-adds of the direct
@@ -455,9 +457,14 @@ def compose_work(t, degq, modp):
     cached = set()
     bfly, mul = 0, 0
 
-    def ntt(n):
+    def ntt(n, upper_zero=False):
+        # upper_zero: a zero-padded operand (length <= n/2): the first
+        # stage's n/2 butterflies are single multiplications (a, a w)
         nonlocal bfly, mul
         bfly += (n // 2) * int(math.log2(n))
+        if upper_zero:
+            bfly -= n // 2
+            mul += n // 2
         if n > 4096:
             mul += n  # four-step twiddles
 
@@ -468,10 +475,10 @@ def compose_work(t, degq, modp):
             mul += alen * blen
             return
         n = 1 << max(0, (rl - 1).bit_length())
-        ntt(n)                               # forward transform of A
+        ntt(n, 2 * alen <= n)                # forward transform of A
         if (bkey, n) not in cached:          # transform of q^d, once per length
             cached.add((bkey, n))
-            ntt(n)
+            ntt(n, 2 * blen <= n)
             if n <= 4096:
                 mul += n                     # scaled by 1/n once
         mul += n                             # pointwise

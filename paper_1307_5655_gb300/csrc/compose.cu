@@ -56,11 +56,29 @@ __device__ __forceinline__ uint64_t d_mul(uint64_t a, uint64_t b) { return MODP:
 // with one radix-2 stage when log2 n is odd.
 __device__ __forceinline__ int ilog2_dev(int n) { return 31 - __clz(n); }
 
-__device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw, int stride) {
+// upper_zero: the second half of every input vector is zero (a zero-padded
+// product operand), so the first stage's butterflies reduce to (a, a w).
+__device__ void ntt_dif(uint64_t* a, int n, int count, const uint64_t* tw, int stride, bool upper_zero = false) {
   // all sizes are powers of two: indices by shifts and masks; vector v starts
   // at a + v * stride (stride >= n)
   const int logn = ilog2_dev(n), lper = logn - 2;
   int lhalf = logn - 1;
+  if (upper_zero && lhalf >= 1) {  // first two stages with x[i2] = x[i3] = 0 (half = n / 2: one group)
+    __syncthreads();
+    const int lq = lhalf - 1, q = 1 << lq;
+    for (int e = threadIdx.x; e < (count << lper); e += blockDim.x) {
+      const int v = e >> lper, pos = e & ((1 << lper) - 1);
+      uint64_t* x = a + v * stride;
+      const uint64_t b0 = x[pos], b1 = x[pos + q];
+      const uint64_t b2 = d_mul(b0, __ldg(tw + pos)), b3 = d_mul(b1, __ldg(tw + pos + q));
+      const uint64_t t = __ldg(tw + (pos << 1));
+      x[pos] = d_add(b0, b1);
+      x[pos + q] = d_mul(d_sub(b0, b1), t);
+      x[pos + 2 * q] = d_add(b2, b3);
+      x[pos + 3 * q] = d_mul(d_sub(b2, b3), t);
+    }
+    lhalf -= 2;
+  }
   for (; lhalf >= 1; lhalf -= 2) {  // half = 2^lhalf >= 2: two stages
     __syncthreads();
     const int lq = lhalf - 1, q = 1 << lq;
@@ -160,7 +178,7 @@ __global__ void k_ntt_fwd_small(const uint64_t* src, int64_t src_pitch, int len,
     const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
-  ntt_dif(sh, n, vpb, tw, n);
+  ntt_dif(sh, n, vpb, tw, n, 2 * len <= n);
   for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
     const int v = e >> logn, i = e & (n - 1);
     dst[(p0 + v) * dst_pitch + i] = scale == 1 ? sh[e] : d_mul(sh[e], scale);
@@ -203,7 +221,7 @@ __global__ void k_ntt_product_small(const uint64_t* src, int64_t src_pitch, int 
     const int v = e >> logn, i = e & (n - 1);
     sh[e] = (v < cnt && i < len) ? src[(p0 + v) * src_pitch + i] : 0;
   }
-  ntt_dif(sh, n, vpb, tw, n);
+  ntt_dif(sh, n, vpb, tw, n, 2 * len <= n);
   for (int e = threadIdx.x; e < vpb * n; e += blockDim.x) {
     const int v = e >> logn, i = e & (n - 1);
     if (v < cnt) sh[e] = d_mul(sh[e], fb[(p0 + v) * fb_pitch + i]);
@@ -237,7 +255,7 @@ __global__ void k_ntt_cols(const uint64_t* src, int64_t src_pitch, int len, uint
     sh[c * RS + r] = v;
   }
   if (inverse) ntt_dit(sh, R, TC, twR, RS);
-  else ntt_dif(sh, R, TC, twR, RS);
+  else ntt_dif(sh, R, TC, twR, RS, 2 * (int64_t)len <= (int64_t)R * C);  // rows r >= R/2 hold indices >= len
   for (int e = threadIdx.x; e < R * TC; e += blockDim.x) {
     const int r = e >> lTC, c = e & (TC - 1);
     const int idx = r * C + c0 + c;

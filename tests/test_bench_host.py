@@ -23,9 +23,11 @@ def test_one_small_product():
     # Horner, p = (c2 x + c1) x + c0: the leaf c2 q (65 multiplications), then
     # (c2 q + c1) * q: lengths 65 and 65, result 129, transform length 256:
     # forward, the cached transform of q (scaled by 1/n once: 256
-    # multiplications), pointwise (256), inverse; 3 x 128 x 8 butterflies
+    # multiplications), pointwise (256), inverse; 3 x 128 x 8 butterflies,
+    # less the first stage of the two forward transforms of operands of
+    # length <= 128, which is 128 single multiplications each
     t = _tree(3, "H")
-    assert bench.compose_work(t, 64, True) == (3 * 128 * 8, 65 + 256 + 256)
+    assert bench.compose_work(t, 64, True) == (3 * 128 * 8 - 2 * 128, 65 + 256 + 256 + 2 * 128)
     # FP64: the same product as a direct convolution, 65 x 65 multiply-adds
     assert bench.compose_work(t, 64, False) == (0, 65 * 65)
 
@@ -33,9 +35,11 @@ def test_one_small_product():
 def test_one_four_step_product():
     # deg q = 3000: the product has 3001 x 3001 coefficients, 6001 long, so
     # length 8192 > 4096: three four-step transforms (forward, cached q,
-    # inverse) of 4096 x 13 butterflies and 8192 twiddles each, the pointwise
-    # product (8192), no separate scaling, and the leaf c2 q (3001)
+    # inverse) of 4096 x 13 butterflies and 8192 twiddles each (the two
+    # forward ones on operands of length <= 4096: first stage 4096 single
+    # multiplications), the pointwise product (8192), no separate scaling,
+    # and the leaf c2 q (3001)
     t = _tree(3, "H")
     bfly, mul = bench.compose_work(t, 3000, True)
-    assert bfly == 3 * 4096 * 13
-    assert mul == 3001 + 3 * 8192 + 8192
+    assert bfly == 3 * 4096 * 13 - 2 * 4096
+    assert mul == 3001 + 3 * 8192 + 8192 + 2 * 4096
