@@ -127,16 +127,6 @@ size_t value_bytes_out(fp_dtype dt) {  // bytes of output per point
   return 0;
 }
 
-size_t point_bytes(fp_dtype dt) {  // bytes of input per point and variable
-  switch (dt) {
-    case FP_F64: return 8;
-    case FP_F32C: return 4;
-    case FP_IV64: return 16;
-    case FP_MODP: return 8;
-  }
-  return 0;
-}
-
 bool dtype_ok(const fp_tree* t, fp_dtype dt) {
   if (t->dev.device < 0) return false;  // host-only tree
   if (dt == FP_MODP) return t->coeff_type == FP_MODP;

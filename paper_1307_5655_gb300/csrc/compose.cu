@@ -385,11 +385,6 @@ int grid_for(int64_t total) {
   return (int)(b < 1 ? 1 : (b > 65536 ? 65536 : b));
 }
 
-int ilog2(int64_t n) {
-  int l = 0;
-  while ((int64_t)1 << l < n) ++l;
-  return l;
-}
 
 // ------------------------------------------------------------ host plan
 struct Buf {
