@@ -30,6 +30,26 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def _enum(name_prefix):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(%s[A-Z0-9_]+)\s*=\s*(-?\d+)" % name_prefix, src)}
+
+
+def test_binding_constants_match_header():
+    """The binding's names and codes are the header's: rates in enum order,
+    value types, schemes and status codes."""
+    rates = _enum("FP_RATE_")
+    count = rates.pop("FP_RATE_COUNT")
+    assert count == len(fpl.RATE_NAMES) == len(rates)
+    assert sorted(rates.values()) == list(range(count))
+    by_index = [k[len("FP_RATE_"):].lower() for k, _ in sorted(rates.items(), key=lambda kv: kv[1])]
+    assert by_index == list(fpl.RATE_NAMES)
+    dtypes = _enum("FP_")
+    for name, code in fpl.DTYPES.items():
+        assert dtypes["FP_" + name.upper()] == code, name
+    assert dtypes["FP_OK"] == 0 and dtypes["FP_E_TIMEOUT"] == -8
+
+
 def _compare(exps, coeffs, scheme, ftab=None):
     t = fpl.fp_compile_host(exps, coeffs, scheme, ftab)
     got = t.export()
