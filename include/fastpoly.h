@@ -273,14 +273,15 @@ void fp_batch_free(fp_batch* batch);
  * thread and complete asynchronously.  A worker thread admits pending
  * requests oldest first while their device footprint (points + results) fits
  * in hbm_budget_bytes (a request larger than the whole budget runs alone),
- * groups requests of one value type into one batched launch on one of
- * `streams` streams (copies in, fp_eval_batch, copies out), and retires
+ * groups requests of one value type into one batched launch in one of
+ * `streams` slots (copies in, fp_eval_batch, copies out), and retires
  * batches as they finish, so requests that arrive while batches run are
- * admitted as soon as a stream and memory free up.  A batch lasts as long as
+ * admitted as soon as a slot and memory free up.  A batch lasts as long as
  * its largest request: small requests (estimated work below about 1.7 ms of
- * FP64 evaluation) are batched apart from large ones and launched on
- * streams of the highest priority, and with two or more streams the first
- * takes small requests only.  Results equal fp_eval's.
+ * FP64 evaluation) are batched apart from large ones and launched on a
+ * stream of the highest priority (each slot has one beside its
+ * default-priority stream), and with two or more slots the first takes
+ * small requests only.  Results equal fp_eval's.
  * Host buffers should be pinned (page-locked) for the copies to overlap; they
  * must stay valid until the request completes.  Trees must outlive the
  * requests that use them.
@@ -289,7 +290,7 @@ typedef struct fp_server fp_server;
 typedef struct {
   size_t hbm_budget_bytes;  /* device bytes for the points and results in flight (> 0) */
   int max_batch_jobs;       /* requests per batched launch (<= 0: 1024) */
-  int streams;              /* batches in flight at once (<= 0: 4) */
+  int streams;              /* slots: batches in flight at once (<= 0: 4) */
 } fp_server_cfg;
 typedef struct {
   int64_t ticket;     /* as returned by fp_server_submit */

@@ -7,14 +7,14 @@
 //   - admits pending requests, oldest first, while their device footprint
 //     (points + results) fits in the HBM budget, grouping requests of one
 //     value type and one size class into one batched launch (fp_eval_batch)
-//     on a free stream: host->device copies, the launch, device->host copies,
+//     in a free slot: host->device copies, the launch, device->host copies,
 //     release of the buffers, then an event -- all stream-ordered.  A batch
 //     lasts as long as its largest request, so small requests (estimated
 //     work below kSmallWork) are never batched with large ones and run on
 //     high-priority streams, and with two or more slots the first is kept
 //     for small requests (an express lane);
 //   - sleeps on a condition variable (bounded) when there is nothing to do.
-// Requests arriving while batches run are admitted as soon as a stream and
+// Requests arriving while batches run are admitted as soon as a slot and
 // memory are free, so their work overlaps with the batches in flight.
 #include <atomic>
 #include <chrono>
