@@ -241,7 +241,10 @@ int ops_layout(fp_tree* t) {
   t->ops_root_lh = root_h;
   t->ops_root_pid = t->root_pid >= 0 ? pos[t->root_pid] : -1;
   t->ops_pos_x1 = t->pid_x1 >= 0 && live[t->pid_x1] ? pos[t->pid_x1] : -1;
-  for (int d = 0; d <= kMaxBlock; ++d) t->ops_pid_pow[d] = t->pid_pow[d] >= 0 ? pos[t->pid_pow[d]] : -1;
+  // template powers exist only for trees with blocks (E, B): without, their
+  // positions may have been reused by temporaries, so none is reported
+  for (int d = 0; d <= kMaxBlock; ++d)
+    t->ops_pid_pow[d] = t->block_scheme && t->pid_pow[d] >= 0 ? pos[t->pid_pow[d]] : -1;
   return FP_OK;
 }
 

@@ -213,3 +213,50 @@ def test_multivariate_with_virtual_roots_and_gaps():
     c2 = W.residues(len(e2), 14)
     for scheme in ("E", "B"):
         _check(e2, c2, scheme, npts=2, seed=6)
+
+
+def _random_terms(r, nvars):
+    """Exponent sets mixing dense runs with holes in every variable: each
+    group (fixed outer exponents) keeps a random prefix and random gaps of
+    the innermost variable's run, so blocks, partial blocks, chains, single
+    nodes and virtual group roots all occur."""
+    deg = int(r.integers(3, 40 if nvars == 1 else 12))
+    full = W.total_degree_exps(nvars, deg) if nvars > 1 else np.arange(deg + 1)[::-1].reshape(-1, 1)
+    keep = r.random(len(full)) < r.uniform(0.3, 1.0)
+    e = full[keep]
+    if len(e) == 0:
+        e = full[:1]
+    return np.ascontiguousarray(e.astype(np.int32))
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_random_schedules_replay_for_both_coefficient_types(seed):
+    """Fuzz: random sparse multivariate term sets under random schemes
+    (including random split tables), for the mod-p trees (blocks up to 64
+    nodes) and the floating-point trees (up to 16), replayed mod p."""
+    r = W.rng(9000 + seed)
+    nvars = int(r.integers(1, 4))
+    e = _random_terms(r, nvars)
+    k = len(e)
+    scheme = ["H", "E", "B", "D", "CUSTOM"][int(r.integers(0, 5))]
+    ftab = None
+    if scheme == "CUSTOM":
+        nmax = max(k, int(e.max()) + 1)
+        ftab = np.zeros(nmax + 1, dtype=np.int32)
+        for n in range(1, nmax + 1):
+            ftab[n] = r.integers(1, n + 1)
+    res = W.residues(k, 9100 + seed)
+    x = W.points_modp(nvars, 1, 9200 + seed)
+    ref = int(O.eval_modp(e, res, x)[0])
+    xs = [int(v) for v in x[:, 0]]
+    for modp in (True, False):
+        coeffs = res if modp else W.uniform_f64(k, 9300 + seed)
+        t = fpl.fp_compile_host(e, coeffs, scheme, ftab, modp=modp)
+        if not modp:  # same tree shape, so the residues go where the floats went
+            assert t.info()["nnodes"] >= k
+        assert _replay(t, res, xs) == ref, (seed, scheme, nvars, k, modp)
+        if not modp:
+            sc = t.schedule()
+            blk = (sc["op_words"][:, 0] & 3) >= 2
+            assert (sc["op_words"][:, 1][blk] + 1 <= 16).all()
+        t.free()
