@@ -152,3 +152,27 @@ def test_eval_on_host_only_tree_is_rejected():
     t = fpl.fp_compile_host(np.array([[1], [0]]), np.array([1.0, 2.0]), "E")
     rc = fpl._lib.fp_eval(t.handle, 0, None, 0, None, None)
     assert rc == -4
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_random_sparse_trees_match_oracle(seed):
+    """Fuzz: random sparse term sets in 1-4 variables, given in random order,
+    under random schemes (including random split tables): the host compiler's
+    tree equals the oracle's index for index."""
+    r = W.rng(29000 + seed)
+    nvars = int(r.integers(1, 5))
+    deg = int(r.integers(1, 60 if nvars == 1 else 10))
+    full = W.total_degree_exps(nvars, deg) if nvars > 1 else np.arange(deg + 1)[::-1].reshape(-1, 1)
+    keep = r.random(len(full)) < r.uniform(0.1, 1.0)
+    e = np.ascontiguousarray(full[keep].astype(np.int32))
+    if len(e) == 0:
+        e = np.ascontiguousarray(full[:1].astype(np.int32))
+    e, c = W.shuffled(e, W.uniform_f64(len(e), seed), seed + 1)
+    scheme = ["H", "E", "B", "D", "CUSTOM"][int(r.integers(0, 5))]
+    ftab = None
+    if scheme == "CUSTOM":
+        nmax = max(len(e), int(e.max()) + 1)
+        ftab = np.zeros(nmax + 1, dtype=np.int32)
+        for n in range(1, nmax + 1):
+            ftab[n] = r.integers(1, n + 1)
+    _compare(e, c, scheme, ftab)
