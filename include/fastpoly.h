@@ -27,7 +27,7 @@ extern "C" {
 /* Status codes. */
 typedef enum {
   FP_OK = 0,
-  FP_E_BAD_VALUE = -1,   /* null pointer, negative size or exponent, coefficient not < p */
+  FP_E_BAD_VALUE = -1,   /* null pointer, negative size or exponent, NaN coefficient, coefficient not < p */
   FP_E_DUP_TERM = -2,    /* two terms with the same exponent vector */
   FP_E_BAD_SCHEME = -3,  /* unknown scheme, or a custom f with f(n) outside (0, n] */
   FP_E_DTYPE = -4,       /* value type not available for this tree */

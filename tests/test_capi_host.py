@@ -139,6 +139,31 @@ def test_compile_errors(bad, code):
     assert ei.value.code == code
 
 
+def test_more_compile_errors():
+    """The documented error codes for bad schemes, split tables, value types
+    and pointers (host-only compile: no GPU)."""
+    e3, c3 = np.array([[2], [1], [0]]), np.array([1.0, 2.0, 3.0])
+    cases = [
+        ((e3, c3, 9), -3),                                    # unknown scheme
+        ((e3, c3, "CUSTOM", np.array([0, 2, 3])), -3),        # f(1) = 2 > 1
+        ((e3, c3, "CUSTOM", np.array([0, 1])), -3),           # table shorter than n
+        ((e3, c3, "CUSTOM", None), -3),                       # no table
+        ((np.zeros((1, 0), dtype=np.int32), np.array([1.0]), "E"), -1),  # no variable
+        ((e3, np.array([np.nan, 1.0, 2.0]), "E"), -1),        # NaN coefficient
+    ]
+    for args, code in cases:
+        with pytest.raises(fpl.FastPolyError) as ei:
+            fpl.fp_compile_host(*args)
+        assert ei.value.code == code, args
+    h = ctypes.c_void_p()
+    lib = fpl._lib
+    assert lib.fp_compile_host(1, 2, None, None, 0, 2, None, 0, ctypes.byref(h)) == -1   # NULL arrays
+    assert lib.fp_compile_host(1, 0, None, None, 0, 2, None, 0, None) == -1              # NULL out
+    assert lib.fp_compile_host(1, -1, None, None, 0, 2, None, 0, ctypes.byref(h)) == -1  # negative count
+    assert lib.fp_compile_host(1, 0, None, None, 2, 2, None, 0, ctypes.byref(h)) == -4   # IV64 coefficients
+    assert lib.fp_compile_host(1, 0, None, None, 7, 2, None, 0, ctypes.byref(h)) == -4   # no such type
+
+
 def test_term_count_limit():
     """One term above FP_MAX_TERMS is refused before any work."""
     n = fpl.MAX_TERMS + 1
