@@ -201,3 +201,19 @@ def test_random_sparse_trees_match_oracle(seed):
         for n in range(1, nmax + 1):
             ftab[n] = r.integers(1, n + 1)
     _compare(e, c, scheme, ftab)
+
+
+def test_argument_checks_before_any_cuda_call():
+    """Entry points refuse bad arguments with FP_E_BAD_VALUE before touching
+    the device, and every status has its own message."""
+    lib = fpl._lib
+    h = ctypes.c_void_p()
+    assert lib.fp_server_create(None, ctypes.byref(h)) == -1
+    cfg = fpl._ServerCfg(0, 0, 0)  # no HBM budget
+    assert lib.fp_server_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    rates = np.zeros(2)
+    assert lib.fp_measure_rates(None, 2, None) == -1
+    assert lib.fp_measure_rates(rates.ctypes.data_as(ctypes.c_void_p), -1, None) == -1
+    msgs = [lib.fp_strerror(c) for c in range(0, -9, -1)]
+    assert msgs[0] == b"ok" and len(set(msgs)) == len(msgs) and all(msgs)
+    assert lib.fp_strerror(-99) == b"unknown status"
