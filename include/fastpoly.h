@@ -340,6 +340,17 @@ void fp_server_destroy(fp_server* s);
 int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
                int64_t npairs, void* out, void* stream);
 
+/* fp_compose_workspace -- the device work space, in bytes, that fp_compose
+ * and fp_compose_noalloc use for these arguments (per_pair_coeffs: non-zero
+ * when pcoeffs will be given, zero for the tree's own coefficients), counted
+ * by running the composition driver without launching, copying or allocating
+ * anything (each buffer rounded up to 256 bytes).  Host only; no CUDA call.
+ * The paper has no counterpart: this is a property of the library.
+ * Errors: those of fp_compose's argument checks (FP_E_BAD_VALUE, FP_E_DTYPE,
+ * FP_E_TOO_LARGE). */
+int fp_compose_workspace(const fp_tree* p, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
+                         size_t* bytes);
+
 /*
  * fp_compose_noalloc -- fp_compose for callers that must not allocate device
  * memory: code running under a memory manager that owns the whole device
@@ -356,9 +367,9 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
  *   - All calls share the region and it keeps the last call's contents, so
  *     calls that overlap on the GPU (other streams, other threads) race:
  *     serialise them.
- *   - A problem whose work space exceeds the region returns FP_E_TOO_LARGE
- *     before any work is enqueued (roughly: npairs x deg(p) x degq x 8 bytes x
- *     (lazy height + 6) must fit).
+ *   - A problem whose work space (fp_compose_workspace) exceeds the region
+ *     returns FP_E_TOO_LARGE before any work is enqueued (roughly: npairs x
+ *     deg(p) x degq x 8 bytes x (lazy height + 6) must fit).
  * The call synchronises `stream` while it uploads its small tables.
  */
 #define FP_NOALLOC_SCRATCH_BYTES (64ull << 20)

@@ -42,6 +42,7 @@ for _name, _args in {
     "fp_eval_plain_f64": [_P, _I64, _P, _I64, _P, _P],
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
     "fp_compose_noalloc": [_P, _I, _P, _P, _I, _I64, _P, _P],
+    "fp_compose_workspace": [_P, _I, _I, _I, _I64, ctypes.POINTER(ctypes.c_size_t)],
 }.items():
     getattr(_lib, _name).restype = _I
     getattr(_lib, _name).argtypes = _args
@@ -79,10 +80,11 @@ def _stream_handle(stream):
 class Tree:
     """A compiled evaluation tree (owned by the library until freed)."""
 
-    def __init__(self, handle, nvars, coeff_type):
+    def __init__(self, handle, nvars, coeff_type, nterms=None):
         self._h = handle
         self.nvars = nvars
         self.coeff_type = coeff_type
+        self.nterms = nterms  # terms given to the compiler (rows of per-pair coefficients)
 
     @property
     def handle(self):
@@ -155,7 +157,7 @@ def _compile(fn, exps, coeffs, scheme, ftab, modp):
             SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
             None if ft is None else _ptr(ft), 0 if ft is None else len(ft), ctypes.byref(h))
     _check(rc, fn.__name__)
-    return Tree(h.value, nvars, "modp" if modp else "f64")
+    return Tree(h.value, nvars, "modp" if modp else "f64", nterms)
 
 
 def fp_compile(exps, coeffs, scheme="E", ftab=None, modp=False):
@@ -352,21 +354,54 @@ def fp_eval_plain_f64(coeffs_by_degree, points, out=None, stream=None):
     return out
 
 
+def _compose_args(tree, dtype, q, pcoeffs, out, degp):
+    """Check the tensors of a composition before they reach the C ABI (a host
+    pointer or a wrongly shaped buffer there would be a device fault, not an
+    error code) and allocate `out` when it is None."""
+    import torch
+    if dtype not in ("f64", "modp"):
+        raise ValueError("composition value types are 'f64' and 'modp'")
+    want = _torch_dtype(dtype)
+
+    def dev_tensor(name, a):
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if a.dim() != 2 or not a.is_contiguous():
+            raise ValueError("%s must be a contiguous 2-D tensor" % name)
+        if a.dtype != want:
+            raise ValueError("%s must have dtype %s for '%s'" % (name, want, dtype))
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError("%s must be on the current CUDA device (the tree's)" % name)
+
+    dev_tensor("q", q)
+    npairs, nq = q.shape
+    if nq < 1:
+        raise ValueError("q needs at least one coefficient")
+    if degp is None:
+        degp = int(tree.export()["node_e"][0, 0]) if tree.info()["nnodes"] else 0
+    if pcoeffs is not None:
+        dev_tensor("pcoeffs", pcoeffs)
+        if tree.nterms is not None and tuple(pcoeffs.shape) != (npairs, tree.nterms):
+            raise ValueError("pcoeffs must have shape [npairs, nterms] = [%d, %d]" % (npairs, tree.nterms))
+        if pcoeffs.shape[0] != npairs:
+            raise ValueError("pcoeffs must have one row per pair")
+    shape = (npairs, degp * (nq - 1) + 1)
+    if out is None:
+        out = torch.empty(shape, dtype=want, device=q.device)
+    dev_tensor("out", out)
+    if tuple(out.shape) != shape:
+        raise ValueError("out must have shape [npairs, deg(p) * deg(q) + 1] = [%d, %d]" % shape)
+    return npairs, nq - 1, out
+
+
 def fp_compose(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
     """Batched composition p_j(q_j(y)): q is a CUDA tensor [npairs, degq + 1]
     (float64, or int64 holding residues for 'modp'); pcoeffs an optional CUDA
     tensor [npairs, nterms] of per-pair coefficients in the compiled term
     order.  Returns out [npairs, deg(p) * degq + 1]."""
-    import torch
-    if not q.is_cuda or not q.is_contiguous():
-        raise ValueError("q must be a contiguous CUDA tensor")
-    npairs, nq = q.shape
-    if degp is None:
-        degp = int(tree.export()["node_e"][0, 0]) if tree.info()["nnodes"] else 0
-    if out is None:
-        out = torch.empty((npairs, degp * (nq - 1) + 1), dtype=_torch_dtype(dtype), device=q.device)
+    npairs, degq, out = _compose_args(tree, dtype, q, pcoeffs, out, degp)
     pc = None if pcoeffs is None else _ptr(pcoeffs)
-    _check(_lib.fp_compose(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
+    _check(_lib.fp_compose(tree.handle, DTYPES[dtype], pc, _ptr(q), degq, npairs, _ptr(out),
                            _stream_handle(stream)), "fp_compose")
     return out
 
@@ -374,19 +409,23 @@ def fp_compose(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
+def fp_compose_workspace(tree, dtype, degq, npairs, per_pair_coeffs=True):
+    """Device bytes of work space that fp_compose / fp_compose_noalloc use for
+    these sizes (host only: a dry run of the composition driver)."""
+    b = ctypes.c_size_t()
+    _check(_lib.fp_compose_workspace(tree.handle, DTYPES[dtype], 1 if per_pair_coeffs else 0, degq, npairs,
+                                     ctypes.byref(b)), "fp_compose_workspace")
+    return b.value
+
+
 def fp_compose_noalloc(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
     """fp_compose without any device allocation by the library: the work space
     is a fixed region (NOALLOC_SCRATCH_BYTES per device) shared by all calls,
     so calls must not overlap on the GPU.  The output buffer `out` should be
     provided by the caller (allocating it here would defeat the purpose)."""
-    import torch
-    npairs, nq = q.shape
-    if degp is None:
-        degp = int(tree.export()["node_e"][0, 0]) if tree.info()["nnodes"] else 0
-    if out is None:
-        out = torch.empty((npairs, degp * (nq - 1) + 1), dtype=_torch_dtype(dtype), device=q.device)
+    npairs, degq, out = _compose_args(tree, dtype, q, pcoeffs, out, degp)
     pc = None if pcoeffs is None else _ptr(pcoeffs)
-    _check(_lib.fp_compose_noalloc(tree.handle, DTYPES[dtype], pc, _ptr(q), nq - 1, npairs, _ptr(out),
+    _check(_lib.fp_compose_noalloc(tree.handle, DTYPES[dtype], pc, _ptr(q), degq, npairs, _ptr(out),
                                    _stream_handle(stream)), "fp_compose_noalloc")
     return out
 

@@ -294,9 +294,11 @@ int eval_device(const fp_tree* t, fp_dtype dt, const void* points, int64_t npts,
 }
 
 int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
-                   void* out, cudaStream_t st, unsigned char* arena, size_t arena_cap);
+                   void* out, cudaStream_t st, unsigned char* arena, size_t arena_cap, size_t* dry_bytes);
 int compose_noalloc_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
                            int64_t npairs, void* out, cudaStream_t st);
+int compose_workspace_device(const fp_tree* t, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
+                             size_t* bytes);
 
 }  // namespace fp
 
@@ -706,7 +708,12 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
                void* out, void* stream) {
   int dev = -1;
   if (p && (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev.device)) { cudaGetLastError(); return FP_E_BAD_VALUE; }
-  return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream, nullptr, 0);
+  return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+int fp_compose_workspace(const fp_tree* p, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
+                         size_t* bytes) {
+  return compose_workspace_device(p, dtype, per_pair_coeffs, degq, npairs, bytes);
 }
 
 int fp_compose_noalloc(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,

@@ -13,6 +13,8 @@
 //   FP64: by direct convolution (componentwise error bound).
 // Powers q^d follow the tree's power program (squarings and products by q).
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -408,6 +410,11 @@ struct Composer {
   // of being allocated (fp_compose_noalloc)
   unsigned char* arena = nullptr;
   size_t arena_cap = 0, arena_used = 0;
+  // dry run: every buffer is only counted (arena_used, 256-byte granules) and
+  // nothing is launched, copied or computed -- the one account of the work
+  // space, since the same driver code decides every buffer
+  bool dry = false;
+  bool live() const { return !dry && status == FP_OK; }
   int sms = 0;  // multiprocessors of the current device
 
   // vectors of length n <= 4096 per block of an in-shared-memory transform:
@@ -434,6 +441,10 @@ struct Composer {
   void* alloc(size_t bytes) {
     void* p = nullptr;
     if (status != FP_OK) return nullptr;
+    if (dry) {  // a distinct, never dereferenced stand-in address per buffer
+      arena_used += (bytes + 255) & ~(size_t)255;
+      return (void*)(uintptr_t)arena_used;
+    }
     if (arena) {
       const size_t sz = (bytes + 255) & ~(size_t)255;
       if (arena_used + sz > arena_cap) {
@@ -457,12 +468,13 @@ struct Composer {
     owned.clear();
   }
   void check() {
-    if (status == FP_OK && cudaGetLastError() != cudaSuccess) status = FP_E_CUDA;
+    if (!dry && status == FP_OK && cudaGetLastError() != cudaSuccess) status = FP_E_CUDA;
   }
 
   std::pair<uint64_t*, uint64_t*> twiddles(int n) {
     auto it = tw.find(n);
     if (it != tw.end()) return it->second;
+    if (dry) return tw[n] = {(uint64_t*)alloc(n * 8), (uint64_t*)alloc(n * 8)};
     std::vector<uint64_t> f(n), b(n);
     const uint64_t w = h_pow(7, (kP - 1) / (uint64_t)n);  // 7 generates (Z/pZ)^*
     const uint64_t wi = h_pow(w, kP - 2);
@@ -491,6 +503,7 @@ struct Composer {
   std::pair<uint64_t*, uint64_t*> four_step_twiddles(int n) {
     auto it = tw4.find(n);
     if (it != tw4.end()) return it->second;
+    if (dry) return tw4[n] = {(uint64_t*)alloc(n * 8), (uint64_t*)alloc(n * 8)};
     int R, C;
     split(n, R, C);
     int logR = 0;
@@ -534,6 +547,7 @@ struct Composer {
     if (status != FP_OK) return;
     if (n <= kNttSmemMax) {
       auto w = twiddles(n);
+      if (!live()) return;
       const int vpb = small_vpb(n);
       k_ntt_fwd_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
           (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, n, vpb, npairs, w.first, scale);
@@ -544,6 +558,7 @@ struct Composer {
       auto wR = twiddles(R);
       auto wC = twiddles(C);
       auto w4 = four_step_twiddles(n);
+      if (!live()) return;
       k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
           (const uint64_t*)src.ptr, src.pitch, len, (uint64_t*)dst.ptr, dst.pitch, R, C, TC, wR.first, w4.first, 0, 0,
           0, nullptr, 0);
@@ -566,6 +581,7 @@ struct Composer {
     auto wR = twiddles(R);
     auto wC = twiddles(C);
     auto w4 = four_step_twiddles(n);
+    if (!live()) return;
     k_ntt_cols<<<(unsigned)(npairs * (C / TC)), 256, (size_t)(R + 1) * TC * 8, st>>>(
         (const uint64_t*)a.ptr, a.pitch, len, (uint64_t*)work.ptr, work.pitch, R, C, TC, wR.first, w4.first, 0, 0, 0,
         nullptr, 0);
@@ -583,8 +599,9 @@ struct Composer {
   void mul_inv(const Buf& fa, const Buf& fbuf, int n, const Buf& out, int outlen, int mode, const uint64_t* init,
                int64_t init_pitch) {
     if (status != FP_OK) return;
-    const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
     auto w = twiddles(n);
+    if (!live()) return;
+    const uint64_t ninv = h_pow((uint64_t)n, kP - 2);
     const int vpb = small_vpb(n);
     k_ntt_mul_inv_small<<<(unsigned)((npairs + vpb - 1) / vpb), small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
         (const uint64_t*)fa.ptr, fa.pitch, (const uint64_t*)fbuf.ptr, fbuf.pitch, n, vpb, npairs, w.second, ninv,
@@ -602,13 +619,20 @@ int64_t next_pow2(int64_t x) {
 }  // namespace
 
 // Composition entry (declared in capi.cu).
+// With dry_bytes non-NULL nothing is launched, copied or allocated: the call
+// only writes the bytes of work space the same arguments would use (buffers
+// rounded up to 256 bytes, as the allocation-free entry carves them).
 int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq, int64_t npairs,
-                   void* out, cudaStream_t st, unsigned char* arena = nullptr, size_t arena_cap = 0) {
+                   void* out, cudaStream_t st, unsigned char* arena = nullptr, size_t arena_cap = 0,
+                   size_t* dry_bytes = nullptr) {
   if (!t || !q || !out || degq < 0 || npairs < 0) return FP_E_BAD_VALUE;
   if (t->nvars != 1) return FP_E_BAD_VALUE;
   if (dtype == FP_MODP ? t->coeff_type != FP_MODP : (dtype != FP_F64 || t->coeff_type != FP_F64)) return FP_E_DTYPE;
-  if (t->dev.device < 0) return FP_E_DTYPE;
-  if (npairs == 0) return FP_OK;
+  if (t->dev.device < 0 && !dry_bytes) return FP_E_DTYPE;  // a dry run needs no device copy
+  if (npairs == 0) {
+    if (dry_bytes) *dry_bytes = 0;
+    return FP_OK;
+  }
   const bool modp = dtype == FP_MODP;
   const int64_t N = t->nnodes;
   const int64_t dmax = N > 0 ? t->node_e[0] : 0;  // degree of p (node 0 is the highest term)
@@ -618,8 +642,11 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   Composer cm{t, dtype, degq, npairs, st};
   cm.arena = arena;
   cm.arena_cap = arena_cap;
+  cm.dry = dry_bytes != nullptr;
+  if (cm.dry) *dry_bytes = 0;
   Buf outb{out, outlen};
   if (N == 0) {  // zero polynomial
+    if (cm.dry) return FP_OK;
     k_fill_zero<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, 0, (int)outlen, npairs);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
   }
@@ -639,18 +666,20 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       d_pc = cm.alloc(own.size() * 8);
     }
     if (cm.status != FP_OK) { cm.release(); return cm.status; }
-    cudaMemcpyAsync(d_map, t->term_of_node.data(), N * 8, cudaMemcpyHostToDevice, st);
-    if (!pcoeffs) cudaMemcpyAsync(d_pc, own.data(), own.size() * 8, cudaMemcpyHostToDevice, st);
-    // term_of_node indexes the caller's input order (rows of nterms_in)
-    const int64_t row = pcoeffs ? t->nterms_in : 0;
-    if (modp)
-      k_gather_coeffs<uint64_t><<<grid_for(npairs * N), 256, 0, st>>>(
-          (const uint64_t*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (uint64_t*)cn.ptr, npairs, 1);
-    else
-      k_gather_coeffs<double><<<grid_for(npairs * N), 256, 0, st>>>(
-          (const double*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (double*)cn.ptr, npairs, 0);
-    cm.check();
-    cudaStreamSynchronize(st);  // the host vectors above must outlive their copies
+    if (cm.live()) {
+      cudaMemcpyAsync(d_map, t->term_of_node.data(), N * 8, cudaMemcpyHostToDevice, st);
+      if (!pcoeffs) cudaMemcpyAsync(d_pc, own.data(), own.size() * 8, cudaMemcpyHostToDevice, st);
+      // term_of_node indexes the caller's input order (rows of nterms_in)
+      const int64_t row = pcoeffs ? t->nterms_in : 0;
+      if (modp)
+        k_gather_coeffs<uint64_t><<<grid_for(npairs * N), 256, 0, st>>>(
+            (const uint64_t*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (uint64_t*)cn.ptr, npairs, 1);
+      else
+        k_gather_coeffs<double><<<grid_for(npairs * N), 256, 0, st>>>(
+            (const double*)(pcoeffs ? pcoeffs : d_pc), row, d_map, N, (double*)cn.ptr, npairs, 0);
+      cm.check();
+      cudaStreamSynchronize(st);  // the host vectors above must outlive their copies
+    }
   }
   // ---- degrees of node values: deg(N) = degq * (max exponent in subtree - e(N))
   std::vector<int64_t> maxe(N);
@@ -692,8 +721,8 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       const int n = (int)next_pow2(rl);
       if (bk >= 0 && n <= kNttSmemMax) {  // one fused launch
         const Buf fb = qhat_of(bk, n);
-        if (cm.status != FP_OK) return;
         auto w = cm.twiddles(n);
+        if (!cm.live()) return;
         const int vpb = cm.small_vpb(n);
         k_ntt_product_small<<<(unsigned)((npairs + vpb - 1) / vpb), cm.small_threads(vpb, n), (size_t)vpb * n * 8, st>>>(
             (const uint64_t*)A.ptr, A.pitch, (int)alen, (const uint64_t*)fb.ptr, fb.pitch, n, vpb, npairs, w.first,
@@ -716,6 +745,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       if (cm.status != FP_OK) return;
       cm.mul_inv(ta, fb, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
     } else {
+      if (!cm.live()) return;
       // the source may be the destination slot: convolve from a copy
       k_copy_rows<double><<<grid_for(npairs * alen), 256, 0, st>>>((const double*)A.ptr, A.pitch, (double*)ta.ptr,
                                                                     ta.pitch, (int)alen, npairs, 0);
@@ -731,6 +761,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
     const uint32_t w = t->pow_prog[k];
     const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
     if (op == kPowLoad) {
+      if (cm.dry) continue;
       if (modp) k_copy_rows<uint64_t><<<grid_for(npairs * (degq + 1)), 256, 0, st>>>(
           (const uint64_t*)q, degq + 1, (uint64_t*)qp[k].ptr, qp[k].pitch, degq + 1, npairs, 1);
       else k_copy_rows<double><<<grid_for(npairs * (degq + 1)), 256, 0, st>>>(
@@ -757,6 +788,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
     const int mode = first ? 2 : 1;
     const void* init = (const char*)cn.ptr + P * esz;
     if (!has_child[i]) {  // leaf: c_i * q^d
+      if (cm.dry) continue;
       const int len = (int)qd.pitch;
       if (modp)
         k_leaf<uint64_t><<<grid_for(npairs * len), 256, 0, st>>>(
@@ -776,7 +808,8 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
     const int64_t R = N - 1;
     const int64_t d0 = t->pd[R];
     if (!has_child[R]) {  // a single term c x^d: c * q^d
-      if (d0 == 0) {
+      if (cm.dry) {
+      } else if (d0 == 0) {
         k_fill_zero<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((uint64_t*)out, outlen, 0, (int)outlen, npairs);
         if (modp) k_copy_rows<uint64_t><<<grid_for(npairs), 256, 0, st>>>((const uint64_t*)cn.ptr + R, N, (uint64_t*)out, outlen, 1, npairs, 0);
         else k_copy_rows<double><<<grid_for(npairs), 256, 0, st>>>((const double*)cn.ptr + R, N, (double*)out, outlen, 1, npairs, 0);
@@ -794,7 +827,8 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       cm.check();
     } else if (d0 == 0) {
       const Buf& src = acc[t->lh[R]];
-      if (modp) k_copy_rows<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((const uint64_t*)src.ptr, src.pitch, (uint64_t*)out, outlen, (int)outlen, npairs, 0);
+      if (cm.dry) {
+      } else if (modp) k_copy_rows<uint64_t><<<grid_for(npairs * outlen), 256, 0, st>>>((const uint64_t*)src.ptr, src.pitch, (uint64_t*)out, outlen, (int)outlen, npairs, 0);
       else k_copy_rows<double><<<grid_for(npairs * outlen), 256, 0, st>>>((const double*)src.ptr, src.pitch, (double*)out, outlen, (int)outlen, npairs, 0);
       cm.check();
     } else {
@@ -805,6 +839,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   }
   const int rc = cm.status;
   cm.release();
+  if (cm.dry) *dry_bytes = cm.arena_used;
   return rc;
 }
 
@@ -817,68 +852,9 @@ static __device__ __align__(256) unsigned char g_compose_scratch[FP_NOALLOC_SCRA
 
 namespace {
 
-// Bytes fp_compose's work space needs, buffer by buffer in the order the
-// driver carves them (each rounded up to 256 bytes).
-size_t compose_workspace_bytes(const fp_tree* t, bool modp, bool shared_coeffs, int32_t degq, int64_t npairs) {
-  auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const int64_t N = t->nnodes;
-  if (N == 0) return 0;
-  size_t total = r256(npairs * N * 8) + r256(N * 8);
-  if (shared_coeffs) total += r256(t->nterms_in * 8);
-  std::vector<int64_t> maxe(N);
-  for (int64_t i = 0; i < N; ++i) maxe[i] = t->node_e[i];
-  for (int64_t i = 0; i + 1 < N; ++i) maxe[t->parent[i]] = std::max(maxe[t->parent[i]], maxe[i]);
-  auto degval = [&](int64_t i) { return (maxe[i] - t->node_e[i]) * (int64_t)degq; };
-  std::vector<int64_t> cap(t->max_lh + 1, 1);
-  for (int64_t i = 0; i < N; ++i) cap[t->lh[i]] = std::max(cap[t->lh[i]], degval(i) + 1);
-  for (int64_t c : cap) total += r256(npairs * c * 8);
-  const int npow = (int)t->pow_prog.size();
-  int64_t maxprod = 1;
-  for (int k = 0; k < npow; ++k) {
-    total += r256(npairs * (t->pow_deg[k] * degq + 1) * 8);
-    maxprod = std::max(maxprod, t->pow_deg[k] * degq + 1);
-  }
-  for (int64_t i = 0; i + 1 < N; ++i) maxprod = std::max(maxprod, degval(i) + t->pd[i] * degq + 1);
-  const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
-  total += 2 * r256(npairs * Lmax * 8);
-  if (!modp) return total;
-  // transforms: twiddle tables per length and cached transforms of q^d
-  std::map<std::pair<int32_t, int64_t>, int> pid;
-  for (int k = 0; k < npow; ++k) pid[{t->pow_var[k], t->pow_deg[k]}] = k;
-  std::map<int64_t, int> tw;
-  std::map<std::pair<int, int64_t>, int> qh;
-  auto use = [&](int64_t rl, int bk) {
-    const int64_t n = next_pow2(rl);
-    if (n <= kNttSmemMax) tw[n] = 1;
-    else {  // tables of R, C and the four-step table of n (all 2 x length entries)
-      int lg = 0;
-      while ((1ll << lg) < n) ++lg;
-      const int64_t C = 1ll << ((lg + 1) / 2);
-      tw[n / C] = 1;
-      tw[C] = 1;
-      tw[n] = 1;
-    }
-    if (bk >= 0) qh[{bk, n}] = 1;
-  };
-  for (int k = 0; k < npow; ++k) {
-    const uint32_t w = t->pow_prog[k];
-    const uint32_t op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
-    const int64_t l1 = t->pow_deg[a1] * degq + 1;
-    if (op == kPowSq) use(2 * l1 - 1, (int)a1);
-    else if (op == kPowMulX) use(l1 + t->pow_deg[a2] * degq, (int)a2);
-  }
-  std::vector<uint8_t> has_child(N, 0);
-  for (int64_t i = 0; i + 1 < N; ++i) has_child[t->parent[i]] = 1;
-  for (int64_t i = 0; i + 1 < N; ++i)
-    if (has_child[i]) use(degval(i) + 1 + t->pd[i] * degq, pid.at({0, t->pd[i]}));
-  const int64_t R = N - 1;
-  if (has_child[R] && t->pd[R] > 0) use(degval(R) + 1 + t->pd[R] * degq, pid.at({0, t->pd[R]}));
-  for (auto& kv : tw) total += 2 * r256(kv.first * 8);
-  for (auto& kv : qh) total += r256(npairs * kv.first.second * 8);
-  return total;
-}
-
-unsigned char* g_scratch_ptr[256];  // device address of g_compose_scratch, per device
+// device address of g_compose_scratch, per device, looked up once under the lock
+std::atomic<unsigned char*> g_scratch_ptr[256];
+std::mutex g_scratch_lock;
 
 }  // namespace
 
@@ -888,22 +864,36 @@ int compose_noalloc_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs
   if (t->nvars != 1) return FP_E_BAD_VALUE;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return FP_E_CUDA; }
-  if (!g_scratch_ptr[dev]) {
+  unsigned char* base = g_scratch_ptr[dev].load();
+  if (!base) {
     // set-up, once per device, with that device current: host code needs the
     // device address of the array (the symbol itself is a host-side stand-in)
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_compose_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return FP_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_lock);
+    base = g_scratch_ptr[dev].load();
+    if (!base) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_compose_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return FP_E_CUDA;
+      }
+      base = (unsigned char*)ptr;
+      g_scratch_ptr[dev].store(base);
     }
-    g_scratch_ptr[dev] = (unsigned char*)ptr;
   }
-  const bool modp = dtype == FP_MODP;
-  if ((modp || dtype == FP_F64) && npairs > 0 && t->nnodes > 0 && t->dev.device >= 0 &&
-      compose_workspace_bytes(t, modp, pcoeffs == nullptr, degq, npairs) > (size_t)FP_NOALLOC_SCRATCH_BYTES)
-    return FP_E_TOO_LARGE;
-  return compose_device(t, dtype, pcoeffs, q, degq, npairs, out, st, g_scratch_ptr[dev],
-                        (size_t)FP_NOALLOC_SCRATCH_BYTES);
+  // the work space, counted by a dry run of the same driver code
+  size_t need = 0;
+  const int rc = compose_device(t, dtype, pcoeffs, q, degq, npairs, out, st, nullptr, 0, &need);
+  if (rc != FP_OK) return rc;
+  if (need > (size_t)FP_NOALLOC_SCRATCH_BYTES) return FP_E_TOO_LARGE;
+  return compose_device(t, dtype, pcoeffs, q, degq, npairs, out, st, base, (size_t)FP_NOALLOC_SCRATCH_BYTES);
+}
+
+int compose_workspace_device(const fp_tree* t, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
+                             size_t* bytes) {
+  if (!bytes) return FP_E_BAD_VALUE;
+  static const uint64_t dummy = 0;  // stands for the caller's buffers: a dry run reads none of them
+  return compose_device(t, dtype, per_pair_coeffs ? &dummy : nullptr, &dummy, degq, npairs, (void*)&dummy, nullptr,
+                        nullptr, 0, bytes);
 }
 
 }  // namespace fp

@@ -217,3 +217,41 @@ def test_argument_checks_before_any_cuda_call():
     msgs = [lib.fp_strerror(c) for c in range(0, -9, -1)]
     assert msgs[0] == b"ok" and len(set(msgs)) == len(msgs) and all(msgs)
     assert lib.fp_strerror(-99) == b"unknown status"
+
+
+def test_compose_binding_rejects_host_tensors():
+    """The composition bindings check their tensors before the C ABI sees a
+    host pointer: CPU tensors and unsupported value types raise ValueError."""
+    import torch
+    t = fpl.fp_compile_host(W.dense_univariate_exps(4), np.ones(4), "E")
+    q = torch.ones((2, 3), dtype=torch.float64)
+    for fn in (fpl.fp_compose, fpl.fp_compose_noalloc):
+        with pytest.raises(ValueError):
+            fn(t, "f64", q)
+        with pytest.raises(ValueError):
+            fn(t, "iv64", q)
+        with pytest.raises(ValueError):
+            fn(t, "f64", [[1.0, 2.0]])
+
+
+@pytest.mark.parametrize("dtype,scheme", [("modp", "E"), ("modp", "B"), ("f64", "E"), ("f64", "B")])
+def test_compose_workspace_is_affine_in_pairs(dtype, scheme):
+    """The work-space count (a dry run of the composition driver, no CUDA
+    call): per-pair buffers grow exactly linearly in the number of pairs (a
+    multiple of 32 keeps every 8-byte row set a whole number of 256-byte
+    granules), shared tables do not; the tree's own coefficients add one
+    shared row of nterms; transforms longer than 4096 add their tables."""
+    modp = dtype == "modp"
+    degp, degq = 128, 64  # products up to length 16385: four-step transforms
+    e = W.dense_univariate_exps(degp + 1)
+    t = fpl.fp_compile_host(e, np.ones(degp + 1, dtype=np.uint64 if modp else np.float64), scheme, modp=modp)
+    ws = [fpl.fp_compose_workspace(t, dtype, degq, n) for n in (32, 64, 96)]
+    assert ws[0] < ws[1] < ws[2]
+    assert ws[1] - ws[0] == ws[2] - ws[1]
+    shared = fpl.fp_compose_workspace(t, dtype, degq, 64, per_pair_coeffs=False)
+    assert shared - ws[1] == ((degp + 1) * 8 + 255) // 256 * 256
+    # at least the slots, the powers and the two product buffers per pair
+    assert ws[1] - ws[0] >= 32 * 8 * (degp * degq + 1)
+    assert fpl.fp_compose_workspace(t, dtype, degq, 0) == 0
+    with pytest.raises(fpl.FastPolyError):
+        fpl.fp_compose_workspace(t, "f64" if modp else "modp", degq, 32)

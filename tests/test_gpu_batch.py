@@ -1,18 +1,22 @@
-"""Batched evaluation: every job's result in a batch equals fp_eval's result
-for that job alone (bit for bit: the batch kernel runs the same per-tile
-code), for mixed tree sizes, schemes, variable counts and point counts; and a
-planned batch replays correctly from a captured CUDA graph."""
+"""Batched evaluation: every job's result in a batch meets its value type's
+parity bar against the CPU oracle (tests/checks.py) and equals fp_eval's
+result for that job alone (bit for bit: the batch kernel runs the same
+per-tile code), for mixed tree sizes, schemes, variable counts and point
+counts; and a planned batch replays correctly from a captured CUDA graph."""
 import numpy as np
 import pytest
 
 import workloads as W
 import paper_1307_5655_gb300 as fpl
+from checks import check_any
 from gpu_util import device_points
 
 pytestmark = pytest.mark.gpu
 
 
-def _mixed_jobs(dtype, n, seed):
+def _mixed_jobs(dtype, n, seed, host=None):
+    """n jobs of mixed shape; when host is a list, (exps, coeffs, scheme,
+    host points) of every job are appended to it for the oracle."""
     import torch
     r = W.rng(seed)
     jobs = []
@@ -37,21 +41,27 @@ def _mixed_jobs(dtype, n, seed):
         d = device_points(dtype, pts)
         out = torch.empty(fpl.out_shape(dtype, npts), dtype=fpl._torch_dtype(dtype), device="cuda")
         jobs.append((t, d, out))
+        if host is not None:
+            host.append((e, c, scheme, pts))
     return jobs
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32c", "iv64", "modp"])
 def test_batch_equals_individual_launches(dtype):
     import torch
-    jobs = _mixed_jobs(dtype, 40, {"f64": 1, "f32c": 2, "iv64": 3, "modp": 4}[dtype])
+    host = []
+    jobs = _mixed_jobs(dtype, 40, {"f64": 1, "f32c": 2, "iv64": 3, "modp": 4}[dtype], host)
     for _, _, out in jobs:
         out.fill_(0)
     fpl.fp_eval_batch(dtype, jobs)
     torch.cuda.synchronize()
-    for t, d, out in jobs:
+    for (t, d, out), (e, c, scheme, pts) in zip(jobs, host):
         alone = fpl.fp_eval(t, dtype, d)
         assert torch.equal(alone.view(torch.uint8) if alone.numel() else alone,
                            out.view(torch.uint8) if out.numel() else out)
+        if out.numel():
+            got = out.cpu().numpy()
+            check_any(dtype, e, c, pts, scheme, got.view(np.uint64) if dtype == "modp" else got)
 
 
 def test_planned_batch_replays_from_cuda_graph():

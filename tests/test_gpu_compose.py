@@ -142,6 +142,35 @@ def test_f64_componentwise(scheme, degp, degq):
         assert np.all(err <= K * U * absw + 1e-300), (j, (err / absw).max())
 
 
+def _oracle_f64_pairs(pc, qc, js):
+    """The oracle's schoolbook composition for the pairs js, on all host
+    cores (the C oracle runs outside the interpreter lock)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda j: O.compose_f64(pc[j], qc[j]), js))
+
+
+@pytest.mark.parametrize("scheme", ["E", "B"])
+def test_f64_full_size_sampled(scheme):
+    """The benchmark's FP64 composition, 4096 pairs of deg p 512 and deg q 64,
+    in one call: 16 sampled pairs componentwise against the oracle within
+    K u (|p| o |q|)_i, K = 8 (deg p (deg q + 1) + deg p + 2)."""
+    import torch
+    npairs, degp, degq = 4096, 512, 64
+    pc, qc = W.composition_case(npairs, degp, degq, 4000, "f64")
+    e = W.dense_univariate_exps(degp + 1)
+    t = fpl.fp_compile(e, np.ones(degp + 1), scheme)
+    out = fpl.fp_compose(t, "f64", _to_dev_f64(qc), pcoeffs=_to_dev_f64(pc[:, ::-1]))
+    js = np.sort(W.rng(17).choice(npairs, 16, replace=False))
+    got = out[torch.from_numpy(js).cuda()].cpu().numpy()
+    del out
+    K = 8 * (degp * (degq + 1) + degp + 2)
+    for row, (want, absw), j in zip(got, _oracle_f64_pairs(pc, qc, js), js):
+        err = np.abs(row - want)
+        assert np.all(err <= K * U * absw + 1e-300), (j, (err / np.maximum(absw, 1e-300)).max())
+
+
 def test_compose_rejects_bad_input():
     t = fpl.fp_compile(W.graded_prefix_exps(6, 2), np.ones(6), "E")
     with pytest.raises(fpl.FastPolyError):

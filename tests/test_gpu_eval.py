@@ -1,15 +1,9 @@
 """GPU parity: the CUDA evaluation path against the CPU oracle, element by
 element on seeded inputs, for every value type, scheme and edge case.
 
-Bars:
-  MODP   bit-exact against the plain sum mod p.
-  IV64   bit-exact (both bounds) against the oracle's directed-rounding walk
-         on the oracle's own tree.
-  FP64   |gpu - oracle| <= (4k + g) u S, S = sum |c_e x^e|, u = 2^-53,
-         4k u S the stated bound of the GPU path, g u S the oracle's own
-         bound (g = max total degree + nvars + k).
-  FP32C  inputs rounded to float; |hi + lo - oracle| <= 2 gamma_{2k+64}(2^-24)^2 S
-         + g u S, and the median error below k 2^-48 S.
+Bars (tests/checks.py): MODP and IV64 bit-exact, FP64 within (4k + g) u S,
+FP32C within the compensated bound; at full size, FP64 and FP32C also against
+exact rationals.
 """
 import numpy as np
 import pytest
@@ -18,49 +12,12 @@ import oracle as O
 import workloads as W
 import paper_1307_5655_gb300 as fpl
 from gpu_util import run
+from checks import check_f32c, check_f64, check_iv64, check_modp, g32
 
 pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -53
 U32 = 2.0 ** -24
-
-
-def g32(k):
-    return k * U32 / (1 - k * U32)
-
-
-def check_f64(e, c, x, got):
-    want, S = O.eval_f64(e, c, x)
-    k = len(e)
-    g = int(np.asarray(e).sum(axis=1).max()) + np.asarray(e).shape[1] + k
-    tol = (4 * k + g) * U * S
-    bad = np.abs(got - want) > tol
-    assert not bad.any(), (np.nonzero(bad)[0][:5], got[bad][:5], want[bad][:5])
-
-
-def check_f32c(e, c, x, got):
-    c32 = W.to_f32(c).astype(np.float64)
-    x32 = W.to_f32(x).astype(np.float64)
-    want, S = O.eval_f64(e, c32, x32)
-    k = len(e)
-    g = int(np.asarray(e).sum(axis=1).max()) + np.asarray(e).shape[1] + k
-    val = got[0].astype(np.float64) + got[1].astype(np.float64)
-    err = np.abs(val - want)
-    tol = 2 * g32(2 * k + 64) ** 2 * S + g * U * S + 1e-300
-    assert np.all(err <= tol), (err / S).max()
-    assert np.median(err / S) <= k * 2.0 ** -48
-    return err / S
-
-
-def check_modp(e, c, x, got):
-    assert np.array_equal(got, O.eval_modp(e, c, x))
-
-
-def check_iv64(e, c, lo, hi, scheme, got, ftab=None):
-    t = O.build_tree(e, scheme, ftab)
-    rlo, rhi = O.walk_iv64(t, t.node_coeffs(c, np.float64), lo, hi)
-    assert np.array_equal(got[0], rlo), np.nonzero(got[0] != rlo)[0][:5]
-    assert np.array_equal(got[1], rhi), np.nonzero(got[1] != rhi)[0][:5]
 
 
 # ----------------------------------------------------------------- univariate
@@ -416,18 +373,38 @@ def test_config2_full_size_sampled(k):
         check_f32c(e, c, x[:, idx], got32[:, idx])
 
 
-def test_config2_exact_rational_bound():
-    """North-star FP64 bound against exact rationals: |r - p| <= 4 n u cond."""
+@pytest.mark.parametrize("k", [1000, 3000, 10007])
+def test_config2_exact_rational_bound(k):
+    """Spec bounds against exact rationals at 256 sampled points of the
+    2^24-point launch, under each of H, E and B:
+      FP64   |r - p(x)| <= 4 n u sum |c_i||x|^i  (n = k - 1, u = 2^-53);
+      FP32C  on the float-rounded inputs, |hi + lo - p(x)| <= 2 gamma_{2k+64}(2^-24)^2
+             sum |c_i||x|^i, and the median of |hi + lo - p| / sum below k 2^-48."""
     from fractions import Fraction
-    from oracle import exact as X
-    k = 10007
-    e, c, x = W.univariate_case(k, 1 << 16, 777)
-    t = fpl.fp_compile(e, c, "B")
-    got = run(t, "f64", x)
-    coeffs_by_degree = c[::-1]
-    for j in (0, 1, 2):
-        v, s = X.exact_horner_univariate(coeffs_by_degree, x[0, j])
-        assert abs(Fraction(got[j]) - v) <= 4 * (k - 1) * Fraction(U) * s
+    from exact_pool import exact_horner_many
+    npts = 1 << 24
+    e, c, x = W.univariate_case(k, npts, 777 + k)
+    idx = _sample(npts, 256, 900 + k)
+    xs = x[0, idx]
+    c32 = W.to_f32(c).astype(np.float64)
+    xs32 = W.to_f32(xs).astype(np.float64)
+    ex64 = exact_horner_many(c[::-1], xs)
+    ex32 = exact_horner_many(c32[::-1], xs32)
+    bound64 = 4 * (k - 1) * Fraction(U)
+    bound32 = 2 * Fraction(g32(2 * k + 64)) ** 2
+    for s in ("H", "E", "B"):
+        t = fpl.fp_compile(e, c, s)
+        got = run(t, "f64", x)[idx]
+        for j, (v, sv) in enumerate(ex64):
+            assert abs(Fraction(got[j]) - v) <= bound64 * sv, (s, j)
+        got32 = run(t, "f32c", x)[:, idx]
+        rel = []
+        for j, (v, sv) in enumerate(ex32):
+            err = abs(Fraction(float(got32[0, j])) + Fraction(float(got32[1, j])) - v)
+            assert err <= bound32 * sv, (s, j)
+            rel.append(float(err / sv))
+        assert np.median(rel) <= k * 2.0 ** -48, (s, np.median(rel))
+        t.free()
 
 
 @pytest.mark.parametrize("scheme", ["E", "H"])
@@ -455,15 +432,20 @@ def test_maximum_term_count(scheme):
 
 
 def test_config3_full_size_sampled():
-    """Trivariate total degree 40 (12341 terms), 2^22 boxes and residues."""
+    """Trivariate total degree 40 (12341 terms), 2^22 boxes and residues,
+    under E and B: sampled boxes bit-exact, sampled residues exact."""
     npts = 1 << 22
     e, c, (lo, hi) = W.trivariate_case(40, npts, 300, "iv64")
     idx = _sample(npts, 48, 3)
-    t = fpl.fp_compile(e, c, "E")
-    got = run(t, "iv64", (lo, hi))
-    check_iv64(e, c, lo[:, idx], hi[:, idx], "E", got[:, idx])
+    for s in ("E", "B"):
+        t = fpl.fp_compile(e, c, s)
+        got = run(t, "iv64", (lo, hi))
+        check_iv64(e, c, lo[:, idx], hi[:, idx], s, got[:, idx])
+        t.free()
     em, cm, xm = W.trivariate_case(40, npts, 301, "modp")
-    tm = fpl.fp_compile(em, cm, "E", modp=True)
-    gm = run(tm, "modp", xm)
     idx = _sample(npts, 256, 4)
-    check_modp(em, cm, xm[:, idx], gm[idx])
+    for s in ("E", "B"):
+        tm = fpl.fp_compile(em, cm, s, modp=True)
+        gm = run(tm, "modp", xm)
+        check_modp(em, cm, xm[:, idx], gm[idx])
+        tm.free()

@@ -1,6 +1,7 @@
-"""Serving with continuous batching: each served result equals the same
-request evaluated alone (bit for bit), requests arriving while batches run
-are admitted, the HBM budget bounds what is admitted at once, and several
+"""Serving with continuous batching: each served result meets its value
+type's parity bar against the CPU oracle (tests/checks.py) and equals the
+same request evaluated alone (bit for bit), requests arriving while batches
+run are admitted, the HBM budget bounds what is admitted at once, and several
 threads may submit concurrently."""
 import threading
 import time
@@ -10,6 +11,7 @@ import pytest
 
 import workloads as W
 import paper_1307_5655_gb300 as fpl
+from checks import check_any
 
 pytestmark = pytest.mark.gpu
 DTYPES = ["f64", "f32c", "iv64", "modp"]
@@ -31,7 +33,9 @@ def _out(dtype, npts):
     return np.full(fpl.out_shape(dtype, npts), 7, dtype=npdt)
 
 
-def _requests(n, seed):
+def _requests(n, seed, terms=None):
+    """n requests of mixed value type, variable count, term count and point
+    count; terms (a dict) receives (exps, coeffs, scheme) per tree key."""
     r = W.rng(seed)
     trees = {}
     reqs = []
@@ -43,7 +47,10 @@ def _requests(n, seed):
         if key not in trees:
             e = W.dense_univariate_exps(k) if nv == 1 else W.graded_prefix_exps(k, 2)
             c = W.residues(len(e), k) if dt == "modp" else W.uniform_f64(len(e), k)
-            trees[key] = fpl.fp_compile(e, c, "E" if (k & (k - 1)) == 0 else "B", modp=dt == "modp")
+            scheme = "E" if (k & (k - 1)) == 0 else "B"
+            trees[key] = fpl.fp_compile(e, c, scheme, modp=dt == "modp")
+            if terms is not None:
+                terms[trees[key].handle] = (e, c, scheme)
         npts = int(np.exp(r.uniform(0, np.log(20000))))
         reqs.append((trees[key], dt, _host_points(dt, nv, npts, seed * 1000 + j), _out(dt, npts)))
     return trees, reqs
@@ -53,8 +60,16 @@ def _alone(tree, dt, pts):
     return fpl.fp_eval_host(tree, dt, pts)
 
 
+def _oracle_points(dt, pts):
+    """Host request points in the oracle's layout (iv64: (lo, hi))."""
+    if dt == "iv64":
+        return pts[:, 0, :], pts[:, 1, :]
+    return pts
+
+
 def test_served_results_equal_alone():
-    trees, reqs = _requests(80, 1)
+    terms = {}
+    trees, reqs = _requests(80, 1, terms)
     srv = fpl.Server(hbm_budget_bytes=64 << 20, max_batch_jobs=16, streams=3)
     r = W.rng(2)
     for tree, dt, pts, out in reqs:
@@ -66,6 +81,8 @@ def test_served_results_equal_alone():
     assert len(done) == len(reqs) and all(st == 0 for _, st, _ in done)
     for tree, dt, pts, out in reqs:
         assert np.array_equal(out.view(np.uint8), _alone(tree, dt, pts).view(np.uint8))
+        e, c, scheme = terms[tree.handle]
+        check_any(dt, e, c, _oracle_points(dt, pts), scheme, out)
     assert srv.stats()["batches"] > 1
     srv.close()
 

@@ -7,7 +7,7 @@ import pytest
 import workloads as W
 import paper_1307_5655_gb300 as fpl
 from gpu_util import device_points
-from test_gpu_eval import check_f32c, check_f64, check_modp
+from checks import check_f32c, check_f64, check_modp
 
 pytestmark = pytest.mark.gpu
 

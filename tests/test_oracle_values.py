@@ -256,3 +256,38 @@ def test_compose_f64_vs_exact():
             pw = nx
         for j in range(len(r)):
             assert abs(Fraction(r[j]) - acc[j]) <= Fraction(gamma(12 * 5 * 3)) * Fraction(ra[j])
+
+
+# ------------------------------------------------------------ exact Horner (reference of the FP64 bound)
+@pytest.mark.parametrize("k", [1, 2, 5, 17, 64])
+def test_exact_horner_equals_exact_plain_sum(k):
+    """exact_horner_univariate (coefficients indexed by degree) equals the
+    exact plain sum exact_value (terms with exponents), value and condition
+    sum sum |c_i||x|^i, at dyadic points of both signs."""
+    e, c, x = W.univariate_case(k, 7, 500 + k)  # exps k-1..0, c[j] is the coefficient of x^(k-1-j)
+    for xv in list(x[0]) + [-0.5, 0.0, 1.0]:
+        want_v, want_s = X.exact_value(e, c, (xv,))
+        got_v, got_s = X.exact_horner_univariate(c[::-1], xv)
+        assert got_v == want_v and got_s == want_s, xv
+
+
+def test_exact_horner_coefficient_order_and_signs():
+    """Hand-worked values: the coefficient of x^i sits at index i, and the
+    condition sum takes |c_i| |x|^i (not |sum|)."""
+    assert X.exact_horner_univariate([1.0, 2.0, 3.0], 2.0) == (Fraction(17), Fraction(17))
+    assert X.exact_horner_univariate([0.0, 1.0], 0.5) == (Fraction(1, 2), Fraction(1, 2))
+    assert X.exact_horner_univariate([1.0, 3.0], -0.5) == (Fraction(-1, 2), Fraction(5, 2))
+    assert X.exact_horner_univariate([-1.0, 3.0, -2.0], -0.25) == (Fraction(-15, 8), Fraction(15, 8))
+    assert X.exact_horner_univariate([0.25], -3.0) == (Fraction(1, 4), Fraction(1, 4))
+
+
+@pytest.mark.parametrize("xv", [0.75, -0.99609375, 1.0 + 2.0 ** -20])
+def test_exact_horner_geometric_closed_form_10007(xv):
+    """k = 10007 ones: sum x^i = (x^k - 1) / (x - 1) and the condition sum is
+    (|x|^k - 1) / (|x| - 1), exactly."""
+    k = 10007
+    v, s = X.exact_horner_univariate(np.ones(k), xv)
+    x = Fraction(xv)
+    ax = abs(x)
+    assert v == (x ** k - 1) / (x - 1)
+    assert s == (ax ** k - 1) / (ax - 1)
