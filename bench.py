@@ -44,6 +44,30 @@ FP64_DFMA_GPS = FP64_PEAK_TFLOPS * 1e3 / 2  # 629 G DFMA/s
 
 CPU_SAMPLE_POINTS = 1 << 18  # points per evaluation in the CPU-oracle sample
 
+# Integer-ALU issue roofline of the arithmetic mod p = 2^64 - 2^32 + 1 (the
+# mod-p walk and transforms are ALU bound: ncu shows the ALU pipe as the
+# busiest).  ALU pipe: 64 lanes per clock per SM (the rate at which ncu's ALU
+# utilisation and the measured IMAD chains agree: 64 x 152 x 2070 MHz).
+# Minimum ALU-pipe instructions of the method as written: (a b + c) mod p =
+# 3 carry additions of the 128-bit product + 2 for the addend + 19 for the
+# Goldilocks reduction on 32-bit halves = 24; a radix-2 butterfly = one
+# product (22) + a modular addition (9) + a modular subtraction (5) = 36.
+# The four 32 x 32 partial products run on the FMA pipe (IMAD), beside them.
+ALU_GOPS = 64 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9  # 20.1 T ALU lane-ops/s
+ALU_OPS_MULADD = 24
+ALU_OPS_BUTTERFLY = 36
+# Interval walk: 4 directed-rounding FP64 operations per node on the FP64
+# pipe (2 lanes per clock per SM, like DFMA)
+IV64_NODE_GPS = FP64_DFMA_GPS / 4
+
+
+def modp_issue_roofline(butterflies, multiplications, rates=None):
+    """Time bound of a mod-p workload from the ALU pipe's issue rate."""
+    ms = (butterflies * ALU_OPS_BUTTERFLY + multiplications * ALU_OPS_MULADD) / (ALU_GOPS * 1e9) * 1e3
+    return {"time_roof_alu_issue": ms,
+            "alu_issue_basis": "ALU pipe 64 lanes/clk/SM x 152 x 2070 MHz = %.1f T/s; %d ALU ops per butterfly, "
+                               "%d per multiply-add" % (ALU_GOPS / 1e3, ALU_OPS_BUTTERFLY, ALU_OPS_MULADD)}
+
 
 def workload_config():
     return {
@@ -325,6 +349,30 @@ def run_ours(args):
     value = units / (ms * 1e-3) / 1e9
     e2e_value = workload_config()["term_evals_per_step"] * world / e2e_s / 1e9
 
+    # the other configurations, measured after the timed region (one GPU)
+    configs = None
+    if world == 1 and not args.no_configs:
+        del h64, h32, ho64, ho32
+        torch.cuda.empty_cache()
+        cfg_clocks = ClockSampler()
+        cfg_clocks.start()
+        rates = fpl.fp_measure_rates()
+        configs = {"config1": measure_config1(fpl, W),
+                   "config3": measure_config3(fpl, W, rates, tune=not args.no_tune)}
+        torch.cuda.empty_cache()
+        configs["config4"] = {
+            "workload": "batched composition p o q, 4096 pairs, deg p 512, deg q 64, schemes E and B; MODP exact "
+                        "(NTT), FP64 (tensor-core split-precision convolution)",
+            "results": measure_compose(fpl, W, 4096, ["modp", "f64"], ["E", "B"], {"modp": 5, "f64": 2}, 1, rates)}
+        torch.cuda.empty_cache()
+        configs["config5"] = measure_serve(fpl, W, args.serve_requests, args.hbm_budget, overload=False)
+        configs["config5"]["workload"] = (
+            "serving stream, a stated subsample of %d of the configuration's 100k Poisson requests (same "
+            "generator: uni/bivariate, k log-uniform [8, 65536], points log-uniform [1, 2^20], value types "
+            "uniform over f64/f32c/iv64/modp)" % args.serve_requests)
+        configs["batched_vs_plain_f64"] = measure_batched(fpl, W, 256, args.hbm_budget)
+        configs["clocks"] = cfg_clocks.stop(torch.cuda.current_device())
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
@@ -360,6 +408,7 @@ def run_ours(args):
             "gpu_launches": len(trees) * len(DTYPES) * args.steps,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "configs": configs,
         }
         print(json.dumps(line))
     if dist:
@@ -500,20 +549,14 @@ def compose_work(t, degq, modp):
     return bfly, mul
 
 
-def run_compose(args):
-    """Batched composition: 4096 pairs, deg p = 512, deg q = 64 (E and B
-    schemes; MODP exact by NTT, FP64 by direct convolution)."""
+def measure_compose(fpl, W, npairs, dtypes, schemes, steps, warmup, rates):
+    """Batched composition: npairs pairs, deg p = 512, deg q = 64 (MODP exact
+    by NTT, FP64 by the tensor-core split-precision convolution); per (value
+    type, scheme) the time per batch, compositions/s and the roofline."""
     import torch
-    import workloads as W
-    import paper_1307_5655_gb300 as fpl
-    torch.cuda.set_device(0)
-    npairs, degp, degq = args.pairs, 512, 64
+    degp, degq = 512, 64
     res = {}
-    # the mod-p roofline: butterflies and multiplications mod p as the library
-    # computes them, measured on this GPU (fp_measure_rates); FP64: 2 DFMA per
-    # clock per SM
-    rates = fpl.fp_measure_rates()
-    for dt in args.compose_dtypes.split(","):
+    for dt in dtypes:
         pc, qc = W.composition_case(npairs, degp, degq, 4000, dt)
         e = W.dense_univariate_exps(degp + 1)
         if dt == "modp":
@@ -524,28 +567,268 @@ def run_compose(args):
             dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1])).cuda()
         out = torch.empty((npairs, degp * degq + 1), dtype=torch.int64 if dt == "modp" else torch.float64,
                           device="cuda")
-        for s in args.compose_schemes.split(","):
+        for s in schemes:
             t = fpl.fp_compile(e, np.ones(degp + 1, dtype=np.uint64 if dt == "modp" else np.float64), s,
                                modp=dt == "modp")
-            steps = args.steps if dt == "modp" else 1
-            ms = _timed(lambda: fpl.fp_compose(t, dt, dq, pcoeffs=dp, out=out), steps, 1 if dt == "f64" else args.warmup)
+            n_steps = steps[dt] if isinstance(steps, dict) else steps
+            ms = _timed(lambda: fpl.fp_compose(t, dt, dq, pcoeffs=dp, out=out), n_steps, warmup)
             bfly, mul = compose_work(t, degq, dt == "modp")
             if dt == "modp":
                 roof_ms = npairs * (bfly / rates["modp_butterfly"] + mul / rates["modp_muladd"]) / 1e6
                 roof = {"unit": "ms", "butterflies": bfly * npairs, "multiplications": mul * npairs,
                         "butterfly_rate_G_per_s": rates["modp_butterfly"], "mulmod_rate_G_per_s": rates["modp_muladd"],
                         "basis": "measured (fp_measure_rates)"}
+                roof.update(modp_issue_roofline(bfly * npairs, mul * npairs, rates))
             else:
                 roof_ms = npairs * mul / FP64_DFMA_GPS / 1e6
                 roof = {"unit": "ms", "multiply_adds": mul * npairs, "dfma_rate_G_per_s": FP64_DFMA_GPS,
-                        "basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
+                        "basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (the schoolbook convolution's "
+                                 "multiply-adds at the FP64 rate: what the tensor path replaces)"}
             roof.update({"time_roof": roof_ms, "time_measured": ms, "frac": roof_ms / ms})
             res["%s/%s" % (dt, s)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
                                       "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3),
                                       "roofline": roof}
-    line = {"metric": "compositions/s", "workload": "batched composition, %d pairs, deg p %d, deg q %d" %
-            (npairs, degp, degq), "results": res, "n_gpus": 1, "data": "synthetic"}
+            t.free()
+        del out, dq, dp
+        torch.cuda.empty_cache()
+    return res
+
+
+def run_compose(args):
+    """Batched composition: 4096 pairs, deg p = 512, deg q = 64 (E and B
+    schemes; MODP exact by NTT, FP64 on the tensor cores)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    rates = fpl.fp_measure_rates()
+    res = measure_compose(fpl, W, args.pairs, args.compose_dtypes.split(","), args.compose_schemes.split(","),
+                          args.steps, args.warmup, rates)
+    line = {"metric": "compositions/s", "workload": "batched composition, %d pairs, deg p 512, deg q 64" % args.pairs,
+            "results": res, "n_gpus": 1, "data": "synthetic"}
     print(json.dumps(line))
+
+
+def measure_config1(fpl, W):
+    """Dense univariate, 1024 terms, Estrin, 65536 points, FP64."""
+    import torch
+    e, c, x = W.univariate_case(1024, 65536, 1)
+    t = fpl.fp_compile(e, c, "E")
+    dx = torch.from_numpy(x).cuda()
+    out = torch.empty(65536, dtype=torch.float64, device="cuda")
+    tune = fpl.fp_tune(t, "f64", dx, out=out)
+    ms = _timed(lambda: fpl.fp_eval(t, "f64", dx, out=out), 200, 20)
+    rate = 1024 * 65536 / (ms * 1e6)
+    t.free()
+    return {"workload": "univariate dense, 1024 terms, E, 65536 points uniform[-1,1], FP64", "ms": ms,
+            "G_term_evals_per_s": rate, "launch": tune,
+            "roofline": {"bound": "fp64 issue", "peak_G_per_s": FP64_DFMA_GPS, "frac": rate / FP64_DFMA_GPS,
+                         "basis": "1 DFMA per term-eval; 2 DFMA/clk/SM x 152 x 2070 MHz"}}
+
+
+def measure_config3(fpl, W, rates, tune=True):
+    """Trivariate total degree 40 (12341 terms) at 2^22 points: intervals
+    (width 1e-6 boxes) and residues mod p, under E and B."""
+    import torch
+    npts = 1 << 22
+    res = {}
+    e, c, (lo, hi) = W.trivariate_case(40, npts, 300, "iv64")
+    dp = torch.from_numpy(np.ascontiguousarray(np.stack([lo, hi], axis=1))).cuda()
+    em, cm, xm = W.trivariate_case(40, npts, 301, "modp")
+    dm = torch.from_numpy(xm.view(np.int64)).cuda()
+    out_iv = torch.empty((2, npts), dtype=torch.float64, device="cuda")
+    out_m = torch.empty(npts, dtype=torch.int64, device="cuda")
+    for s in ("E", "B"):
+        t = fpl.fp_compile(e, c, s)
+        lt = fpl.fp_tune(t, "iv64", dp[:, :, : 1 << 18].contiguous()) if tune else None
+        ms = _timed(lambda: fpl.fp_eval(t, "iv64", dp, out=out_iv), 3, 1)
+        rate = len(e) * npts / (ms * 1e6)
+        res["iv64/%s" % s] = {"ms": ms, "G_term_evals_per_s": rate, "launch": lt,
+                              "roofline": {"bound": "fp64 issue (directed rounding)", "peak_G_per_s": IV64_NODE_GPS,
+                                           "frac": rate / IV64_NODE_GPS,
+                                           "frac_of_measured_rd_rate": rate / (rates["dadd_rd"] / 4),
+                                           "basis": "4 directed-rounding FP64 ops per node at 2 per clk per SM"}}
+        t.free()
+        tm = fpl.fp_compile(em, cm, s, modp=True)
+        lt = fpl.fp_tune(tm, "modp", dm[:, : 1 << 20].contiguous()) if tune else None
+        ms = _timed(lambda: fpl.fp_eval(tm, "modp", dm, out=out_m), 5, 1)
+        rate = len(em) * npts / (ms * 1e6)
+        peak = ALU_GOPS / ALU_OPS_MULADD
+        res["modp/%s" % s] = {"ms": ms, "G_term_evals_per_s": rate, "launch": lt,
+                              "roofline": {"bound": "integer ALU issue", "peak_G_per_s": peak, "frac": rate / peak,
+                                           "frac_of_measured_muladd_rate": rate / rates["modp_muladd"],
+                                           "basis": "%d ALU-pipe ops per (a b + c) mod p at 64 lanes/clk/SM"
+                                                    % ALU_OPS_MULADD}}
+        tm.free()
+    return res
+
+
+def serve_requests(fpl, W, n, seed=5000):
+    """The serving stream's requests: uni/bivariate polynomials with term count
+    log-uniform in [8, 65536] (bivariate: the first k monomials in graded
+    order), point count log-uniform in [1, 2^20], value type uniform over FP64 /
+    FP32C / IV64 / MODP; scheme E (B when k is not a power of two).  Trees are
+    compiled once and stay resident (8 per value type and variable count);
+    points and results live in pinned host pools.  Returns (requests, term-evals,
+    trees)."""
+    import torch
+    r = W.rng(seed)
+    dts = ["f64", "f32c", "iv64", "modp"]
+    maxp = 1 << 20
+    pools, trees = {}, {}
+    for dt in dts:
+        for nv in (1, 2):
+            cnt = maxp * nv * (2 if dt == "iv64" else 1)
+            npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
+            buf = torch.empty(cnt, dtype=torch.float64 if npdt in (np.float64,) else
+                              (torch.float32 if npdt == np.float32 else torch.int64), pin_memory=True).numpy()
+            if dt == "modp":
+                buf = buf.view(np.uint64)
+                buf[:] = W.residues(cnt, 11 + nv)
+            else:
+                buf[:] = W.uniform_f64(cnt, 13 + nv).astype(npdt)
+            pools[(dt, nv)] = buf
+            lst = []
+            for i in range(8):
+                k = int(np.exp(r.uniform(np.log(8), np.log(65536))))
+                e = W.dense_univariate_exps(k) if nv == 1 else W.graded_prefix_exps(k, 2)
+                c = W.residues(len(e), 100 + i) if dt == "modp" else W.uniform_f64(len(e), 100 + i)
+                lst.append((fpl.fp_compile(e, c, "E" if (k & (k - 1)) == 0 else "B", modp=dt == "modp"), len(e)))
+            trees[(dt, nv)] = lst
+    outs = {}
+    for dt in dts:
+        npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
+        t = torch.empty(2 * maxp * (2 if npdt == np.float32 else 1), dtype=torch.float64, pin_memory=True).numpy()
+        outs[dt] = t.view(npdt)
+    reqs = []
+    for j in range(n):
+        dt = dts[int(r.integers(0, 4))]
+        nv = 1 + int(r.integers(0, 2))
+        tree, k = trees[(dt, nv)][int(r.integers(0, 8))]
+        npts = int(np.exp(r.uniform(0, np.log(maxp))))
+        per = nv * (2 if dt == "iv64" else 1)
+        pts = pools[(dt, nv)][: per * npts].reshape((nv, 2, npts) if dt == "iv64" else (nv, npts))
+        shp = fpl.out_shape(dt, npts)
+        out = outs[dt][: int(np.prod(shp))].reshape(shp)
+        reqs.append((tree, dt, pts, out, k * npts))
+    return reqs, sum(x[4] for x in reqs), trees
+
+
+def measure_serve(fpl, W, n, hbm_budget_mib=8192, seed=5000, overload=True, isolated=True):
+    """Continuous batching on the request stream: saturated throughput (all
+    submitted at once), Poisson arrivals at 0.7 x that rate (p50/p99 latency,
+    slowdown against each request's own isolated time), an overload stream at
+    1.2 x, and one launch per request (fp_eval_host in turn)."""
+    reqs, total_evals, _trees = serve_requests(fpl, W, n, seed)
+
+    def serve(arrivals):
+        srv = fpl.Server(hbm_budget_bytes=hbm_budget_mib << 20, max_batch_jobs=256, streams=4)
+        done, tickets = {}, []
+        t0 = time.perf_counter()
+        for (tree, dt, pts, out, _), ta in zip(reqs, arrivals):
+            if ta is not None:
+                while time.perf_counter() - t0 < ta:
+                    pass
+            tickets.append(srv.submit(tree, dt, pts, out))
+            done.update({x[0]: x[2] for x in srv.poll()})
+        srv.drain(3600)
+        wall = time.perf_counter() - t0
+        done.update({x[0]: x[2] for x in srv.poll()})
+        st = srv.stats()
+        srv.close()
+        return wall, np.array([done.get(tk, np.nan) for tk in tickets], dtype=np.float64), st
+
+    serve([None] * min(8, len(reqs)))  # warm the server path
+    wall_sat, _lat_sat, st_sat = serve([None] * len(reqs))
+    rate = len(reqs) / wall_sat
+    gaps = W.rng(seed + 1).exponential(1.0 / (0.7 * rate), size=len(reqs))
+    wall_open, lat_open, st_open = serve(list(np.cumsum(gaps)))
+    lat_open = np.where(np.isnan(lat_open), np.nanmax(lat_open), lat_open)
+    res = {
+        "requests": len(reqs), "term_evals": int(total_evals),
+        "saturated": {"wall_s": wall_sat, "requests_per_s": rate, "G_term_evals_per_s": total_evals / wall_sat / 1e9,
+                      "batches": st_sat["batches"], "peak_hbm_bytes": st_sat["peak_bytes"]},
+        "poisson_0.7": {"rate_per_s": 0.7 * rate, "wall_s": wall_open,
+                        "p50_ms": float(np.percentile(lat_open, 50)) / 1e3,
+                        "p99_ms": float(np.percentile(lat_open, 99)) / 1e3,
+                        "G_term_evals_per_s": total_evals / wall_open / 1e9, "batches": st_open["batches"]},
+        "hbm_budget_MiB": hbm_budget_mib,
+    }
+    if overload:
+        wall_over, lat_over, st_over = serve(list(np.cumsum(gaps * (0.7 / 1.2))))
+        lat_over = np.where(np.isnan(lat_over), np.nanmax(lat_over), lat_over)
+        res["overload_1.2"] = {"rate_per_s": 1.2 * rate, "wall_s": wall_over,
+                               "p50_ms": float(np.percentile(lat_over, 50)) / 1e3,
+                               "p99_ms": float(np.percentile(lat_over, 99)) / 1e3,
+                               "G_term_evals_per_s": total_evals / wall_over / 1e9, "batches": st_over["batches"],
+                               "peak_hbm_bytes": st_over["peak_bytes"]}
+    if isolated:
+        iso = np.empty(len(reqs))
+        t0 = time.perf_counter()
+        for i, (tree, dt, pts, out, _) in enumerate(reqs):
+            ti = time.perf_counter()
+            fpl.fp_eval_host(tree, dt, pts)
+            iso[i] = (time.perf_counter() - ti) * 1e6
+        wall_seq = time.perf_counter() - t0
+        slow = lat_open / iso
+        res["poisson_0.7"].update({"slowdown_p50": float(np.nanpercentile(slow, 50)),
+                                   "slowdown_p99": float(np.nanpercentile(slow, 99)),
+                                   "slowdown_note": "latency / the request's own run time alone (fp_eval_host)"})
+        res["one_launch_per_request"] = {"wall_s": wall_seq, "requests_per_s": len(reqs) / wall_seq,
+                                         "G_term_evals_per_s": total_evals / wall_seq / 1e9,
+                                         "continuous_batching_speedup": wall_seq / wall_sat}
+    return res
+
+
+def run_compose_accuracy(args):
+    """FP64 composition, 4096 pairs of deg p 512 and deg q 64 (schemes E and
+    B): time and error against the oracle (8 sampled pairs) for the tensor-core
+    products with 6, 7 and 8 slices and for the direct FP64 convolution.
+    Errors are |r - oracle| over s = |p| o |q|, the plain walk on absolute
+    values: componentwise (max over coefficients of err_i / s_i), local (over
+    the maximum of s within +-128 coefficients: the tensor path's blockwise
+    bar) and normwise (max err over max s)."""
+    import os as _os
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    import workloads as W
+    import oracle as O
+    import paper_1307_5655_gb300 as fpl
+    from scipy.ndimage import maximum_filter1d
+    torch.cuda.set_device(0)
+    npairs, degp, degq = args.pairs, 512, 64
+    pc, qc = W.composition_case(npairs, degp, degq, 4000, "f64")
+    js = np.sort(W.rng(17).choice(npairs, 8, replace=False))
+    with ThreadPoolExecutor(max_workers=_os.cpu_count() or 1) as ex:
+        ref = list(ex.map(lambda j: O.compose_f64(pc[j], qc[j]), js))
+    dq = torch.from_numpy(qc).cuda()
+    dp = torch.from_numpy(np.ascontiguousarray(pc[:, ::-1])).cuda()
+    out = torch.empty((npairs, degp * degq + 1), dtype=torch.float64, device="cuda")
+    e = W.dense_univariate_exps(degp + 1)
+    res = {}
+    for s in args.compose_schemes.split(","):
+        t = fpl.fp_compile(e, np.ones(degp + 1), s)
+        for name, (slices, min_len) in (("tc6", (6, 0)), ("tc7", (7, 0)), ("tc8", (8, 0)), ("direct", (0, -1))):
+            fpl.fp_set_compose_f64(slices, min_len)
+            ms = _timed(lambda: fpl.fp_compose(t, "f64", dq, pcoeffs=dp, out=out), 1 if name == "direct" else 2, 1)
+            got = out[torch.from_numpy(js).cuda()].cpu().numpy()
+            comp, loc, norm = 0.0, 0.0, 0.0
+            for row, (want, absw) in zip(got, ref):
+                err = np.abs(row - want)
+                nz = absw > 1e-290
+                comp = max(comp, float((err[nz] / absw[nz]).max()))
+                locs = maximum_filter1d(absw, size=257, mode="constant", cval=0.0)
+                loc = max(loc, float((err / np.maximum(locs, 1e-300)).max()))
+                norm = max(norm, float(err.max() / absw.max()))
+            res["%s/%s" % (s, name)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
+                                        "err_componentwise_max": comp, "err_local_max": loc,
+                                        "err_normwise_max": norm}
+        t.free()
+    fpl.fp_set_compose_f64(0, 0)
+    print(json.dumps({"metric": "FP64 composition time and error vs oracle per product method",
+                      "workload": "%d pairs, deg p 512, deg q 64 (q uniform[-1,1]/65), 8 sampled pairs" % npairs,
+                      "error_basis": "err / s, s = |p| o |q| (componentwise over s_i > 1e-290; local over max s "
+                                     "within +-128; normwise over max s)", "u": 2.0 ** -53, "results": res}))
 
 
 def run_eval_config(args):
@@ -609,122 +892,19 @@ def run_eval_config(args):
 
 
 def run_serve(args):
-    """Serving stream: requests each a univariate or bivariate polynomial with
-    term count log-uniform in [8, 65536] (bivariate: the first k monomials in
-    graded order), point count log-uniform in [1, 2^20], value type uniform
-    over FP64 / FP32C / IV64 / MODP, coefficients and points uniform; scheme E
-    (B when k is not a power of two).  Trees are compiled once and stay
-    resident (a pool of 8 per value type and variable count).  Measured: the
-    saturated throughput (all requests submitted at once), then Poisson
-    arrivals at 0.7 x that rate with p50/p99 latency, an overload stream at
-    1.2 x, and the same requests served one launch at a time (fp_eval_host per
-    request)."""
+    """Serving stream (serve_requests): saturated throughput, Poisson arrivals
+    at 0.7 x that rate with p50/p99 latency, an overload stream at 1.2 x, and
+    the same requests served one launch at a time (fp_eval_host per request)."""
     import torch
     import workloads as W
     import paper_1307_5655_gb300 as fpl
     torch.cuda.set_device(0)
-    r = W.rng(5000)
-    dts = ["f64", "f32c", "iv64", "modp"]
-    maxp = 1 << 20
-    pools, trees = {}, {}
-    for dt in dts:
-        for nv in (1, 2):
-            n = maxp * nv * (2 if dt == "iv64" else 1)
-            npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
-            buf = torch.empty(n, dtype=torch.float64 if npdt in (np.float64,) else
-                              (torch.float32 if npdt == np.float32 else torch.int64), pin_memory=True).numpy()
-            if dt == "modp":
-                buf = buf.view(np.uint64)
-                buf[:] = W.residues(n, 11 + nv)
-            else:
-                buf[:] = W.uniform_f64(n, 13 + nv).astype(npdt)
-            pools[(dt, nv)] = buf
-            lst = []
-            for i in range(8):
-                k = int(np.exp(r.uniform(np.log(8), np.log(65536))))
-                e = W.dense_univariate_exps(k) if nv == 1 else W.graded_prefix_exps(k, 2)
-                c = W.residues(len(e), 100 + i) if dt == "modp" else W.uniform_f64(len(e), 100 + i)
-                lst.append((fpl.fp_compile(e, c, "E" if (k & (k - 1)) == 0 else "B", modp=dt == "modp"), len(e)))
-            trees[(dt, nv)] = lst
-    outs = {}
-    for dt in dts:
-        npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dt]
-        t = torch.empty(2 * maxp * (2 if npdt == np.float32 else 1), dtype=torch.float64, pin_memory=True).numpy()
-        outs[dt] = t.view(npdt)
-    reqs = []
-    for j in range(args.requests):
-        dt = dts[int(r.integers(0, 4))]
-        nv = 1 + int(r.integers(0, 2))
-        tree, k = trees[(dt, nv)][int(r.integers(0, 8))]
-        npts = int(np.exp(r.uniform(0, np.log(maxp))))
-        per = nv * (2 if dt == "iv64" else 1)
-        pts = pools[(dt, nv)][: per * npts].reshape((nv, 2, npts) if dt == "iv64" else (nv, npts))
-        shp = fpl.out_shape(dt, npts)
-        out = outs[dt][: int(np.prod(shp))].reshape(shp)
-        reqs.append((tree, dt, pts, out, k * npts))
-    total_evals = sum(x[4] for x in reqs)
-
-    def serve(arrivals):
-        """Latencies (us) in request order, wall time, server statistics."""
-        srv = fpl.Server(hbm_budget_bytes=args.hbm_budget << 20, max_batch_jobs=256, streams=4)
-        done, tickets = {}, []
-        t0 = time.perf_counter()
-        for (tree, dt, pts, out, _), ta in zip(reqs, arrivals):
-            if ta is not None:
-                while time.perf_counter() - t0 < ta:
-                    pass
-            tickets.append(srv.submit(tree, dt, pts, out))
-            done.update({x[0]: x[2] for x in srv.poll()})
-        srv.drain(3600)
-        wall = time.perf_counter() - t0
-        done.update({x[0]: x[2] for x in srv.poll()})
-        st = srv.stats()
-        srv.close()
-        return wall, np.array([done.get(tk, np.nan) for tk in tickets], dtype=np.float64), st
-
-    serve([None] * 8)  # warm-up on a few requests is implicit in the first call's trees
-    wall_sat, lat_sat, st_sat = serve([None] * len(reqs))
-    rate = len(reqs) / wall_sat
-    gaps = W.rng(5001).exponential(1.0 / (0.7 * rate), size=len(reqs))
-    wall_open, lat_open, st_open = serve(list(np.cumsum(gaps)))
-    lat_open = np.where(np.isnan(lat_open), np.nanmax(lat_open), lat_open)
-    # overload: arrivals at 1.2 x the saturated rate (the queue grows for the
-    # whole stream; the server must keep its throughput and admit by age)
-    wall_over, lat_over, st_over = serve(list(np.cumsum(gaps * (0.7 / 1.2))))
-    lat_over = np.where(np.isnan(lat_over), np.nanmax(lat_over), lat_over)
-    # each request alone, one launch: its isolated service time (the
-    # denominator of its slowdown under the Poisson stream)
-    iso = np.empty(len(reqs))
-    t0 = time.perf_counter()
-    for i, (tree, dt, pts, out, _) in enumerate(reqs):
-        ti = time.perf_counter()
-        fpl.fp_eval_host(tree, dt, pts)
-        iso[i] = (time.perf_counter() - ti) * 1e6
-    wall_seq = time.perf_counter() - t0
-    slow = lat_open / iso
-    line = {
-        "metric": "p50/p99 serve latency and throughput",
-        "workload": "%d requests, uni/bivariate, k log-uniform [8, 65536], points log-uniform [1, 2^20], "
-                    "value types uniform over f64/f32c/iv64/modp" % len(reqs),
-        "term_evals": total_evals,
-        "saturated": {"wall_s": wall_sat, "requests_per_s": rate, "G_term_evals_per_s": total_evals / wall_sat / 1e9,
-                      "batches": st_sat["batches"], "peak_hbm_bytes": st_sat["peak_bytes"]},
-        "poisson_0.7": {"rate_per_s": 0.7 * rate, "wall_s": wall_open,
-                        "p50_ms": float(np.percentile(lat_open, 50)) / 1e3,
-                        "p99_ms": float(np.percentile(lat_open, 99)) / 1e3,
-                        "slowdown_p50": float(np.nanpercentile(slow, 50)),
-                        "slowdown_p99": float(np.nanpercentile(slow, 99)),
-                        "slowdown_note": "latency / the request's own run time alone (fp_eval_host)",
-                        "G_term_evals_per_s": total_evals / wall_open / 1e9, "batches": st_open["batches"]},
-        "overload_1.2": {"rate_per_s": 1.2 * rate, "wall_s": wall_over,
-                         "p50_ms": float(np.percentile(lat_over, 50)) / 1e3,
-                         "p99_ms": float(np.percentile(lat_over, 99)) / 1e3,
-                         "G_term_evals_per_s": total_evals / wall_over / 1e9, "batches": st_over["batches"],
-                         "peak_hbm_bytes": st_over["peak_bytes"]},
-        "one_launch_per_request": {"wall_s": wall_seq, "requests_per_s": len(reqs) / wall_seq,
-                                   "G_term_evals_per_s": total_evals / wall_seq / 1e9},
-        "hbm_budget_MiB": args.hbm_budget, "n_gpus": 1, "data": "synthetic",
-    }
+    res = measure_serve(fpl, W, args.requests, args.hbm_budget)
+    line = {"metric": "p50/p99 serve latency and throughput",
+            "workload": "%d requests, uni/bivariate, k log-uniform [8, 65536], points log-uniform [1, 2^20], "
+                        "value types uniform over f64/f32c/iv64/modp" % args.requests,
+            "n_gpus": 1, "data": "synthetic"}
+    line.update(res)
     print(json.dumps(line))
 
 
@@ -788,7 +968,7 @@ def run_staircase(args):
                       "results": res}))
 
 
-def run_batched(args):
+def measure_batched(fpl, W, n, hbm_budget_mib=8192):
     """Many FP64 univariate polynomials of uneven size -- the FP64 univariate
     part of the serving mix: k log-uniform in [8, 65536] dense terms, points
     log-uniform in [1, 2^20], coefficients and points uniform[-1, 1], scheme E
@@ -803,11 +983,7 @@ def run_batched(args):
     warm-up pass; every result is checked against the plain kernel's within
     8 k u S (S = sum |c_e| |x|^e, both are FP64 evaluations within 4 k u S)."""
     import torch
-    import workloads as W
-    import paper_1307_5655_gb300 as fpl
-    torch.cuda.set_device(0)
     r = W.rng(6000)
-    n = args.batch_polys
     polys = []
     for i in range(n):
         k = int(np.exp(r.uniform(np.log(8), np.log(65536))))
@@ -852,7 +1028,7 @@ def run_batched(args):
             o = fpl.fp_eval_plain_f64(coef_d[i], d)
             out_h[i].copy_(o, non_blocking=True)
 
-    srv = fpl.Server(hbm_budget_bytes=args.hbm_budget << 20, max_batch_jobs=256, streams=4)
+    srv = fpl.Server(hbm_budget_bytes=hbm_budget_mib << 20, max_batch_jobs=256, streams=4)
     pts_srv = [p.numpy() for p in pts_h]
 
     def served():
@@ -887,7 +1063,16 @@ def run_batched(args):
                                    "server_host_buffers": evals / host["server_ms"] / 1e6,
                                    "plain_host_buffers": evals / host["plain_with_copies_ms"] / 1e6},
             "max_error_over_8kuS": worst, "n_gpus": 1, "data": "synthetic"}
-    print(json.dumps(line))
+    return line
+
+
+def run_batched(args):
+    """measure_batched on --batch-polys polynomials (one JSON line)."""
+    import torch
+    import workloads as W
+    import paper_1307_5655_gb300 as fpl
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_batched(fpl, W, args.batch_polys, args.hbm_budget)))
 
 
 def run_peaks(args):
@@ -1009,7 +1194,8 @@ def run_hybrid(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "eval-configs", "serve", "accuracy",
+    ap.add_argument("--workload", default="univariate", choices=["univariate", "compose", "compose-accuracy",
+                                                                "eval-configs", "serve", "accuracy",
                                                                 "staircase", "hybrid", "peaks", "rns", "batched"],
                     help="univariate: the benchmark line; the others print their own measurement line")
     ap.add_argument("--pairs", type=int, default=4096)
@@ -1031,11 +1217,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shapes)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="benchmark line only: skip the other configurations' measurements")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving stream measured beside the benchmark line")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
     elif args.workload == "compose":
         run_compose(args)
+    elif args.workload == "compose-accuracy":
+        run_compose_accuracy(args)
     elif args.workload == "eval-configs":
         run_eval_config(args)
     elif args.workload == "serve":

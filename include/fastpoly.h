@@ -322,8 +322,16 @@ void fp_server_destroy(fp_server* s);
  *   p        tree from fp_compile (nvars = 1).  FP_MODP needs a FP_MODP tree,
  *            FP_F64 a FP_F64 tree.
  *   dtype    FP_MODP (exact; products by number-theoretic transforms) or
- *            FP_F64 (products by direct convolution: componentwise error
- *            bounded by the same walk run on |p|, |q|).
+ *            FP_F64: products whose operands both have at least 256
+ *            coefficients run on the tensor cores -- each operand cut into
+ *            blocks of 64 coefficients with an exponent each, every value
+ *            split into 8 signed 7-bit slices (bf16), the slice products
+ *            summed exactly in FP32 and recombined in 64-bit fixed point per
+ *            block of the result; shorter products by direct convolution.
+ *            Error per product coefficient: about 2^-52 of the largest
+ *            block products meeting there (2^-45 with 7 slices); the tests
+ *            hold the result componentwise to the bound of the plain FP64
+ *            walk run on |p|, |q| (fp_set_compose_f64 changes the settings).
  *   pcoeffs  device, [npairs][nterms] in the term order given to fp_compile,
  *            or NULL to use the tree's own coefficients for every pair.  Terms
  *            whose compile-time coefficient was zero are not in the tree and
@@ -333,12 +341,21 @@ void fp_server_destroy(fp_server* s);
  * Work space (about (lazy height + 6) x npairs x deg(p) x degq x 8 bytes) is
  * allocated on `stream` from the library's stream-ordered pool (which keeps
  * up to 4 GiB of freed device memory mapped for reuse) and released before returning;
- * the call synchronises `stream` while it uploads its tables.
+ * the call synchronises `stream` while it uploads its tables, and an FP64
+ * composition that used the tensor cores synchronises it again at the end
+ * to report FP_E_TIMEOUT (a bounded wait for tensor-core work gave up).
  * Errors: FP_E_BAD_VALUE, FP_E_DTYPE, FP_E_TOO_LARGE (output longer than
- * 2^26), FP_E_NOMEM, FP_E_CUDA.
+ * 2^26), FP_E_NOMEM, FP_E_CUDA, FP_E_TIMEOUT.
  */
 int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void* q, int32_t degq,
                int64_t npairs, void* out, void* stream);
+
+/* fp_set_compose_f64 -- process-wide settings of FP64 composition products
+ * (no counterpart in the paper): slices per operand on the tensor cores (6,
+ * 7 or 8; 0 = 8) and the shortest operand length sent to them (0 = 256;
+ * negative: never, every product by direct convolution).  Calls already
+ * enqueued keep the settings they started with.  Errors: FP_E_BAD_VALUE. */
+int fp_set_compose_f64(int slices, int min_len);
 
 /* fp_compose_workspace -- the device work space, in bytes, that fp_compose
  * and fp_compose_noalloc use for these arguments (per_pair_coeffs: non-zero

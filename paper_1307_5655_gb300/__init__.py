@@ -43,6 +43,7 @@ for _name, _args in {
     "fp_compose": [_P, _I, _P, _P, _I, _I64, _P, _P],
     "fp_compose_noalloc": [_P, _I, _P, _P, _I, _I64, _P, _P],
     "fp_compose_workspace": [_P, _I, _I, _I, _I64, ctypes.POINTER(ctypes.c_size_t)],
+    "fp_set_compose_f64": [_I, _I],
 }.items():
     getattr(_lib, _name).restype = _I
     getattr(_lib, _name).argtypes = _args
@@ -407,6 +408,13 @@ def fp_compose(tree, dtype, q, pcoeffs=None, out=None, degp=None, stream=None):
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def fp_set_compose_f64(slices=0, min_len=0):
+    """Process-wide FP64 composition settings: tensor-core slices per operand
+    (6, 7, 8; 0 = 8) and the shortest operand sent to the tensor cores
+    (0 = 256; negative = direct convolution only)."""
+    _check(_lib.fp_set_compose_f64(slices, min_len), "fp_set_compose_f64")
 
 
 def fp_compose_workspace(tree, dtype, degq, npairs, per_pair_coeffs=True):

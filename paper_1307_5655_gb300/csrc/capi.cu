@@ -299,6 +299,7 @@ int compose_noalloc_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs
                            int64_t npairs, void* out, cudaStream_t st);
 int compose_workspace_device(const fp_tree* t, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
                              size_t* bytes);
+int set_compose_f64(int slices, int min_len);
 
 }  // namespace fp
 
@@ -710,6 +711,8 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
   if (p && (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev.device)) { cudaGetLastError(); return FP_E_BAD_VALUE; }
   return compose_device(p, dtype, pcoeffs, q, degq, npairs, out, (cudaStream_t)stream, nullptr, 0, nullptr);
 }
+
+int fp_set_compose_f64(int slices, int min_len) { return set_compose_f64(slices, min_len); }
 
 int fp_compose_workspace(const fp_tree* p, fp_dtype dtype, int per_pair_coeffs, int32_t degq, int64_t npairs,
                          size_t* bytes) {

@@ -10,7 +10,9 @@
 //   MODP: by number-theoretic transforms over p = 2^64 - 2^32 + 1 (roots of
 //         unity of order 2^32 exist): in shared memory for lengths <= 4096,
 //         by a four-step transform (two passes) above;
-//   FP64: by direct convolution (componentwise error bound).
+//   FP64: on the tensor cores (conv_tc.cu: bf16 slices of 64-coefficient
+//         blocks with a block exponent each, exact integer recombination),
+//         or by direct convolution for short operands.
 // Powers q^d follow the tree's power program (squarings and products by q).
 #include <algorithm>
 #include <atomic>
@@ -25,6 +27,17 @@
 #include "tree.hpp"
 
 namespace fp {
+
+size_t conv_tc_workspace(int alen, int blen, int64_t npairs, int slices);
+int conv_tc(const double* a, int64_t a_pitch, int alen, const double* b, int64_t b_pitch, int blen, double* out,
+            int64_t out_pitch, int mode, const double* init, int64_t init_pitch, int64_t npairs, void* work,
+            int* status, int slices, cudaStream_t st);
+
+// FP64 products: slices per operand on the tensor cores, and the shortest
+// operand length that goes to them (shorter ones: direct convolution)
+static std::atomic<int> g_f64_slices{8};
+static std::atomic<int> g_f64_tc_min{256};
+
 namespace {
 
 constexpr uint64_t kP = 0xFFFFFFFF00000001ull;
@@ -699,6 +712,21 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
   for (int k = 0; k < npow; ++k) maxprod = std::max(maxprod, t->pow_deg[k] * degq + 1);
   const int64_t Lmax = modp ? next_pow2(maxprod) : maxprod;
   Buf ta{cm.alloc(npairs * Lmax * esz), Lmax}, tb{cm.alloc(npairs * Lmax * esz), Lmax};
+  // FP64 products on the tensor cores: one work buffer for the longest
+  // operands (A: slots and powers, B: powers; the work space grows with both)
+  const int slices = g_f64_slices.load(), tc_min = g_f64_tc_min.load();
+  int64_t maxA = 1, maxB = 1;
+  for (size_t s = 0; s < cap.size(); ++s) maxA = std::max(maxA, cap[s]);
+  for (int k = 0; k < npow; ++k) maxB = std::max(maxB, qp[k].pitch);
+  maxA = std::max(maxA, maxB);
+  const bool tc_any = !modp && tc_min > 0 && maxB >= tc_min;
+  void* tcw = nullptr;
+  int* tc_status = nullptr;
+  if (tc_any) {
+    tcw = cm.alloc(conv_tc_workspace((int)maxA, (int)maxB, npairs, slices));
+    tc_status = (int*)cm.alloc(sizeof(int));
+    if (cm.live() && cudaMemsetAsync(tc_status, 0, sizeof(int), st) != cudaSuccess) cm.status = FP_E_CUDA;
+  }
   if (cm.status != FP_OK) { cm.release(); return cm.status; }
   // transforms of the powers q^d at the lengths they are used at; for
   // n <= 4096 (used only by the fused product kernel) times 1/n, the scaling
@@ -746,6 +774,18 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       cm.mul_inv(ta, fb, n, dst, (int)rl, mode, (const uint64_t*)init, init_pitch);
     } else {
       if (!cm.live()) return;
+      if (tc_any && alen >= tc_min && blen >= tc_min) {
+        // the longer operand as the rows (fewer empty rows per tile); both
+        // are sliced before the product is written, so dst may be A
+        const bool swap = alen < blen;
+        const int rc = conv_tc((const double*)(swap ? B.ptr : A.ptr), swap ? B.pitch : A.pitch,
+                               (int)(swap ? blen : alen), (const double*)(swap ? A.ptr : B.ptr),
+                               swap ? A.pitch : B.pitch, (int)(swap ? alen : blen), (double*)dst.ptr, dst.pitch,
+                               mode, (const double*)init, init_pitch, npairs, tcw, tc_status, slices, st);
+        if (rc != FP_OK) cm.status = rc;
+        cm.check();
+        return;
+      }
       // the source may be the destination slot: convolve from a copy
       k_copy_rows<double><<<grid_for(npairs * alen), 256, 0, st>>>((const double*)A.ptr, A.pitch, (double*)ta.ptr,
                                                                     ta.pitch, (int)alen, npairs, 0);
@@ -837,10 +877,26 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
       product(acc[t->lh[R]], degval(R) + 1, qd, qd.pitch, qk, outb, 0, nullptr, 0);
     }
   }
-  const int rc = cm.status;
+  int rc = cm.status;
+  if (rc == FP_OK && tc_any && cm.live()) {
+    // a tensor-core tile that gave up waiting for its products reports here
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, tc_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = FP_E_CUDA;
+    else if (flag)
+      rc = FP_E_TIMEOUT;
+  }
   cm.release();
   if (cm.dry) *dry_bytes = cm.arena_used;
   return rc;
+}
+
+int set_compose_f64(int slices, int min_len) {
+  if (slices != 0 && (slices < 6 || slices > 8)) return FP_E_BAD_VALUE;
+  g_f64_slices.store(slices ? slices : 8);
+  g_f64_tc_min.store(min_len == 0 ? 256 : (min_len < 0 ? 0 : min_len));
+  return FP_OK;
 }
 
 

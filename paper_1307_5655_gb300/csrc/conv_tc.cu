@@ -1,0 +1,449 @@
+// FP64 polynomial products on the tensor cores: the products (S + c) q^d of
+// the composition walk (Sec. 2.1 over polynomial values, Sec. 1.2), batched
+// over pairs, as split-precision bf16 matrix products (tcgen05, TMEM) with an
+// exact integer recombination.
+//
+// Blocks.  Both operands are cut into blocks of T = 64 coefficients; block u
+// of a has the exponent bound alpha_u (every |a_i| < 2^alpha_u), and the
+// window of b that output block w meets at step v -- b[64 v - 63 .. 64 v + 63]
+// -- has the bound beta_v.  Output block w (coefficients 64 w .. 64 w + 63) is
+//     out[64 w + r] = sum_v sum_s a[64 (w - v) + s] b[64 v + r - s],
+// so for every v one matrix product D[w][r] = sum_s A[w - v][s] B_v[r][s]
+// with A the blocks of a as rows (a window of rows shifted by one per step)
+// and B_v the 64 x 64 Toeplitz matrix of the window, built in shared memory.
+//
+// Slices.  x in a block of bound 2^alpha is rounded to the integer
+// X = round(x 2^(6 - alpha + 7 (S - 1))) (|X| <= 2^(7 S - 1)) and written in
+// S signed base-128 digits d_0 (most significant, |d_0| <= 64) .. d_{S-1}
+// (in [-64, 63]); slice i holds d_i 2^(-7 i) as a bf16 (exact).  The product
+// of slices i (of a) and j (of b) is d d' 2^(-7 (i + j)); the pairs with
+// i + j <= S - 1 are kept (the dropped ones are below 2^(-7 S) of the block
+// products).  Accumulator g (g = i + j = 0..3) sums one group exactly: over
+// K = 64 its integer value D_g = sum d d' has |D_g| <= 4 * 64^3 < 2^22 and
+// FP32 holds it without rounding.  Accumulator 4 sums the groups g >= 4 with
+// FP32 rounding far below the recombination's resolution.
+//
+// Recombination.  Each step reads the five accumulators (tcgen05.ld), turns
+// each into its integer with one FMA against 1.5 2^23 (exact for |D| < 2^22),
+// and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 + D_4 (|C| < 2^49), so
+// that the step contributes C 2^(alpha_{w-v} + beta_v - 40).  Each output row
+// keeps a 64-bit fixed-point accumulator with unit 2^F_w, F_w = max over the
+// row's steps of alpha + beta - 40 - (15 - hr), hr the bits of the row's step
+// count: every contribution stays below 2^(62 - hr) units and their sum
+// below 2^62; smaller contributions are rounded to the unit.  No FP64
+// arithmetic runs per step (GB300's FP64 rate is 1/64 of its FP32 rate).  The
+// result is (double) acc 2^F_w.
+//
+// Error: |result - a * b|_j <= (S + 2) 2^(-7 S) sum_s 2^(alpha + beta) (the
+// slices and dropped pairs, per block product) plus 2^F_w per step (the
+// fixed-point rounding) plus one rounding to double: about 2^-52 (S = 8) of
+// the largest block products that meet at coefficient j.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fastpoly.h"
+
+namespace fp {
+namespace tc {
+
+constexpr int T = 64;                // coefficients per block: N and K of one step
+constexpr int V = 16;                // steps per load of the A window
+constexpr int MROWS = 128;           // output blocks per tile (MMA M, TMEM lanes)
+constexpr int WROWS = MROWS + V;     // rows of the A window in shared memory
+constexpr int STRIP = WROWS * 16;    // bytes of one (slice, 8-column chunk) strip of A
+constexpr int BSTRIP = T * 16;       // bytes of one (slice, 8-column chunk) strip of B_v
+constexpr int NACC = 5;              // TMEM accumulators of 64 columns
+constexpr int THREADS = 256;
+constexpr int ZERO_EXP = -100000;    // exponent bound of an all-zero block
+constexpr int TMEM_COLS = 512;       // power of two >= NACC * 64
+constexpr int SMEM_MIN = 120 * 1024; // at least half the SM: one tile per SM holds the TMEM
+
+__host__ __device__ constexpr int smem_bytes(int S) { return S * 8 * STRIP + S * 8 * BSTRIP + S * 128 * 2; }
+
+// ------------------------------------------------------------------ slicing
+// smallest alpha with |x| < 2^alpha (ZERO_EXP for x = 0)
+__device__ __forceinline__ int exp_bound(double x) {
+  const long long b = __double_as_longlong(x);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return ZERO_EXP;
+  const int e = (int)((b >> 52) & 0x7FF);
+  return e == 0 ? -1022 : e - 1022;
+}
+
+// X = round(x 2^(6 - alpha + 7 (S - 1))) from the bits of x (|x| < 2^alpha)
+template <int S>
+__device__ __forceinline__ long long to_fixed(double x, int alpha) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  long long m = b & 0xFFFFFFFFFFFFFll;
+  if (e) m |= 1ll << 52;
+  const int sh = (e ? e : 1) - 1075 + 6 - alpha + 7 * (S - 1);  // |x| = m 2^(max(e,1) - 1075)
+  long long X;
+  if (sh >= 0) X = m << sh;  // then m 2^sh < 2^(7 S - 1)
+  else if (sh > -64) X = (m + (1ll << (-sh - 1))) >> (-sh);
+  else X = 0;
+  return b < 0 ? -X : X;
+}
+
+// the bf16 bit pattern of d 2^(-7 i) (exact: |d| <= 64)
+__device__ __forceinline__ uint32_t bf16_digit(int d, int i) {
+  const float f = __int2float_rn(d) * __int_as_float((127 - 7 * i) << 23);
+  return __float_as_uint(f) >> 16;
+}
+
+// 8 consecutive values of one block row -> S 16-byte chunks (one per slice)
+template <int S>
+__device__ __forceinline__ void slice8(const double* x, int alpha, uint4* chunk) {
+  uint32_t w[S][4];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    long long X = alpha == ZERO_EXP ? 0 : to_fixed<S>(x[e], alpha);
+    int d[S];
+#pragma unroll
+    for (int i = S - 1; i > 0; --i) {
+      const int r = (int)((X + 64) & 127) - 64;
+      d[i] = r;
+      X = (X - r) >> 7;
+    }
+    d[0] = (int)X;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const uint32_t h = bf16_digit(d[i], i);
+      if (e & 1) w[i][e >> 1] |= h << 16;
+      else w[i][e >> 1] = h;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < S; ++i) chunk[i] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+
+// Blocks of a as rows: ahat[pair][slice][chunk][u] (16 bytes: coefficients
+// 64 u + 8 chunk .. + 7), alpha[pair][u].  Eight threads per block row.
+template <int S>
+__global__ void k_slice_rows(const double* a, int64_t a_pitch, int alen, int nA, int64_t npairs, uint4* ahat,
+                             int* alpha) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = gid >> 3;
+  const int t = (int)(gid & 7);
+  const bool valid = row < npairs * nA;
+  const int64_t pr = valid ? row / nA : 0;
+  const int u = valid ? (int)(row - pr * nA) : 0;
+  double x[8];
+  int al = ZERO_EXP;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int idx = 64 * u + 8 * t + e;
+    x[e] = (valid && idx < alen) ? a[pr * a_pitch + idx] : 0.0;
+    al = max(al, exp_bound(x[e]));
+  }
+  al = max(al, __shfl_xor_sync(0xffffffffu, al, 1));
+  al = max(al, __shfl_xor_sync(0xffffffffu, al, 2));
+  al = max(al, __shfl_xor_sync(0xffffffffu, al, 4));
+  if (!valid) return;
+  uint4 ch[S];
+  slice8<S>(x, al, ch);
+#pragma unroll
+  for (int i = 0; i < S; ++i) ahat[((pr * S + i) * 8 + t) * nA + u] = ch[i];
+  if (t == 0) alpha[pr * nA + u] = al;
+}
+
+// Windows of b reversed: rhat[pair][v][slice][t'] (bf16) holds
+// b[64 v + 63 - t'] for t' < 127 (0 at t' = 127 and outside b), beta[pair][v].
+// Sixteen threads per window, eight entries each.
+template <int S>
+__global__ void k_slice_windows(const double* b, int64_t b_pitch, int blen, int nV, int64_t npairs, uint4* rhat,
+                                int* beta) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t win = gid >> 4;
+  const int m = (int)(gid & 15);
+  const bool valid = win < npairs * nV;
+  const int64_t pr = valid ? win / nV : 0;
+  const int v = valid ? (int)(win - pr * nV) : 0;
+  double x[8];
+  int be = ZERO_EXP;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int tp = 8 * m + e;
+    const int idx = 64 * v + 63 - tp;
+    x[e] = (valid && tp < 127 && idx >= 0 && idx < blen) ? b[pr * b_pitch + idx] : 0.0;
+    be = max(be, exp_bound(x[e]));
+  }
+  be = max(be, __shfl_xor_sync(0xffffffffu, be, 1));
+  be = max(be, __shfl_xor_sync(0xffffffffu, be, 2));
+  be = max(be, __shfl_xor_sync(0xffffffffu, be, 4));
+  be = max(be, __shfl_xor_sync(0xffffffffu, be, 8));
+  if (!valid) return;
+  uint4 ch[S];
+  slice8<S>(x, be, ch);
+#pragma unroll
+  for (int i = 0; i < S; ++i) rhat[((pr * nV + v) * S + i) * 16 + m] = ch[i];
+  if (m == 0) beta[pr * nV + v] = be;
+}
+
+// ------------------------------------------------------------------ tcgen05
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8
+// rows x 16 bytes; lbo = bytes between core matrices along K, sbo = along M/N
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | (uint64_t)((lbo >> 4) & 0x3FFF) << 16 |
+         (uint64_t)((sbo >> 4) & 0x3FFF) << 32 | 1ull << 46;
+}
+
+// instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T >> 3) << 17) | ((uint32_t)(MROWS >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.b32 %0, 1, 0, P1;\n\t}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(phase));
+  return done != 0;
+}
+
+// bounded wait for an mbarrier phase (false: gave up)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try(bar, phase)) return true;
+  return false;
+}
+
+// One tile: output blocks w0 .. w0 + 127 of one pair, all 64 coefficients.
+template <int S>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_conv_tc(const uint4* __restrict__ ahat, const int* __restrict__ alpha, int nA, const uint4* __restrict__ rhat,
+              const int* __restrict__ beta, int nV, int nW, int rl, int mtiles, double* out, int64_t out_pitch,
+              int mode, const double* init, int64_t init_pitch, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + S * 8 * STRIP;
+  uint16_t* sR = (uint16_t*)(sB + S * 8 * BSTRIP);
+  const int64_t pr = blockIdx.x / mtiles;
+  const int w0 = (int)(blockIdx.x % mtiles) * MROWS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, column half
+  const int w = w0 + 32 * q + lane;       // this thread's output block
+  const int* al = alpha + pr * nA;
+  const int* be = beta + pr * nV;
+  const int v_lo = max(0, w0 - nA + 1);
+  const int v_hi = min(nV - 1, w0 + MROWS - 1);
+  // the row's fixed-point unit 2^F: with n steps meeting the row (hr bits),
+  // every contribution |C| 2^E < 2^(47 + 15 - hr) and their sum < 2^62
+  int mx = 2 * ZERO_EXP;
+  const int v_first = max(0, w - nA + 1), v_last = min(nV - 1, w);
+  if (w < nW)
+    for (int v = v_first; v <= v_last; ++v) mx = max(mx, __ldg(al + w - v) + __ldg(be + v));
+  const int hr = 32 - __clz(max(1, v_last - v_first + 1));
+  const int P = 15 - hr;       // C is pre-shifted by P: E <= P
+  const int F = mx - 40 - P;
+  long long acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0;
+
+  const uint32_t bar_addr = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar_addr), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (int v = v_lo; v <= v_hi && !failed; ++v) {
+    const int step = v - v_lo;
+    if (step % V == 0) {
+      // A window: block rows ub .. ub + WROWS - 1 (zero outside a), every
+      // slice and chunk; step v reads rows w0 - v .. w0 - v + 127
+      const int ub = w0 - v - (V - 1);
+      for (int e = threadIdx.x; e < S * 8 * WROWS; e += THREADS) {
+        const int sk = e / WROWS, r = e - sk * WROWS;
+        const int u = ub + r;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (u >= 0 && u < nA) val = __ldg(ahat + (pr * (S * 8) + sk) * (int64_t)nA + u);
+        *(uint4*)(sA + sk * STRIP + r * 16) = val;
+      }
+    }
+    for (int e = threadIdx.x; e < S * 16; e += THREADS) ((uint4*)sR)[e] = __ldg(rhat + (pr * nV + v) * (S * 16) + e);
+    __syncthreads();
+    // B_v[n][k] = b[64 v + n - k] = R[63 - n + k]: chunk (slice j, row n, chunk kc)
+    for (int e = threadIdx.x; e < S * T * 8; e += THREADS) {
+      const int j = e >> 9, n = (e >> 3) & 63, kc = e & 7;
+      const uint16_t* src = sR + j * 128 + (63 - n + 8 * kc);
+      const uint4 val = make_uint4((uint32_t)src[0] | (uint32_t)src[1] << 16, (uint32_t)src[2] | (uint32_t)src[3] << 16,
+                                   (uint32_t)src[4] | (uint32_t)src[5] << 16, (uint32_t)src[6] | (uint32_t)src[7] << 16);
+      *(uint4*)(sB + (j * 8 + kc) * BSTRIP + n * 16) = val;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int roff = (V - 1) - step % V;  // window row of block w0 - v
+      const uint32_t a0 = smem_u32(sA) + 16u * roff, b0 = smem_u32(sB);
+      uint32_t used = 0;
+#pragma unroll 1
+      for (int i = 0; i < S; ++i)
+#pragma unroll 1
+        for (int j = 0; i + j <= S - 1; ++j) {
+          const int g = min(i + j, NACC - 1);
+#pragma unroll
+          for (int ks = 0; ks < T / 16; ++ks) {
+            const uint64_t da = sdesc(a0 + (uint32_t)((i * 8 + 2 * ks) * STRIP), STRIP, 128);
+            const uint64_t db = sdesc(b0 + (uint32_t)((j * 8 + 2 * ks) * BSTRIP), BSTRIP, 128);
+            mma(tmem + (uint32_t)(g * T), da, db, (used >> g) & 1u);
+            used |= 1u << g;
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_addr));
+    }
+    if (!mbar_wait(bar_addr, phase)) s_fail = 1;
+    phase ^= 1;
+    __syncthreads();
+    if (s_fail) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // this row's step: C 2^E units of 2^F, E = alpha + beta - 40 - F <= P
+    const int u = w - v;
+    const int E = (w < nW && u >= 0 && u < nA) ? __ldg(al + u) + __ldg(be + v) - 40 - F : -1000;
+    const int sh = min(63, P - E);
+    const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t r[NACC][16];
+#pragma unroll
+      for (int g = 0; g < NACC; ++g)
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * T + 32 * h + 16 * half), r[g]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        int d[NACC];
+#pragma unroll
+        for (int g = 0; g < NACC; ++g)
+          d[g] = __float_as_int(fmaf(__uint_as_float(r[g][c]), __int_as_float((127 + 7 * g) << 23), 12582912.0f)) -
+                 0x4B400000;
+        const long long C = (long long)d[0] * (1ll << 28) + (long long)d[1] * (1ll << 21) +
+                            (long long)d[2] * (1ll << 14) + (long long)(d[3] * 128 + d[4]);
+        acc[16 * half + c] += ((C << P) + rnd) >> sh;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  }
+  if (failed) {
+    if (threadIdx.x == 0) atomicExch(status, 1);
+    mbar_wait(bar_addr, phase ^ 1);  // the MMAs still in flight, bounded
+  } else if (w < nW) {
+    double* o = out + pr * out_pitch;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const int j = 64 * w + 32 * h + c;
+      if (j < rl) {
+        double val = ldexp((double)acc[c], F);
+        if (mode == 1) val += o[j];
+        else if (mode == 2 && j == 0) val += init[pr * init_pitch];
+        o[j] = val;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct Dims {
+  int nA, nV, nW;
+};
+inline Dims dims(int alen, int blen) {
+  Dims d;
+  d.nA = (int)ceil_div(alen, T);
+  d.nV = (blen + 62) / T + 1;
+  d.nW = (int)ceil_div((int64_t)alen + blen - 1, T);
+  return d;
+}
+inline size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <int S>
+int launch(const double* a, int64_t a_pitch, int alen, const double* b, int64_t b_pitch, int blen, double* out,
+           int64_t out_pitch, int mode, const double* init, int64_t init_pitch, int64_t npairs, void* work,
+           int* status, cudaStream_t st) {
+  const Dims d = dims(alen, blen);
+  unsigned char* p = (unsigned char*)work;
+  uint4* ahat = (uint4*)p;
+  p += r256((size_t)npairs * S * 8 * d.nA * 16);
+  int* alpha = (int*)p;
+  p += r256((size_t)npairs * d.nA * 4);
+  uint4* rhat = (uint4*)p;
+  p += r256((size_t)npairs * d.nV * S * 256);
+  int* beta = (int*)p;
+  const int64_t rows = npairs * d.nA, wins = npairs * d.nV;
+  k_slice_rows<S><<<(unsigned)ceil_div(rows * 8, 256), 256, 0, st>>>(a, a_pitch, alen, d.nA, npairs, ahat, alpha);
+  k_slice_windows<S><<<(unsigned)ceil_div(wins * 16, 256), 256, 0, st>>>(b, b_pitch, blen, d.nV, npairs, rhat, beta);
+  const int smem = smem_bytes(S) > SMEM_MIN ? smem_bytes(S) : SMEM_MIN;
+  if (cudaFuncSetAttribute(k_conv_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return FP_E_CUDA;
+  const int mtiles = (int)ceil_div(d.nW, MROWS);
+  k_conv_tc<S><<<(unsigned)(npairs * mtiles), THREADS, smem, st>>>(ahat, alpha, d.nA, rhat, beta, d.nV, d.nW,
+                                                                  alen + blen - 1, mtiles, out, out_pitch, mode,
+                                                                  init, init_pitch, status);
+  return cudaGetLastError() == cudaSuccess ? FP_OK : FP_E_CUDA;
+}
+
+}  // namespace tc
+
+// Work space of conv_tc for these lengths (bytes, 256-byte granules).
+size_t conv_tc_workspace(int alen, int blen, int64_t npairs, int slices) {
+  const tc::Dims d = tc::dims(alen, blen);
+  return tc::r256((size_t)npairs * slices * 8 * d.nA * 16) + tc::r256((size_t)npairs * d.nA * 4) +
+         tc::r256((size_t)npairs * d.nV * slices * 256) + tc::r256((size_t)npairs * d.nV * 4);
+}
+
+// out[pair][0 .. alen + blen - 1) = a[pair] * b[pair] (mode 0), added into out
+// (mode 1), or written with init[pair] added at degree 0 (mode 2); `out` may
+// be `a` or `b` (both are sliced before the product is written).  status: a
+// device int set to 1 if a tile gave up waiting for its tensor-core work.
+int conv_tc(const double* a, int64_t a_pitch, int alen, const double* b, int64_t b_pitch, int blen, double* out,
+            int64_t out_pitch, int mode, const double* init, int64_t init_pitch, int64_t npairs, void* work,
+            int* status, int slices, cudaStream_t st) {
+  if (alen < 1 || blen < 1 || npairs < 1) return FP_E_BAD_VALUE;
+  switch (slices) {
+    case 6: return tc::launch<6>(a, a_pitch, alen, b, b_pitch, blen, out, out_pitch, mode, init, init_pitch, npairs, work, status, st);
+    case 7: return tc::launch<7>(a, a_pitch, alen, b, b_pitch, blen, out, out_pitch, mode, init, init_pitch, npairs, work, status, st);
+    case 8: return tc::launch<8>(a, a_pitch, alen, b, b_pitch, blen, out, out_pitch, mode, init, init_pitch, npairs, work, status, st);
+  }
+  return FP_E_BAD_VALUE;
+}
+
+}  // namespace fp

@@ -68,3 +68,23 @@ def check_any(dtype, e, c, pts, scheme, got):
         check_modp(e, c, pts, got)
     else:
         check_iv64(e, c, pts[0], pts[1], scheme, got)
+
+
+def local_scale(absw, radius=128):
+    """max of absw over [j - radius, j + radius]: the scale of the largest
+    block products that meet at coefficient j in the tensor-core FP64
+    composition (64-coefficient blocks: a block product lands in its own
+    output block or one of the two beside it)."""
+    from scipy.ndimage import maximum_filter1d
+    return maximum_filter1d(np.asarray(absw, dtype=np.float64), size=2 * radius + 1, mode="constant", cval=0.0)
+
+
+def check_compose_f64(got, want, absw, K, local):
+    """FP64 composition bar: |got - want| <= K u s_j with s_j = (|p| o |q|)_j
+    (componentwise: the direct convolution) or its local maximum
+    (local_scale: the tensor-core products, blockwise accurate)."""
+    scale = local_scale(absw) if local else absw
+    err = np.abs(got - want)
+    ok = err <= K * U * scale + 1e-300
+    assert ok.all(), (int(np.argmin(ok)), float((err / np.maximum(scale, 1e-300)).max()))
+    return err

@@ -245,13 +245,13 @@ def test_compose_workspace_is_affine_in_pairs(dtype, scheme):
     degp, degq = 128, 64  # products up to length 16385: four-step transforms
     e = W.dense_univariate_exps(degp + 1)
     t = fpl.fp_compile_host(e, np.ones(degp + 1, dtype=np.uint64 if modp else np.float64), scheme, modp=modp)
-    ws = [fpl.fp_compose_workspace(t, dtype, degq, n) for n in (32, 64, 96)]
+    ws = [fpl.fp_compose_workspace(t, dtype, degq, n) for n in (64, 128, 192)]
     assert ws[0] < ws[1] < ws[2]
     assert ws[1] - ws[0] == ws[2] - ws[1]
-    shared = fpl.fp_compose_workspace(t, dtype, degq, 64, per_pair_coeffs=False)
+    shared = fpl.fp_compose_workspace(t, dtype, degq, 128, per_pair_coeffs=False)
     assert shared - ws[1] == ((degp + 1) * 8 + 255) // 256 * 256
     # at least the slots, the powers and the two product buffers per pair
-    assert ws[1] - ws[0] >= 32 * 8 * (degp * degq + 1)
+    assert ws[1] - ws[0] >= 64 * 8 * (degp * degq + 1)
     assert fpl.fp_compose_workspace(t, dtype, degq, 0) == 0
     with pytest.raises(fpl.FastPolyError):
         fpl.fp_compose_workspace(t, "f64" if modp else "modp", degq, 32)

@@ -7,7 +7,9 @@ plus a full schoolbook check of sampled pairs.
 FP64: componentwise, |gpu - oracle|_i <= K u (|p| o |q|)_i with
 K = 8 (deg p (deg q + 1) + deg p + 2): both the GPU walk and the oracle's
 plain sum accumulate at most deg p (deg q + 1) + deg p roundings per
-coefficient, each relative to the absolute-value computation.
+coefficient, each relative to the absolute-value computation (products
+shorter than 256: direct convolution); at the full size, where the products
+run on the tensor cores, blockwise (tests/checks.py: check_compose_f64).
 """
 import numpy as np
 import pytest
@@ -15,6 +17,7 @@ import pytest
 import oracle as O
 import workloads as W
 import paper_1307_5655_gb300 as fpl
+from checks import check_compose_f64
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
@@ -154,8 +157,9 @@ def _oracle_f64_pairs(pc, qc, js):
 @pytest.mark.parametrize("scheme", ["E", "B"])
 def test_f64_full_size_sampled(scheme):
     """The benchmark's FP64 composition, 4096 pairs of deg p 512 and deg q 64,
-    in one call: 16 sampled pairs componentwise against the oracle within
-    K u (|p| o |q|)_i, K = 8 (deg p (deg q + 1) + deg p + 2)."""
+    in one call (products on the tensor cores): 16 sampled pairs against the
+    oracle within K u max((|p| o |q|) over i +- 128), K = 8 (deg p (deg q + 1)
+    + deg p + 2) -- the blockwise bar of the tensor-core products."""
     import torch
     npairs, degp, degq = 4096, 512, 64
     pc, qc = W.composition_case(npairs, degp, degq, 4000, "f64")
@@ -167,8 +171,7 @@ def test_f64_full_size_sampled(scheme):
     del out
     K = 8 * (degp * (degq + 1) + degp + 2)
     for row, (want, absw), j in zip(got, _oracle_f64_pairs(pc, qc, js), js):
-        err = np.abs(row - want)
-        assert np.all(err <= K * U * absw + 1e-300), (j, (err / np.maximum(absw, 1e-300)).max())
+        check_compose_f64(row, want, absw, K, local=True)
 
 
 def test_compose_rejects_bad_input():
