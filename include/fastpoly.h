@@ -325,13 +325,16 @@ void fp_server_destroy(fp_server* s);
  *            FP_F64: products whose operands both have at least 256
  *            coefficients run on the tensor cores -- each operand cut into
  *            blocks of 64 coefficients with an exponent each, every value
- *            split into 8 signed 7-bit slices (bf16), the slice products
+ *            split into 7 signed 7-bit slices (bf16), the slice products
  *            summed exactly in FP32 and recombined in 64-bit fixed point per
  *            block of the result; shorter products by direct convolution.
- *            Error per product coefficient: about 2^-52 of the largest
- *            block products meeting there (2^-45 with 7 slices); the tests
- *            hold the result componentwise to the bound of the plain FP64
- *            walk run on |p|, |q| (fp_set_compose_f64 changes the settings).
+ *            The tensor-core products are accurate blockwise: the error at a
+ *            coefficient is about 2^-45 (8 slices: 2^-52) of the largest
+ *            block products meeting there, not of the coefficient itself (a
+ *            coefficient far below its 64-coefficient neighbourhood, as in
+ *            the steep tails of q^e, keeps only that absolute accuracy); the
+ *            direct convolution (fp_set_compose_f64 with min_len < 0) is
+ *            componentwise: |error|_i <= gamma (|p| o |q|)_i.
  *   pcoeffs  device, [npairs][nterms] in the term order given to fp_compile,
  *            or NULL to use the tree's own coefficients for every pair.  Terms
  *            whose compile-time coefficient was zero are not in the tree and
@@ -352,7 +355,7 @@ int fp_compose(const fp_tree* p, fp_dtype dtype, const void* pcoeffs, const void
 
 /* fp_set_compose_f64 -- process-wide settings of FP64 composition products
  * (no counterpart in the paper): slices per operand on the tensor cores (6,
- * 7 or 8; 0 = 8) and the shortest operand length sent to them (0 = 256;
+ * 7 or 8; 0 = 7) and the shortest operand length sent to them (0 = 256;
  * negative: never, every product by direct convolution).  Calls already
  * enqueued keep the settings they started with.  Errors: FP_E_BAD_VALUE. */
 int fp_set_compose_f64(int slices, int min_len);

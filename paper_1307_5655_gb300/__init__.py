@@ -412,7 +412,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 def fp_set_compose_f64(slices=0, min_len=0):
     """Process-wide FP64 composition settings: tensor-core slices per operand
-    (6, 7, 8; 0 = 8) and the shortest operand sent to the tensor cores
+    (6, 7, 8; 0 = 7) and the shortest operand sent to the tensor cores
     (0 = 256; negative = direct convolution only)."""
     _check(_lib.fp_set_compose_f64(slices, min_len), "fp_set_compose_f64")
 

@@ -35,7 +35,7 @@ int conv_tc(const double* a, int64_t a_pitch, int alen, const double* b, int64_t
 
 // FP64 products: slices per operand on the tensor cores, and the shortest
 // operand length that goes to them (shorter ones: direct convolution)
-static std::atomic<int> g_f64_slices{8};
+static std::atomic<int> g_f64_slices{7};
 static std::atomic<int> g_f64_tc_min{256};
 
 namespace {
@@ -894,7 +894,7 @@ int compose_device(const fp_tree* t, fp_dtype dtype, const void* pcoeffs, const 
 
 int set_compose_f64(int slices, int min_len) {
   if (slices != 0 && (slices < 6 || slices > 8)) return FP_E_BAD_VALUE;
-  g_f64_slices.store(slices ? slices : 8);
+  g_f64_slices.store(slices ? slices : 7);
   g_f64_tc_min.store(min_len == 0 ? 256 : (min_len < 0 ? 0 : min_len));
   return FP_OK;
 }

@@ -10,7 +10,15 @@
 //     out[64 w + r] = sum_v sum_s a[64 (w - v) + s] b[64 v + r - s],
 // so for every v one matrix product D[w][r] = sum_s A[w - v][s] B_v[r][s]
 // with A the blocks of a as rows (a window of rows shifted by one per step)
-// and B_v the 64 x 64 Toeplitz matrix of the window, built in shared memory.
+// and B_v the 64 x 64 Toeplitz matrix of the window.  With the block stored
+// reversed (k = 63 - s) the second operand is b[64 v - 63 + r + k], a Hankel
+// matrix: its 8-element core rows are 16-byte lines W[8 m + rho .. + 7] of
+// the window W = b[64 v - 63 ..], m = row group + column group, rho = row in
+// the group.  Eight copies of the window, shifted by rho elements and
+// interleaved line by line (line m * 8 + rho), are therefore that operand as
+// it stands: a K-major descriptor with both core-matrix strides 128 bytes
+// reads it (2 KB per slice instead of an 8 KB Toeplitz tile), and the next
+// step's copies are built while the tensor cores run this step's.
 //
 // Slices.  x in a block of bound 2^alpha is rounded to the integer
 // X = round(x 2^(6 - alpha + 7 (S - 1))) (|X| <= 2^(7 S - 1)) and written in
@@ -25,8 +33,10 @@
 //
 // Recombination.  Each step reads the five accumulators (tcgen05.ld), turns
 // each into its integer with one FMA against 1.5 2^23 (exact for |D| < 2^22),
-// and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 + D_4 (|C| < 2^49), so
-// that the step contributes C 2^(alpha_{w-v} + beta_v - 40).  Each output row
+// and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 (|C| < 2^47) and D_4:
+// the step contributes (C + D_4) 2^(alpha_{w-v} + beta_v - 40).  The exact
+// groups are committed first and read out while the tensor cores run the
+// combined group; the next window of b is loaded meanwhile.  Each output row
 // keeps a 64-bit fixed-point accumulator with unit 2^F_w, F_w = max over the
 // row's steps of alpha + beta - 40 - (15 - hr), hr the bits of the row's step
 // count: every contribution stays below 2^(62 - hr) units and their sum
@@ -52,14 +62,14 @@ constexpr int V = 16;                // steps per load of the A window
 constexpr int MROWS = 128;           // output blocks per tile (MMA M, TMEM lanes)
 constexpr int WROWS = MROWS + V;     // rows of the A window in shared memory
 constexpr int STRIP = WROWS * 16;    // bytes of one (slice, 8-column chunk) strip of A
-constexpr int BSTRIP = T * 16;       // bytes of one (slice, 8-column chunk) strip of B_v
+constexpr int HANKEL = 16 * 8 * 16;  // bytes of one slice's shifted window copies (16 lines x 8 shifts)
 constexpr int NACC = 5;              // TMEM accumulators of 64 columns
 constexpr int THREADS = 256;
 constexpr int ZERO_EXP = -100000;    // exponent bound of an all-zero block
 constexpr int TMEM_COLS = 512;       // power of two >= NACC * 64
 constexpr int SMEM_MIN = 120 * 1024; // at least half the SM: one tile per SM holds the TMEM
 
-__host__ __device__ constexpr int smem_bytes(int S) { return S * 8 * STRIP + S * 8 * BSTRIP + S * 128 * 2; }
+__host__ __device__ constexpr int smem_bytes(int S) { return S * 8 * STRIP + 2 * S * HANKEL + S * 128 * 2; }
 
 // ------------------------------------------------------------------ slicing
 // smallest alpha with |x| < 2^alpha (ZERO_EXP for x = 0)
@@ -117,8 +127,9 @@ __device__ __forceinline__ void slice8(const double* x, int alpha, uint4* chunk)
   for (int i = 0; i < S; ++i) chunk[i] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
 
-// Blocks of a as rows: ahat[pair][slice][chunk][u] (16 bytes: coefficients
-// 64 u + 8 chunk .. + 7), alpha[pair][u].  Eight threads per block row.
+// Blocks of a as rows, each reversed: ahat[pair][slice][chunk][u] (16 bytes:
+// coefficients 64 u + 63 - 8 chunk down to 64 u + 56 - 8 chunk), alpha[pair][u].
+// Eight threads per block row.
 template <int S>
 __global__ void k_slice_rows(const double* a, int64_t a_pitch, int alen, int nA, int64_t npairs, uint4* ahat,
                              int* alpha) {
@@ -140,16 +151,19 @@ __global__ void k_slice_rows(const double* a, int64_t a_pitch, int alen, int nA,
   al = max(al, __shfl_xor_sync(0xffffffffu, al, 2));
   al = max(al, __shfl_xor_sync(0xffffffffu, al, 4));
   if (!valid) return;
-  uint4 ch[S];
-  slice8<S>(x, al, ch);
+  double xr[8];
 #pragma unroll
-  for (int i = 0; i < S; ++i) ahat[((pr * S + i) * 8 + t) * nA + u] = ch[i];
+  for (int e = 0; e < 8; ++e) xr[e] = x[7 - e];
+  uint4 ch[S];
+  slice8<S>(xr, al, ch);
+#pragma unroll
+  for (int i = 0; i < S; ++i) ahat[((pr * S + i) * 8 + (7 - t)) * nA + u] = ch[i];
   if (t == 0) alpha[pr * nA + u] = al;
 }
 
-// Windows of b reversed: rhat[pair][v][slice][t'] (bf16) holds
-// b[64 v + 63 - t'] for t' < 127 (0 at t' = 127 and outside b), beta[pair][v].
-// Sixteen threads per window, eight entries each.
+// Windows of b: rhat[pair][v][slice][t] (bf16) holds b[64 v - 63 + t] for
+// t < 127 (0 at t = 127 and outside b), beta[pair][v].  Sixteen threads per
+// window, eight entries each.
 template <int S>
 __global__ void k_slice_windows(const double* b, int64_t b_pitch, int blen, int nV, int64_t npairs, uint4* rhat,
                                 int* beta) {
@@ -164,7 +178,7 @@ __global__ void k_slice_windows(const double* b, int64_t b_pitch, int blen, int 
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int tp = 8 * m + e;
-    const int idx = 64 * v + 63 - tp;
+    const int idx = 64 * v - 63 + tp;
     x[e] = (valid && tp < 127 && idx >= 0 && idx < blen) ? b[pr * b_pitch + idx] : 0.0;
     be = max(be, exp_bound(x[e]));
   }
@@ -193,11 +207,72 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 // instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = 64
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T >> 3) << 17) | ((uint32_t)(MROWS >> 4) << 24);
 
+// COL: what the MMA does with the A collector buffer -- 0 read A from shared
+// memory and discard it, 1 read and keep it (fill), 2 reuse the kept A (use),
+// 3 reuse it for the last time (lastuse)
+template <int COL>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+  if constexpr (COL == 0)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+  else if constexpr (COL == 1)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+  else if constexpr (COL == 2)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+  else
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+// The MMAs of one step for the exact groups (PASS 0: i + j < NACC - 1) or
+// the combined group (PASS 1): slice i of the A window times slice j of B_v
+// over K = 64 (four MMAs of K = 16), into accumulator min(i + j, NACC - 1);
+// the first MMA into an accumulator overwrites it.  For each slice i and
+// K step, the A tile is read from shared memory once and kept in the
+// collector buffer for every slice j it meets.  The start-address field of a
+// descriptor holds addr >> 4 (14 bits, shared memory < 256 KB): adding
+// offset >> 4 moves it.
+template <int S, int PASS, int I, int KS, int J, int FIRST>
+__device__ __forceinline__ void issue_j(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t& used) {
+  if constexpr (J < S) {
+    constexpr bool keep = I + J <= S - 1 && ((I + J < NACC - 1) == (PASS == 0));
+    if constexpr (keep) {
+      // the last j this (i, K step) meets in this pass
+      constexpr int JLAST = PASS == 0 ? (NACC - 2 - I) : (S - 1 - I);
+      constexpr int COL = (FIRST && J == JLAST) ? 0 : (FIRST ? 1 : (J == JLAST ? 3 : 2));
+      constexpr int g = I + J < NACC - 1 ? I + J : NACC - 1;
+      mma<COL>(tmem + (uint32_t)(g * T), dA + (uint64_t)(((I * 8 + 2 * KS) * STRIP) >> 4),
+               dB + (uint64_t)((J * HANKEL + 2 * KS * 128) >> 4), (used >> g) & 1u);
+      used |= 1u << g;
+      issue_j<S, PASS, I, KS, J + 1, 0>(tmem, dA, dB, used);
+    } else {
+      issue_j<S, PASS, I, KS, J + 1, FIRST>(tmem, dA, dB, used);
+    }
+  }
+}
+
+template <int S, int PASS, int I, int KS>
+__device__ __forceinline__ void issue_iks(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t& used) {
+  if constexpr (I < S) {
+    if constexpr (KS < T / 16) {
+      issue_j<S, PASS, I, KS, 0, 1>(tmem, dA, dB, used);
+      issue_iks<S, PASS, I, KS + 1>(tmem, dA, dB, used);
+    } else {
+      issue_iks<S, PASS, I + 1, 0>(tmem, dA, dB, used);
+    }
+  }
+}
+
+template <int S, int PASS>
+__device__ __forceinline__ void issue_mmas(uint32_t tmem, uint64_t dA, uint64_t dB) {
+  uint32_t used = 0;
+  issue_iks<S, PASS, 0, 0>(tmem, dA, dB, used);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
@@ -231,12 +306,12 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int* __restrict__ beta, int nV, int nW, int rl, int mtiles, double* out, int64_t out_pitch,
               int mode, const double* init, int64_t init_pitch, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + S * 8 * STRIP;
-  uint16_t* sR = (uint16_t*)(sB + S * 8 * BSTRIP);
+  unsigned char* sA = smem;                                // A window: S x 8 strips
+  unsigned char* sH = smem + S * 8 * STRIP;                // Hankel operand: 2 buffers x S slices
+  uint32_t* sW = (uint32_t*)(sH + 2 * S * HANKEL);         // staged window: S x 64 words
   const int64_t pr = blockIdx.x / mtiles;
   const int w0 = (int)(blockIdx.x % mtiles) * MROWS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -259,10 +334,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = 0;
 
-  const uint32_t bar_addr = smem_u32(&bar);
+  const uint32_t barx = smem_u32(&bar[0]), bary = smem_u32(&bar[1]);
   if (threadIdx.x == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar_addr), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(barx), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bary), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -270,6 +346,28 @@ __global__ void __launch_bounds__(THREADS, 1)
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
+  // W_v of every slice into sW
+  auto stage_window = [&](int v) {
+    if (threadIdx.x < S * 16) ((uint4*)sW)[threadIdx.x] = __ldg(rhat + (pr * nV + v) * (S * 16) + threadIdx.x);
+  };
+  // the shifted copies of sW into Hankel buffer hb: line m * 8 + rho of slice
+  // j holds W_j[8 m + rho .. + 7] (m < 15: the MMAs read row group + column
+  // group <= 14); lines in order, so eight threads store 128 consecutive bytes
+  auto build_hankel = [&](int hb) {
+    unsigned char* base = sH + hb * (S * HANKEL);
+    for (int e = threadIdx.x; e < S * 120; e += THREADS) {
+      const int j = e / 120, line = e - j * 120, m = line >> 3, rho = line & 7;
+      const uint32_t* src = sW + j * 64 + 4 * m + (rho >> 1);
+      const uint32_t sft = 16u * (rho & 1);
+      const uint32_t x0 = src[0], x1 = src[1], x2 = src[2], x3 = src[3], x4 = src[4];
+      *(uint4*)(base + j * HANKEL + line * 16) = make_uint4(__funnelshift_r(x0, x1, sft), __funnelshift_r(x1, x2, sft),
+                                                            __funnelshift_r(x2, x3, sft), __funnelshift_r(x3, x4, sft));
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  };
+  if (v_lo <= v_hi) stage_window(v_lo);
+  __syncthreads();
+  if (v_lo <= v_hi) build_hankel(v_lo & 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -277,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t phase = 0;
   bool failed = false;
 
-  for (int v = v_lo; v <= v_hi && !failed; ++v) {
+  for (int v = v_lo; v <= v_hi; ++v) {
     const int step = v - v_lo;
     if (step % V == 0) {
       // A window: block rows ub .. ub + WROWS - 1 (zero outside a), every
@@ -290,76 +388,80 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (u >= 0 && u < nA) val = __ldg(ahat + (pr * (S * 8) + sk) * (int64_t)nA + u);
         *(uint4*)(sA + sk * STRIP + r * 16) = val;
       }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
     }
-    for (int e = threadIdx.x; e < S * 16; e += THREADS) ((uint4*)sR)[e] = __ldg(rhat + (pr * nV + v) * (S * 16) + e);
-    __syncthreads();
-    // B_v[n][k] = b[64 v + n - k] = R[63 - n + k]: chunk (slice j, row n, chunk kc)
-    for (int e = threadIdx.x; e < S * T * 8; e += THREADS) {
-      const int j = e >> 9, n = (e >> 3) & 63, kc = e & 7;
-      const uint16_t* src = sR + j * 128 + (63 - n + 8 * kc);
-      const uint4 val = make_uint4((uint32_t)src[0] | (uint32_t)src[1] << 16, (uint32_t)src[2] | (uint32_t)src[3] << 16,
-                                   (uint32_t)src[4] | (uint32_t)src[5] << 16, (uint32_t)src[6] | (uint32_t)src[7] << 16);
-      *(uint4*)(sB + (j * 8 + kc) * BSTRIP + n * 16) = val;
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
     if (threadIdx.x == 0) {
+      // the exact groups (i + j <= 3) first, committed to barx, then the
+      // combined group to bary: the exact accumulators are read out while
+      // the tensor cores run the rest.  Fully unrolled: every operand offset
+      // and accumulate flag is a constant added to two base descriptors.
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int roff = (V - 1) - step % V;  // window row of block w0 - v
-      const uint32_t a0 = smem_u32(sA) + 16u * roff, b0 = smem_u32(sB);
-      uint32_t used = 0;
-#pragma unroll 1
-      for (int i = 0; i < S; ++i)
-#pragma unroll 1
-        for (int j = 0; i + j <= S - 1; ++j) {
-          const int g = min(i + j, NACC - 1);
-#pragma unroll
-          for (int ks = 0; ks < T / 16; ++ks) {
-            const uint64_t da = sdesc(a0 + (uint32_t)((i * 8 + 2 * ks) * STRIP), STRIP, 128);
-            const uint64_t db = sdesc(b0 + (uint32_t)((j * 8 + 2 * ks) * BSTRIP), BSTRIP, 128);
-            mma(tmem + (uint32_t)(g * T), da, db, (used >> g) & 1u);
-            used |= 1u << g;
-          }
-        }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_addr));
+      const uint64_t dA = sdesc(smem_u32(sA) + 16u * roff, STRIP, 128);
+      const uint64_t dB = sdesc(smem_u32(sH) + (uint32_t)((v & 1) * S * HANKEL), 128, 128);
+      issue_mmas<S, 0>(tmem, dA, dB);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barx));
+      issue_mmas<S, 1>(tmem, dA, dB);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bary));
     }
-    if (!mbar_wait(bar_addr, phase)) s_fail = 1;
-    phase ^= 1;
+    // the next step's operand, built while the tensor cores work (its buffer
+    // was last read by the previous step's MMAs, which have completed)
+    if (v < v_hi) stage_window(v + 1);
     __syncthreads();
-    if (s_fail) {
-      failed = true;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (v < v_hi) build_hankel((v + 1) & 1);
     // this row's step: C 2^E units of 2^F, E = alpha + beta - 40 - F <= P
     const int u = w - v;
     const int E = (w < nW && u >= 0 && u < nA) ? __ldg(al + u) + __ldg(be + v) - 40 - F : -1000;
     const int sh = min(63, P - E);
     const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0;
+    if (!mbar_wait(barx, phase)) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      uint32_t r[NACC][16];
+      uint32_t r[NACC - 1][16];
 #pragma unroll
-      for (int g = 0; g < NACC; ++g)
+      for (int g = 0; g < NACC - 1; ++g)
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * T + 32 * h + 16 * half), r[g]);
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        int d[NACC];
+        int d[NACC - 1];
 #pragma unroll
-        for (int g = 0; g < NACC; ++g)
+        for (int g = 0; g < NACC - 1; ++g)
           d[g] = __float_as_int(fmaf(__uint_as_float(r[g][c]), __int_as_float((127 + 7 * g) << 23), 12582912.0f)) -
                  0x4B400000;
         const long long C = (long long)d[0] * (1ll << 28) + (long long)d[1] * (1ll << 21) +
-                            (long long)d[2] * (1ll << 14) + (long long)(d[3] * 128 + d[4]);
+                            (long long)d[2] * (1ll << 14) + (long long)d[3] * 128;
         acc[16 * half + c] += ((C << P) + rnd) >> sh;
       }
     }
+    if (!mbar_wait(bary, phase)) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    {
+      uint32_t r[2][16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((NACC - 1) * T + 32 * h), r[0]);
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((NACC - 1) * T + 32 * h + 16), r[1]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const long long d = __float_as_int(fmaf(__uint_as_float(r[c >> 4][c & 15]),
+                                                __int_as_float((127 + 7 * (NACC - 1)) << 23), 12582912.0f)) -
+                            0x4B400000;
+        acc[c] += ((d << P) + rnd) >> sh;
+      }
+    }
+    phase ^= 1;
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (s_fail) {
+      failed = true;
+      break;
+    }
   }
   if (failed) {
     if (threadIdx.x == 0) atomicExch(status, 1);
-    mbar_wait(bar_addr, phase ^ 1);  // the MMAs still in flight, bounded
+    mbar_wait(bary, phase ^ 1);  // the MMAs still in flight, bounded
   } else if (w < nW) {
     double* o = out + pr * out_pitch;
 #pragma unroll
