@@ -468,7 +468,17 @@ def _timed(fn, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
-def compose_work(t, degq, modp):
+def measured_bf16_tflops():
+    """Dense bf16 peak of the GB300s (MEASURED_PEAKS.json, burst) or
+    the recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def compose_work(t, degq, modp, tc_min=256):
     """Algorithmic operations of one batched composition per pair, following
     the walk's products as the library sizes them.  MODP: (butterflies,
     multiplications) -- a transform of length n is (n/2) log2 n radix-2
@@ -478,8 +488,9 @@ def compose_work(t, degq, modp):
     leaf scalings are single
     multiplications (the inverse transform's 1/n rides on the inverse
     four-step twiddles, or on the cached transform of q^d for n <= 4096,
-    scaled once when cached).  FP64: (0, multiply-adds of the direct
-    convolutions)."""
+    scaled once when cached).  FP64: (multiply-adds of the products that run
+    on the tensor cores -- both operands at least tc_min long -- , multiply-
+    adds of the direct convolutions)."""
     import math
     ex = t.export()
     n_nodes = len(ex["parent"])
@@ -505,6 +516,7 @@ def compose_work(t, degq, modp):
                 stack.append(m)
     cached = set()
     bfly, mul = 0, 0
+    tcmac = 0
 
     def ntt(n, upper_zero=False):
         # upper_zero: a zero-padded operand (length <= n/2): the first
@@ -519,9 +531,13 @@ def compose_work(t, degq, modp):
 
     def product(alen, blen, bkey):
         nonlocal mul
+        nonlocal tcmac
         rl = alen + blen - 1
         if not modp:
-            mul += alen * blen
+            if alen >= tc_min and blen >= tc_min:
+                tcmac += alen * blen
+            else:
+                mul += alen * blen
             return
         n = 1 << max(0, (rl - 1).bit_length())
         ntt(n, 2 * alen <= n)                # forward transform of A
@@ -546,7 +562,7 @@ def compose_work(t, degq, modp):
             product(int(degval[i]) + 1, qlen, int(pd[i]))
         elif modp:
             mul += qlen                      # leaf: c * q^d
-    return bfly, mul
+    return (bfly, mul) if modp else (tcmac, mul)
 
 
 def measure_compose(fpl, W, npairs, dtypes, schemes, steps, warmup, rates):
@@ -580,10 +596,23 @@ def measure_compose(fpl, W, npairs, dtypes, schemes, steps, warmup, rates):
                         "basis": "measured (fp_measure_rates)"}
                 roof.update(modp_issue_roofline(bfly * npairs, mul * npairs, rates))
             else:
-                roof_ms = npairs * mul / FP64_DFMA_GPS / 1e6
-                roof = {"unit": "ms", "multiply_adds": mul * npairs, "dfma_rate_G_per_s": FP64_DFMA_GPS,
-                        "basis": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (the schoolbook convolution's "
-                                 "multiply-adds at the FP64 rate: what the tensor path replaces)"}
+                # the tensor-core products: each kept slice pair is one bf16
+                # multiply-add per coefficient pair (S (S + 1) / 2 pairs of S =
+                # 7 slices); the short products: direct FP64 multiply-adds
+                tcmac, dmac = bfly, mul
+                pairs = 7 * 8 // 2
+                peak, basis = measured_bf16_tflops()
+                tc_ms = npairs * tcmac * pairs * 2 / (peak * 1e12) * 1e3
+                dfma_ms = npairs * dmac / FP64_DFMA_GPS / 1e6
+                roof_ms = tc_ms + dfma_ms
+                roof = {"unit": "ms", "bound": "tensor (bf16) + fp64 issue",
+                        "tensor_multiply_adds": tcmac * npairs, "slice_pairs": pairs,
+                        "bf16_peak_TFLOP_s": peak, "peak_basis": basis, "time_tensor": tc_ms,
+                        "direct_multiply_adds": dmac * npairs, "dfma_rate_G_per_s": FP64_DFMA_GPS,
+                        "time_direct": dfma_ms,
+                        "direct_convolution_time_roof": npairs * (tcmac + dmac) / FP64_DFMA_GPS / 1e6,
+                        "basis": "useful slice products (coefficient pairs x kept slice pairs) at the bf16 peak, "
+                                 "plus the short products' FP64 multiply-adds at 2 DFMA/clk/SM x 152 x 2070 MHz"}
             roof.update({"time_roof": roof_ms, "time_measured": ms, "frac": roof_ms / ms})
             res["%s/%s" % (dt, s)] = {"ms": ms, "compositions_per_s": npairs / (ms * 1e-3),
                                       "output_coeffs_per_s": npairs * (degp * degq + 1) / (ms * 1e-3),
