@@ -80,6 +80,35 @@ def exact_horner_univariate(coeffs_by_degree, x):
     return to_fraction(r), to_fraction(ar)
 
 
+def horner_enclosure(coeffs_by_degree, x, frac_bits=1200):
+    """Fixed-point Horner with a rigorous error bound, for |x| <= 1: returns
+    integers (V, A, E) with |p(x) - V 2^-F| <= E 2^-F and |sum |c_i||x|^i -
+    A 2^-F| <= E 2^-F, F = frac_bits.  Every coefficient must be a multiple
+    of 2^-F (doubles of exponent >= -F + 52).  Each step multiplies by x and
+    rounds down to the unit 2^-F (an error in [0, 1) unit) and adds the
+    coefficient exactly; |x| <= 1 keeps the earlier errors from growing, so
+    after k steps E = k.  Linear in k per step (numbers of about F bits),
+    where the exact rational Horner's numbers grow by 53 bits per step."""
+    xm, xk = _split(x)
+    assert abs(float(x)) <= 1.0
+    F = frac_bits
+    axm = abs(xm)
+
+    def times_x(v, m):
+        t = v * m
+        return t << xk if xk >= 0 else t >> -xk  # floor
+
+    V, A, k = 0, 0, 0
+    for c in reversed(list(coeffs_by_degree)):
+        cm, ck = _split(c)
+        assert cm == 0 or F + ck >= 0, "coefficient finer than the fixed-point unit"
+        C = cm << (F + ck) if cm else 0
+        V = times_x(V, xm) + C
+        A = times_x(A, axm) + abs(C)
+        k += 1
+    return V, A, k
+
+
 def modp_value(exps, coeffs, point):
     """p(point) mod 2^64 - 2^32 + 1 with Python integers."""
     s = 0

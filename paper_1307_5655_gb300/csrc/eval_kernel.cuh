@@ -716,14 +716,16 @@ __device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]
   }
 }
 
-template <class A, int PPT, int SCHEME>
+// TPB: threads per block (the stride of the per-point table); kTPB unless the
+// launch chose narrower blocks for a small grid
+template <class A, int PPT, int SCHEME, int TPB = kTPB>
 __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int64_t base, unsigned char* smem_raw) {
   using V = typename A::val;
   using W = typename A::pw;
   using C = typename A::coef;
   static_assert(sizeof(V) == sizeof(W), "powers and slots share one table");
   W* pw = reinterpret_cast<W*>(smem_raw);                        // [entries][PPT][TPB]
-  V* acc = reinterpret_cast<V*>(smem_raw) + (size_t)o.nlive * PPT * kTPB;  // slots above the walk's powers
+  V* acc = reinterpret_cast<V*>(smem_raw) + (size_t)o.nlive * PPT * TPB;  // slots above the walk's powers
   const int tid = threadIdx.x;
 
   for (int k = 0; k < o.nprog; ++k) {
@@ -731,12 +733,12 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     const uint32_t op = e.x & 3u, a1 = (e.x >> 2) & 0x7FFFu, a2 = e.x >> 17, dst = e.y;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-      const int64_t idx = base + p * kTPB + tid;
+      const int64_t idx = base + p * TPB + tid;
       W r;
       if (op == kPowLoad) r = idx < g.npts ? A::load_point(g.points, (int)a1, idx, g.npts) : A::dummy_point();
-      else if (op == kPowSq) r = A::square(pw[(a1 * PPT + p) * kTPB + tid]);
-      else r = A::mulx(pw[(a1 * PPT + p) * kTPB + tid], pw[(a2 * PPT + p) * kTPB + tid]);
-      pw[(dst * PPT + p) * kTPB + tid] = r;
+      else if (op == kPowSq) r = A::square(pw[(a1 * PPT + p) * TPB + tid]);
+      else r = A::mulx(pw[(a1 * PPT + p) * TPB + tid], pw[(a2 * PPT + p) * TPB + tid]);
+      pw[(dst * PPT + p) * TPB + tid] = r;
     }
   }
 
@@ -750,7 +752,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
       if (block_uses_power<SCHEME>(d)) {
         const int q = o.pid_pow[d] < 0 ? 0 : o.pid_pow[d];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) xp[p][d] = pw[(q * PPT + p) * kTPB + tid];
+        for (int p = 0; p < PPT; ++p) xp[p][d] = pw[(q * PPT + p) * TPB + tid];
       }
     }
   }
@@ -770,17 +772,17 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     V v[PPT];
     if (kind == kOpNode) {
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(a) : acc[(S * PPT + p) * kTPB + tid];
+      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(a) : acc[(S * PPT + p) * TPB + tid];
     } else if (kind == kOpChain) {
       const int64_t j0 = (int64_t)h.z;
       const C* cs = st + off;  // node j0 + t uses cs[t]
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(__ldg(cs)) : acc[(S * PPT + p) * kTPB + tid];
+      for (int p = 0; p < PPT; ++p) v[p] = leaf ? A::from_coef(__ldg(cs)) : acc[(S * PPT + p) * TPB + tid];
       if ((h.x >> kOpUniform) & 1u) {
         const int pc = (int)__ldg(o.chain_pid + j0);
         W xu[PPT];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) xu[p] = pw[(pc * PPT + p) * kTPB + tid];
+        for (int p = 0; p < PPT; ++p) xu[p] = pw[(pc * PPT + p) * TPB + tid];
         if (pc == o.pos_x1) {  // Horner runs over consecutive exponents
           for (int t = 1; t < len; ++t) {
             const V cj = A::from_coef(__ldg(cs + t));
@@ -800,7 +802,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
           const V cj = A::from_coef(__ldg(cs + t));
 #pragma unroll
           for (int p = 0; p < PPT; ++p)
-            v[p] = A::template mad_k<false, true, false>(v[p], pw[(pc * PPT + p) * kTPB + tid], cj);
+            v[p] = A::template mad_k<false, true, false>(v[p], pw[(pc * PPT + p) * TPB + tid], cj);
         }
       }
     } else if constexpr (SCHEME != 0 && A::kExact) {
@@ -819,7 +821,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
       }
       const V cl = A::from_coef(__ldg(cs + len - 1));
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xp[p][1], partial ? acc[(S * PPT + p) * kTPB + tid] : cl);
+      for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xp[p][1], partial ? acc[(S * PPT + p) * TPB + tid] : cl);
     } else {
       if constexpr (SCHEME != 0) {
         C c[kMaxBlock];
@@ -837,7 +839,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
         V slot[PPT];
         if (partial) {
 #pragma unroll
-          for (int p = 0; p < PPT; ++p) slot[p] = acc[(S * PPT + p) * kTPB + tid];
+          for (int p = 0; p < PPT; ++p) slot[p] = acc[(S * PPT + p) * TPB + tid];
         }
         block_dispatch<A, SCHEME, PPT>(len, partial, c, xp, slot, v);
       }
@@ -845,26 +847,26 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     // the outgoing edge of the op's last node
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-      V* dst = &acc[(D * PPT + p) * kTPB + tid];
+      V* dst = &acc[(D * PPT + p) * TPB + tid];
       const V init = first ? A::from_coef(b) : *dst;
-      *dst = A::mad(v[p], pw[(pid * PPT + p) * kTPB + tid], init);
+      *dst = A::mad(v[p], pw[(pid * PPT + p) * TPB + tid], init);
     }
   }
 
   const C rc = A::coef_from_bits(g.root_c);
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    const int64_t idx = base + p * kTPB + tid;
-    V r = A::root(g.root_leaf, rc, &acc[(o.root_lh * PPT + p) * kTPB + tid]);
-    if (o.root_pid >= 0) r = A::apply_root_power(r, pw[(o.root_pid * PPT + p) * kTPB + tid]);
+    const int64_t idx = base + p * TPB + tid;
+    V r = A::root(g.root_leaf, rc, &acc[(o.root_lh * PPT + p) * TPB + tid]);
+    if (o.root_pid >= 0) r = A::apply_root_power(r, pw[(o.root_pid * PPT + p) * TPB + tid]);
     if (idx < g.npts) A::store(g.out, idx, g.npts, r);
   }
 }
 
-template <class A, int PPT, int SCHEME>
-__global__ void __launch_bounds__(kTPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
+template <class A, int PPT, int SCHEME, int TPB = kTPB>
+__global__ void __launch_bounds__(TPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ops_tile<A, PPT, SCHEME>(g, o, (int64_t)blockIdx.x * (kTPB * PPT), smem_raw);
+  ops_tile<A, PPT, SCHEME, TPB>(g, o, (int64_t)blockIdx.x * (TPB * PPT), smem_raw);
 }
 
 // Launch helpers (defined per type in eval_<type>.cu).  variant: 0 = choose,
@@ -917,24 +919,56 @@ size_t ops_smem(const OpArgs& o) {
   return sizeof(typename A::pw) * (size_t)o.entries * PPT * kTPB;
 }
 
-template <class A, int PPT, int SCHEME>
-cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
-  const size_t smem = ops_smem<A, PPT>(o);
+template <class A, int PPT, int SCHEME, int TPB>
+cudaError_t launch_eval_ops_tpb(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
+  const size_t smem = ops_smem<A, PPT>(o) / kTPB * TPB;
   if (smem > kSmemMax) return cudaErrorInvalidValue;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured_dev != dev) {
-    cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, PPT, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, PPT, SCHEME, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e != cudaSuccess) return e;
     configured_dev = dev;
   }
-  const int64_t per_block = (int64_t)kTPB * PPT;
+  const int64_t per_block = (int64_t)TPB * PPT;
   const int64_t blocks = (a.npts + per_block - 1) / per_block;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
-  eval_ops_kernel<A, PPT, SCHEME><<<(unsigned)blocks, kTPB, smem, s>>>(a, o);
+  eval_ops_kernel<A, PPT, SCHEME, TPB><<<(unsigned)blocks, TPB, smem, s>>>(a, o);
   return cudaGetLastError();
+}
+
+// multiprocessors of the current device (cached per device)
+inline int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 152; }
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// Small grids balance badly over the SMs (a grid of 3.4 blocks per SM runs
+// as long as its SMs with 4): one point per thread and fewer than 16 blocks
+// of kTPB threads per SM takes narrower blocks (64, or 32 under 4 per SM), so
+// the remainder is a smaller fraction of each SM's share.  Results do not
+// depend on the block width.
+template <class A, int PPT, int SCHEME>
+cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
+  if constexpr (PPT == 1) {
+    const int64_t blocks = (a.npts + kTPB - 1) / kTPB;
+    const int64_t sms = sm_count();
+    if (blocks < 4 * sms) return launch_eval_ops_tpb<A, PPT, SCHEME, 32>(a, o, s);
+    if (blocks < 16 * sms) return launch_eval_ops_tpb<A, PPT, SCHEME, 64>(a, o, s);
+  }
+  return launch_eval_ops_tpb<A, PPT, SCHEME, kTPB>(a, o, s);
 }
 
 // Kernel choice for the fused types: the grouped-op kernel whenever the power

@@ -291,3 +291,44 @@ def test_exact_horner_geometric_closed_form_10007(xv):
     ax = abs(x)
     assert v == (x ** k - 1) / (x - 1)
     assert s == (ax ** k - 1) / (ax - 1)
+
+
+# ------------------------------------------------------------ fixed-point enclosure (fast reference)
+@pytest.mark.parametrize("k", [1, 2, 17, 64, 300])
+def test_horner_enclosure_contains_exact_value(k):
+    """The enclosure V 2^-F +- k 2^-F contains the exact value (exact rational
+    Horner) and the condition sum, at points of both signs in [-1, 1]; with
+    F large the interval is far below 2^-1000."""
+    e, c, x = W.univariate_case(k, 6, 700 + k)
+    F = 1200
+    for xv in list(x[0]) + [-1.0, 1.0, 0.0, -0.5]:
+        v, s = X.exact_horner_univariate(c[::-1], xv)
+        V, A, E = X.horner_enclosure(c[::-1], xv, F)
+        assert E == k
+        scale = Fraction(2) ** -F
+        assert abs(v - V * scale) <= E * scale, xv
+        assert abs(s - A * scale) <= E * scale, xv
+
+
+def test_horner_enclosure_geometric_10007():
+    """k = 10007 ones at x = -0.99609375: the enclosure contains (x^k - 1)/(x - 1)
+    and (|x|^k - 1)/(|x| - 1)."""
+    k, xv, F = 10007, -0.99609375, 1200
+    V, A, E = X.horner_enclosure(np.ones(k), xv, F)
+    x = Fraction(xv)
+    scale = Fraction(2) ** -F
+    assert abs((x ** k - 1) / (x - 1) - V * scale) <= E * scale
+    assert abs((abs(x) ** k - 1) / (abs(x) - 1) - A * scale) <= E * scale
+
+
+def test_horner_enclosure_rounds_down_only():
+    """A planted error is caught: dropping the coefficient of x^1 moves the
+    enclosure away from the exact value by that coefficient."""
+    c = np.array([0.5, 0.25, -0.75])
+    V, A, E = X.horner_enclosure(c, 0.5, 64)
+    v, _ = X.exact_horner_univariate(c, 0.5)
+    assert abs(v - Fraction(V, 2 ** 64)) <= Fraction(E, 2 ** 64)
+    c2 = c.copy()
+    c2[1] = 0.0
+    V2, _, _ = X.horner_enclosure(c2, 0.5, 64)
+    assert abs(v - Fraction(V2, 2 ** 64)) > Fraction(1, 10)
