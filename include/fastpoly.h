@@ -268,6 +268,60 @@ int fp_batch_launch(const fp_batch* batch, void* stream);
 void fp_batch_free(fp_batch* batch);
 
 /*
+ * A resident evaluation kernel with a device work queue: persistent blocks
+ * that stay on the GPU and take tiles of jobs published while they run, so
+ * new work enters a running kernel without a launch (no counterpart in the
+ * paper).  One value type per resident kernel.  Jobs use the layouts and give
+ * the results of fp_eval.  The queue lives in pinned host memory mapped into
+ * the device: fp_resident_submit writes a job's descriptor and publishes its
+ * tiles with plain stores (no stream operation); blocks claim tiles one at a
+ * time (dynamic balance over the SMs); the block that finishes a job's last
+ * tile sets its completion flag, which fp_resident_query reads.
+ * Waits are bounded: idle blocks sleep between polls and exit after
+ * idle_exit_s without work; a later submission (or fp_resident_wait) launches
+ * the kernel again.  The kernel occupies up to blocks_per_sm blocks on every
+ * SM while it runs.  One host thread should drive a resident kernel.  The
+ * kernel follows no stream: a job's points (and anything that writes its
+ * output buffer) must be complete on the device when it is submitted.
+ */
+typedef struct fp_resident fp_resident;
+typedef struct {
+  fp_dtype dtype;       /* value type of every job */
+  int max_jobs;         /* capacity of the job table (1 .. 2^24) */
+  size_t smem_bytes;    /* shared memory per block (0: 48 KB): a job whose
+                           per-point table needs more is refused (FP_E_TOO_LARGE) */
+  int blocks_per_sm;    /* <= 0: as many as fit */
+  double idle_exit_s;   /* blocks exit after this long without work (<= 0: 0.05 s) */
+  int64_t max_items;    /* capacity of the work-item table (<= 0: the larger of
+                           16 max_jobs and 65536; 16 bytes each); a
+                           job takes one item per 4 tiles of 128 (FP32C, MODP:
+                           256) points */
+} fp_resident_cfg;
+
+/* Allocates the queue and launches the kernel on a stream of its own.
+ * Errors: FP_E_BAD_VALUE, FP_E_DTYPE, FP_E_TOO_LARGE, FP_E_NOMEM, FP_E_CUDA. */
+int fp_resident_create(const fp_resident_cfg* cfg, fp_resident** out);
+/* Publish a job (tree, device points and output; see fp_job) and return its
+ * ticket.  The job's buffers and tree must stay valid until it completes.
+ * Errors: FP_E_BAD_VALUE (zero polynomial included: use fp_eval), FP_E_DTYPE,
+ * FP_E_TOO_LARGE (table too large for the blocks, or the job or item table
+ * is full). */
+int fp_resident_submit(fp_resident* r, const fp_job* job, int64_t* ticket);
+/* FP_OK when the job has completed, 1 while it is pending. */
+int fp_resident_query(const fp_resident* r, int64_t ticket);
+/* Wait at most timeout_s seconds for the job: FP_OK or FP_E_TIMEOUT. */
+int fp_resident_wait(fp_resident* r, int64_t ticket, double timeout_s);
+/* Whether the kernel is running, whether its blocks have ever left on the
+ * idle timeout (the device-side wait that ran out), jobs submitted. */
+int fp_resident_state(const fp_resident* r, int* running, int* idle_exits, int64_t* jobs);
+/* Ask the blocks to exit once the published tiles are taken, and wait at most
+ * timeout_s (<= 0: 60) for them: FP_OK or FP_E_TIMEOUT.  Submissions after a
+ * stop are refused (FP_E_BAD_VALUE). */
+int fp_resident_stop(fp_resident* r, double timeout_s);
+/* Stops the kernel (waiting up to 60 s) and releases everything. */
+void fp_resident_free(fp_resident* r);
+
+/*
  * Serving with continuous batching.  Requests (a resident compiled tree, a
  * value type, host points, a host result buffer) are submitted from any
  * thread and complete asynchronously.  A worker thread admits pending

@@ -44,11 +44,19 @@ for _name, _args in {
     "fp_compose_noalloc": [_P, _I, _P, _P, _I, _I64, _P, _P],
     "fp_compose_workspace": [_P, _I, _I, _I, _I64, ctypes.POINTER(ctypes.c_size_t)],
     "fp_set_compose_f64": [_I, _I],
+    "fp_resident_create": [_P, ctypes.POINTER(_P)],
+    "fp_resident_submit": [_P, _P, ctypes.POINTER(_I64)],
+    "fp_resident_query": [_P, _I64],
+    "fp_resident_wait": [_P, _I64, ctypes.c_double],
+    "fp_resident_state": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)],
+    "fp_resident_stop": [_P, ctypes.c_double],
 }.items():
     getattr(_lib, _name).restype = _I
     getattr(_lib, _name).argtypes = _args
 _lib.fp_free.restype = None
 _lib.fp_free.argtypes = [_P]
+_lib.fp_resident_free.restype = None
+_lib.fp_resident_free.argtypes = [_P]
 _lib.fp_strerror.restype = ctypes.c_char_p
 _lib.fp_strerror.argtypes = [_I]
 
@@ -562,6 +570,67 @@ class Server:
         if self._h:
             _lib.fp_server_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _ResidentCfg(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("max_jobs", ctypes.c_int), ("smem_bytes", ctypes.c_size_t),
+                ("blocks_per_sm", ctypes.c_int), ("idle_exit_s", ctypes.c_double), ("max_items", ctypes.c_int64)]
+
+
+class Resident:
+    """A resident evaluation kernel with a device work queue (fp_resident_*):
+    jobs submitted while it runs enter the running kernel.  One value type."""
+
+    def __init__(self, dtype, max_jobs=4096, smem_bytes=0, blocks_per_sm=0, idle_exit_s=0.05, max_items=0):
+        cfg = _ResidentCfg(DTYPES[dtype], max_jobs, smem_bytes, blocks_per_sm, idle_exit_s, max_items)
+        h = ctypes.c_void_p()
+        _check(_lib.fp_resident_create(ctypes.byref(cfg), ctypes.byref(h)), "fp_resident_create")
+        self._h = h.value
+        self.dtype = dtype
+        self._keep = {}  # ticket -> (tree, points, out): alive until the job completes
+
+    def submit(self, tree, points, out):
+        """points, out: CUDA tensors in fp_eval layouts.  Returns the ticket."""
+        if not points.is_cuda or not out.is_cuda or not points.is_contiguous() or not out.is_contiguous():
+            raise ValueError("points and out must be contiguous CUDA tensors")
+        job = _Job(tree.handle, points.data_ptr(), points.shape[-1], out.data_ptr())
+        t = ctypes.c_int64()
+        _check(_lib.fp_resident_submit(self._h, ctypes.byref(job), ctypes.byref(t)), "fp_resident_submit")
+        self._keep[t.value] = (tree, points, out)
+        return t.value
+
+    def done(self, ticket):
+        rc = _lib.fp_resident_query(self._h, ticket)
+        if rc < 0:
+            _check(rc, "fp_resident_query")
+        if rc == 0:
+            self._keep.pop(ticket, None)
+        return rc == 0
+
+    def wait(self, ticket, timeout_s=60.0):
+        _check(_lib.fp_resident_wait(self._h, ticket, timeout_s), "fp_resident_wait")
+        self._keep.pop(ticket, None)
+
+    def state(self):
+        running, idle, jobs = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(_lib.fp_resident_state(self._h, ctypes.byref(running), ctypes.byref(idle), ctypes.byref(jobs)),
+               "fp_resident_state")
+        return {"running": bool(running.value), "idle_exits": bool(idle.value), "jobs": jobs.value}
+
+    def stop(self, timeout_s=60.0):
+        _check(_lib.fp_resident_stop(self._h, timeout_s), "fp_resident_stop")
+
+    def close(self):
+        if self._h:
+            _lib.fp_resident_free(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
