@@ -1067,10 +1067,58 @@ def measure_batched(fpl, W, n, hbm_budget_mib=8192):
         done = srv.poll()
         assert len(done) == n and all(st == 0 for _, st, _ in done), "server requests failed"
 
-    res = {"plain_one_launch_per_poly_ms": wall(plain_device), "fp_eval_batch_ms": wall(batch_call),
-           "planned_batch_launch_ms": wall(planned.launch)}
+    # the resident kernel: every polynomial submitted into the running kernel
+    # (device-resident inputs), waiting for all
+    out_res = [torch.empty((1, m), dtype=torch.float64, device=dev) for _, m, _, _, _ in polys]
+    items = sum(-(-(-(-m // 128)) // 4) for _, m, _, _, _ in polys)  # work items of one pass (4 tiles of 128 points)
+    resident = fpl.Resident("f64", max_jobs=5 * n + 64, idle_exit_s=1.0, max_items=5 * items + 64)
+    torch.cuda.synchronize()
+
+    def resident_pass():
+        tk = [resident.submit(t, pts_d[i], out_res[i]) for i, (_, _, t, _, _) in enumerate(polys)]
+        for x in tk:
+            resident.wait(x, 600.0)
+
+    def wall_resident():
+        # the resident kernel stays on its own stream until its idle timeout:
+        # a device-wide synchronize would wait for that; the pass is timed
+        # from the first submission to the last completion
+        ts = []
+        for rep in range(4):
+            torch.cuda.current_stream().synchronize()
+            t0 = time.perf_counter()
+            resident_pass()
+            if rep:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts))
+
+    res = {"resident_kernel_ms": wall_resident()}
+    res.update({"plain_one_launch_per_poly_ms": wall(plain_device), "fp_eval_batch_ms": wall(batch_call),
+                "planned_batch_launch_ms": wall(planned.launch)})
     res["speedup_fp_eval_batch"] = res["plain_one_launch_per_poly_ms"] / res["fp_eval_batch_ms"]
     res["speedup_planned_batch"] = res["plain_one_launch_per_poly_ms"] / res["planned_batch_launch_ms"]
+    res["speedup_resident_kernel"] = res["plain_one_launch_per_poly_ms"] / res["resident_kernel_ms"]
+    # admission latency of a small job (100 terms, 1000 points): submitted to
+    # the running resident kernel, against a launch of fp_eval with a synchronize
+    e_s, c_s, x_s = W.univariate_case(100, 1000, 6050)
+    t_s = fpl.fp_compile(e_s, c_s, "B")
+    d_s = torch.from_numpy(x_s).to(dev)
+    o_s = torch.empty((1, 1000), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    lat_res, lat_launch = [], []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        resident.wait(resident.submit(t_s, d_s, o_s), 60.0)
+        lat_res.append((time.perf_counter() - t0) * 1e6)
+    resident.close()  # stops the kernel (the synchronizes below would wait for its idle timeout)
+    for _ in range(50):
+        t0 = time.perf_counter()
+        fpl.fp_eval(t_s, "f64", d_s, out=o_s[0])
+        torch.cuda.synchronize()
+        lat_launch.append((time.perf_counter() - t0) * 1e6)
+    res["small_job_latency_us"] = {"resident_kernel_median": float(np.median(lat_res)),
+                                   "launch_and_sync_median": float(np.median(lat_launch)),
+                                   "job": "100 terms, 1000 points, FP64"}
     host = {"plain_with_copies_ms": wall(plain_host), "server_ms": wall(served)}
     host["speedup_server"] = host["plain_with_copies_ms"] / host["server_ms"]
     # the results agree within the FP64 bound
@@ -1078,7 +1126,7 @@ def measure_batched(fpl, W, n, hbm_budget_mib=8192):
     for i, (k, m, _, c, x) in enumerate(polys):
         S = fpl.fp_eval_plain_f64(coef_d[i].abs(), pts_d[i].abs()).cpu().numpy()
         ref = out_plain[i].cpu().numpy()
-        for got in (out_batch[i][0].cpu().numpy(), out_h[i].numpy(), out_srv[i][0]):
+        for got in (out_batch[i][0].cpu().numpy(), out_h[i].numpy(), out_srv[i][0], out_res[i][0].cpu().numpy()):
             worst = max(worst, float(np.max(np.abs(got - ref) / (8 * k * 2.0 ** -53 * S + 1e-300))))
     planned.free()
     srv.close()
@@ -1089,6 +1137,7 @@ def measure_batched(fpl, W, n, hbm_budget_mib=8192):
             "G_term_evals_per_s": {"plain": evals / res["plain_one_launch_per_poly_ms"] / 1e6,
                                    "fp_eval_batch": evals / res["fp_eval_batch_ms"] / 1e6,
                                    "planned_batch": evals / res["planned_batch_launch_ms"] / 1e6,
+                                   "resident_kernel": evals / res["resident_kernel_ms"] / 1e6,
                                    "server_host_buffers": evals / host["server_ms"] / 1e6,
                                    "plain_host_buffers": evals / host["plain_with_copies_ms"] / 1e6},
             "max_error_over_8kuS": worst, "n_gpus": 1, "data": "synthetic"}

@@ -75,6 +75,13 @@ __device__ __forceinline__ int ld_acquire_sys_i32(const int* p) {
 __device__ __forceinline__ void st_release_sys_i32(int* p, int v) {
   asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// acquire-release add at device scope: a block's tile count orders its
+// results before the count, and the last block's acquire sees every block's
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -101,7 +108,7 @@ __device__ unsigned long long claim_tile(ResQueue* q, unsigned long long* claime
       return kNoTile;
     }
     __nanosleep(sleep);
-    if (sleep < 4096) sleep *= 2;
+    if (sleep < 1024) sleep *= 2;
   }
 }
 
@@ -137,31 +144,37 @@ __global__ void __launch_bounds__(kTPB) resident_kernel(ResQueue* q, const ResJo
     }
     __syncthreads();
     if (threadIdx.x == 0) s_cached = job;
-    for (int t = 0; t < s_ntiles; ++t) {
-      const int64_t base = (s_tile + t) * (kTPB * PPT);
+    // the arguments in registers: read from shared memory inside the tile
+    // code, every store to the per-point table (shared memory too) could
+    // alias them and force reloads in the hot loops
+    const EvalArgs g = s_desc.g;
+    const int mode = s_desc.mode, scheme = s_desc.scheme, ntiles = s_ntiles;
+    const int64_t tile = s_tile;
+    for (int t = 0; t < ntiles; ++t) {
+      const int64_t base = (tile + t) * (kTPB * PPT);
       if constexpr (std::is_same<A, IV64>::value) {
-        if (s_desc.mode == kResModeNodeTable) node_tile<A, PPT, true>(s_desc.g, base, smem_raw);
-        else node_tile<A, PPT, false>(s_desc.g, base, smem_raw);
+        if (mode == kResModeNodeTable) node_tile<A, PPT, true>(g, base, smem_raw);
+        else node_tile<A, PPT, false>(g, base, smem_raw);
       } else {
-        if (s_desc.mode == kResModeOps) {
-          if (s_desc.scheme == FP_SCHEME_E) ops_tile<A, PPT, FP_SCHEME_E>(s_desc.g, s_desc.o, base, smem_raw);
-          else if (s_desc.scheme == FP_SCHEME_B) ops_tile<A, PPT, FP_SCHEME_B>(s_desc.g, s_desc.o, base, smem_raw);
-          else ops_tile<A, PPT, 0>(s_desc.g, s_desc.o, base, smem_raw);
-        } else if (s_desc.mode == kResModeNodeTable) {
-          node_tile<A, PPT, true>(s_desc.g, base, smem_raw);
+        if (mode == kResModeOps) {
+          const OpArgs o = s_desc.o;
+          if (scheme == FP_SCHEME_E) ops_tile<A, PPT, FP_SCHEME_E>(g, o, base, smem_raw);
+          else if (scheme == FP_SCHEME_B) ops_tile<A, PPT, FP_SCHEME_B>(g, o, base, smem_raw);
+          else ops_tile<A, PPT, 0>(g, o, base, smem_raw);
+        } else if (mode == kResModeNodeTable) {
+          node_tile<A, PPT, true>(g, base, smem_raw);
         } else {
-          node_tile<A, PPT, false>(s_desc.g, base, smem_raw);
+          node_tile<A, PPT, false>(g, base, smem_raw);
         }
       }
     }
-    // every thread's results visible system-wide before the job is counted
-    __threadfence_system();
+    // the block's results happen before thread 0's release (the barrier),
+    // which the count carries to the last block; its system-scope release of
+    // the flag is cumulative, so the host's acquire sees every result
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (atomicAdd(&tiles_done[job], s_ntiles) + s_ntiles == (int)s_desc.ntiles) {
-        __threadfence_system();
+      if (atom_add_acq_rel_gpu(&tiles_done[job], ntiles) + ntiles == (int)s_desc.ntiles)
         st_release_sys_i32(&done[job], 1);
-      }
     }
     __syncthreads();
   }
