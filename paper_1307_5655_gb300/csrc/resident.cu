@@ -50,7 +50,7 @@ struct ResJob {
 struct ResQueue {             // mapped host memory
   unsigned long long published;
   int stop;
-  int pad;
+  int active;                 // blocks of the current launch not yet exited
 };
 
 struct ResItem {  // one claim: tiles [tile, tile + ntiles) of job `job`
@@ -108,7 +108,7 @@ __device__ unsigned long long claim_tile(ResQueue* q, unsigned long long* claime
       return kNoTile;
     }
     __nanosleep(sleep);
-    if (sleep < 1024) sleep *= 2;
+    if (sleep < 256) sleep *= 2;
   }
 }
 
@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(kTPB) resident_kernel(ResQueue* q, const ResJo
       }
     }
     __syncthreads();
-    if (s_item == kNoTile) break;
+    if (s_item == kNoTile) {
+      if (threadIdx.x == 0) atomicSub_system(&q->active, 1);
+      break;
+    }
     const int job = s_job;
     // the descriptor into shared memory, unless it is already there (it was
     // written before its items were published: the acquire load ordered it)
@@ -245,6 +248,7 @@ namespace {
 
 int res_start(fp_resident* r) {
   cudaError_t e = cudaSuccess;
+  reinterpret_cast<std::atomic<int>*>(&r->q->active)->store(r->grid, std::memory_order_release);
 #define FP_RES_LAUNCH(T, P)                                                                                      \
   e = res_launch<T, P>(r->grid, r->smem, r->stream, r->dq, r->djobs, r->ditems, r->claimed, r->tiles_done, r->ddone, \
                        r->idle_ns, r->state)
@@ -279,8 +283,15 @@ void res_release(fp_resident* r) {
 // queue's counters persist); a block may time out just before a submission
 // it did not see, so waits call this too.
 int res_kick(fp_resident* r) {
-  if (r->running && cudaStreamQuery(r->stream) == cudaSuccess) r->running = false;
-  cudaGetLastError();
+  // every block of the launch has left (a plain read of the count the blocks
+  // decrement on exit; no driver call on the submission path)
+  if (r->running && reinterpret_cast<std::atomic<int>*>(&r->q->active)->load(std::memory_order_acquire) == 0) {
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return FP_E_CUDA;
+    }
+    r->running = false;
+  }
   if (r->running || r->q->stop) return FP_OK;
   unsigned long long claimed = 0;
   if (cudaMemcpy(&claimed, r->claimed, sizeof(claimed), cudaMemcpyDeviceToHost) != cudaSuccess) {
