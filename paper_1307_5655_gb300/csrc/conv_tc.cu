@@ -28,15 +28,20 @@
 // i + j <= S - 1 are kept (the dropped ones are below 2^(-7 S) of the block
 // products).  Accumulator g (g = i + j = 0..3) sums one group exactly: over
 // K = 64 its integer value D_g = sum d d' has |D_g| <= 4 * 64^3 < 2^22 and
-// FP32 holds it without rounding.  Accumulator 4 sums the groups g >= 4 with
-// FP32 rounding far below the recombination's resolution.
+// FP32 holds it without rounding.  The groups g >= 4 are summed with FP32
+// rounding far below the recombination's resolution, in two accumulators
+// (the pairs with i even and odd: two parts of a step that two threads can
+// issue side by side).
 //
-// Recombination.  Each step reads the five accumulators (tcgen05.ld), turns
+// Recombination.  Each step reads the six accumulators (tcgen05.ld), turns
 // each into its integer with one FMA against 1.5 2^23 (exact for |D| < 2^22),
-// and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 (|C| < 2^47) and D_4:
-// the step contributes (C + D_4) 2^(alpha_{w-v} + beta_v - 40).  The exact
-// groups are committed first and read out while the tensor cores run the
-// combined group; the next window of b is loaded meanwhile.  Each output row
+// and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 (|C| < 2^47) and
+// D_4 (the two combined accumulators' integers, each rounded to the unit):
+// the step contributes (C + D_4) 2^(alpha_{w-v} + beta_v - 40).  TMEM holds
+// the four exact accumulators once and the combined pair twice (512
+// columns), so all of step v + 1 is issued as soon as step v's exact groups
+// are read out, and the tensor cores run it while step v's combined group is
+// read out and the Hankel operand of step v + 2 is built.  Each output row
 // keeps a 64-bit fixed-point accumulator with unit 2^F_w, F_w = max over the
 // row's steps of alpha + beta - 40 - (15 - hr), hr the bits of the row's step
 // count: every contribution stays below 2^(62 - hr) units and their sum
@@ -63,13 +68,15 @@ constexpr int MROWS = 128;           // output blocks per tile (MMA M, TMEM lane
 constexpr int WROWS = MROWS + V;     // rows of the A window in shared memory
 constexpr int STRIP = WROWS * 16;    // bytes of one (slice, 8-column chunk) strip of A
 constexpr int HANKEL = 16 * 8 * 16;  // bytes of one slice's shifted window copies (16 lines x 8 shifts)
-constexpr int NACC = 5;              // TMEM accumulators of 64 columns
-constexpr int THREADS = 256;
+constexpr int NACC = 5;              // accumulator groups: exact g = 0..3, combined g >= 4
+constexpr int NCOMB = 2;             // TMEM accumulators of the combined group
+constexpr int READERS = 256;         // warps 0-7 read the accumulators out and build the operands
+constexpr int THREADS = READERS + 32;  // warp 8 issues the MMAs
 constexpr int ZERO_EXP = -100000;    // exponent bound of an all-zero block
-constexpr int TMEM_COLS = 512;       // power of two >= NACC * 64
+constexpr int TMEM_COLS = 512;       // exact groups 4 x 64, combined group 2 buffers x NCOMB x 64
 constexpr int SMEM_MIN = 120 * 1024; // at least half the SM: one tile per SM holds the TMEM
 
-__host__ __device__ constexpr int smem_bytes(int S) { return S * 8 * STRIP + 2 * S * HANKEL + S * 128 * 2; }
+__host__ __device__ constexpr int smem_bytes(int S) { return S * 8 * STRIP + 2 * S * HANKEL + 2 * S * 256; }
 
 // ------------------------------------------------------------------ slicing
 // smallest alpha with |x| < 2^alpha (ZERO_EXP for x = 0)
@@ -230,30 +237,25 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
                  "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
 }
 
-// The MMAs of one step for the exact groups (PASS 0: i + j < NACC - 1) or
-// the combined group (PASS 1): slice i of the A window times slice j of B_v
-// over K = 64 (four MMAs of K = 16), into accumulator min(i + j, NACC - 1);
-// the first MMA into an accumulator overwrites it.  For each slice i and
-// K step, the A tile is read from shared memory once and kept in the
-// collector buffer for every slice j it meets.  The start-address field of a
-// descriptor holds addr >> 4 (14 bits, shared memory < 256 KB): adding
-// offset >> 4 moves it.
-template <int S, int PASS, int I, int KS, int J, int FIRST>
+// The MMAs of one step: PASS 0 the exact groups (i + j < NACC - 1, into
+// accumulator i + j at column 64 (i + j) of tmem), PASS 1 and 2 the combined
+// group's pairs with i even / odd (into the one accumulator at tmem): slice i
+// of the A window times slice j of B_v over K = 64 (four MMAs of K = 16).
+// Each accumulator gets its MMAs from one pass, in order (deterministic
+// sums), and the first MMA into it overwrites it.  The start-address field of a descriptor holds addr >> 4 (14
+// bits, shared memory < 256 KB): adding offset >> 4 moves it.
+template <int S, int PASS, int I, int KS, int J>
 __device__ __forceinline__ void issue_j(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t& used) {
   if constexpr (J < S) {
-    constexpr bool keep = I + J <= S - 1 && ((I + J < NACC - 1) == (PASS == 0));
+    constexpr bool exact = I + J < NACC - 1;
+    constexpr bool keep = I + J <= S - 1 && (PASS == 0 ? exact : (!exact && (I & 1) == PASS - 1));
     if constexpr (keep) {
-      // the last j this (i, K step) meets in this pass
-      constexpr int JLAST = PASS == 0 ? (NACC - 2 - I) : (S - 1 - I);
-      constexpr int COL = (FIRST && J == JLAST) ? 0 : (FIRST ? 1 : (J == JLAST ? 3 : 2));
-      constexpr int g = I + J < NACC - 1 ? I + J : NACC - 1;
-      mma<COL>(tmem + (uint32_t)(g * T), dA + (uint64_t)(((I * 8 + 2 * KS) * STRIP) >> 4),
-               dB + (uint64_t)((J * HANKEL + 2 * KS * 128) >> 4), (used >> g) & 1u);
+      constexpr int g = PASS == 0 ? I + J : 0;
+      mma<0>(tmem + (uint32_t)(g * T), dA + (uint64_t)(((I * 8 + 2 * KS) * STRIP) >> 4),
+             dB + (uint64_t)((J * HANKEL + 2 * KS * 128) >> 4), (used >> g) & 1u);
       used |= 1u << g;
-      issue_j<S, PASS, I, KS, J + 1, 0>(tmem, dA, dB, used);
-    } else {
-      issue_j<S, PASS, I, KS, J + 1, FIRST>(tmem, dA, dB, used);
     }
+    issue_j<S, PASS, I, KS, J + 1>(tmem, dA, dB, used);
   }
 }
 
@@ -261,7 +263,7 @@ template <int S, int PASS, int I, int KS>
 __device__ __forceinline__ void issue_iks(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t& used) {
   if constexpr (I < S) {
     if constexpr (KS < T / 16) {
-      issue_j<S, PASS, I, KS, 0, 1>(tmem, dA, dB, used);
+      issue_j<S, PASS, I, KS, 0>(tmem, dA, dB, used);
       issue_iks<S, PASS, I, KS + 1>(tmem, dA, dB, used);
     } else {
       issue_iks<S, PASS, I + 1, 0>(tmem, dA, dB, used);
@@ -275,12 +277,18 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem, uint64_t dA, uint64_t 
   issue_iks<S, PASS, 0, 0>(tmem, dA, dB, used);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// eight consecutive columns of the warp's 32 TMEM lanes (one lane per thread)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+// the reader warps' barrier (named barrier 1; the issuing warp takes no part)
+__device__ __forceinline__ void readers_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(READERS) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
@@ -300,45 +308,70 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 // One tile: output blocks w0 .. w0 + 127 of one pair, all 64 coefficients.
+// Warps 0-7 (the readers) read the accumulators out -- warp i reads TMEM
+// lanes 32 (i & 3) .. + 31 and columns 32 (i >> 2) .. + 31 of each
+// accumulator: one output block and 32 of its coefficients per thread -- and
+// build the operands; lane 0 of warp 8 issues the MMAs.  tcgen05.mma holds
+// its thread while the tensor cores' queue is full, so a thread that issued
+// and also read out would leave the tensor cores idle during its readout.
+//
+// Steps k = 0 .. v_hi - v_lo (v = v_lo + k).  Barriers:
+//   full_x     step k's exact groups are in TMEM (commit; phase k)
+//   full_y(b)  step k's combined group, b = k & 1 (commit; phase k >> 1)
+//   ready      step k's operands are in shared memory and step k - 1's exact
+//              groups are read out (the readers; phase k - 1; step 0 is
+//              covered by the prologue's __syncthreads)
+//   free_y(b)  step k's combined group is read out (the readers; phase k >> 1)
+// A step is issued only after the readers passed the previous phase of each
+// barrier it waits on, so no wait is ever more than one phase behind and the
+// parity of the awaited phase identifies it.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     k_conv_tc(const uint4* __restrict__ ahat, const int* __restrict__ alpha, int nA, const uint4* __restrict__ rhat,
               const int* __restrict__ beta, int nV, int nW, int rl, int mtiles, double* out, int64_t out_pitch,
               int mode, const double* init, int64_t init_pitch, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[6];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ int s_fail[3];  // a reader's wait of iteration k gave up (slot k & 1); the issuer's (slot 2)
   unsigned char* sA = smem;                                // A window: S x 8 strips
   unsigned char* sH = smem + S * 8 * STRIP;                // Hankel operand: 2 buffers x S slices
-  uint32_t* sW = (uint32_t*)(sH + 2 * S * HANKEL);         // staged window: S x 64 words
+  uint32_t* sW = (uint32_t*)(sH + 2 * S * HANKEL);         // staged windows: 2 buffers x S x 64 words
   const int64_t pr = blockIdx.x / mtiles;
   const int w0 = (int)(blockIdx.x % mtiles) * MROWS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, column half
-  const int w = w0 + 32 * q + lane;       // this thread's output block
+  const bool reader = threadIdx.x < READERS;
+  const int q = warp & 3, h = (warp >> 2) & 1;  // TMEM lane quadrant, column half
+  const int w = w0 + 32 * q + lane;             // a reader's output block
   const int* al = alpha + pr * nA;
   const int* be = beta + pr * nV;
   const int v_lo = max(0, w0 - nA + 1);
   const int v_hi = min(nV - 1, w0 + MROWS - 1);
+  const int nsteps = v_hi - v_lo + 1;  // may be <= 0
   // the row's fixed-point unit 2^F: with n steps meeting the row (hr bits),
   // every contribution |C| 2^E < 2^(47 + 15 - hr) and their sum < 2^62
   int mx = 2 * ZERO_EXP;
   const int v_first = max(0, w - nA + 1), v_last = min(nV - 1, w);
-  if (w < nW)
+  if (reader && w < nW)
     for (int v = v_first; v <= v_last; ++v) mx = max(mx, __ldg(al + w - v) + __ldg(be + v));
   const int hr = 32 - __clz(max(1, v_last - v_first + 1));
-  const int P = 15 - hr;       // C is pre-shifted by P: E <= P
+  const int P = 15 - hr;  // C is pre-shifted by P: E <= P
   const int F = mx - 40 - P;
   long long acc[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = 0;
 
-  const uint32_t barx = smem_u32(&bar[0]), bary = smem_u32(&bar[1]);
+  const uint32_t full_x = smem_u32(&bar[0]), ready = smem_u32(&bar[3]);
+  auto full_y = [&](int b) { return smem_u32(&bar[1 + b]); };
+  auto free_y = [&](int b) { return smem_u32(&bar[4 + b]); };
   if (threadIdx.x == 0) {
-    s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(barx), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bary), "r"(1));
+    s_fail[0] = s_fail[1] = s_fail[2] = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_x), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_y(0)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_y(1)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ready), "r"(READERS));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(free_y(0)), "r"(READERS));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(free_y(1)), "r"(READERS));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -346,123 +379,177 @@ __global__ void __launch_bounds__(THREADS, 1)
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
-  // W_v of every slice into sW
-  auto stage_window = [&](int v) {
-    if (threadIdx.x < S * 16) ((uint4*)sW)[threadIdx.x] = __ldg(rhat + (pr * nV + v) * (S * 16) + threadIdx.x);
+  // W_v of every slice into staging buffer sb (readers)
+  auto stage_window = [&](int v, int sb) {
+    if (threadIdx.x < S * 16)
+      ((uint4*)(sW + sb * S * 64))[threadIdx.x] = __ldg(rhat + (pr * nV + v) * (S * 16) + threadIdx.x);
   };
-  // the shifted copies of sW into Hankel buffer hb: line m * 8 + rho of slice
-  // j holds W_j[8 m + rho .. + 7] (m < 15: the MMAs read row group + column
-  // group <= 14); lines in order, so eight threads store 128 consecutive bytes
-  auto build_hankel = [&](int hb) {
+  // the shifted copies of staging buffer sb into Hankel buffer hb: line
+  // m * 8 + rho of slice j holds W_j[8 m + rho .. + 7] (m < 15: the MMAs read
+  // row group + column group <= 14); lines in order, so eight threads store
+  // 128 consecutive bytes
+  auto build_hankel = [&](int hb, int sb) {
     unsigned char* base = sH + hb * (S * HANKEL);
-    for (int e = threadIdx.x; e < S * 120; e += THREADS) {
+    const uint32_t* wsrc = sW + sb * S * 64;
+    for (int e = threadIdx.x; e < S * 120; e += READERS) {
       const int j = e / 120, line = e - j * 120, m = line >> 3, rho = line & 7;
-      const uint32_t* src = sW + j * 64 + 4 * m + (rho >> 1);
+      const uint32_t* src = wsrc + j * 64 + 4 * m + (rho >> 1);
       const uint32_t sft = 16u * (rho & 1);
       const uint32_t x0 = src[0], x1 = src[1], x2 = src[2], x3 = src[3], x4 = src[4];
       *(uint4*)(base + j * HANKEL + line * 16) = make_uint4(__funnelshift_r(x0, x1, sft), __funnelshift_r(x1, x2, sft),
                                                             __funnelshift_r(x2, x3, sft), __funnelshift_r(x3, x4, sft));
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   };
-  if (v_lo <= v_hi) stage_window(v_lo);
-  __syncthreads();
-  if (v_lo <= v_hi) build_hankel(v_lo & 1);
+  // A window for the chunk of steps starting at v: block rows ub .. ub +
+  // WROWS - 1 (zero outside a), every slice and chunk; step v' reads rows
+  // w0 - v' .. w0 - v' + 127
+  auto load_window = [&](int v) {
+    const int ub = w0 - v - (V - 1);
+    for (int e = threadIdx.x; e < S * 8 * WROWS; e += READERS) {
+      const int sk = e / WROWS, r = e - sk * WROWS;
+      const int u = ub + r;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (u >= 0 && u < nA) val = __ldg(ahat + (pr * (S * 8) + sk) * (int64_t)nA + u);
+      *(uint4*)(sA + sk * STRIP + r * 16) = val;
+    }
+  };
+
+  // Prologue (readers): the operands of steps 0 and 1.
+  if (reader && nsteps > 0) {
+    stage_window(v_lo, 0);
+    if (nsteps > 1) stage_window(v_lo + 1, 1);
+    load_window(v_lo);
+  }
+  if (reader) readers_sync();
+  if (reader && nsteps > 0) {
+    build_hankel(0, 0);
+    if (nsteps > 1) build_hankel(1, 1);
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base;
-  uint32_t phase = 0;
-  bool failed = false;
 
-  for (int v = v_lo; v <= v_hi; ++v) {
-    const int step = v - v_lo;
-    if (step % V == 0) {
-      // A window: block rows ub .. ub + WROWS - 1 (zero outside a), every
-      // slice and chunk; step v reads rows w0 - v .. w0 - v + 127
-      const int ub = w0 - v - (V - 1);
-      for (int e = threadIdx.x; e < S * 8 * WROWS; e += THREADS) {
-        const int sk = e / WROWS, r = e - sk * WROWS;
-        const int u = ub + r;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (u >= 0 && u < nA) val = __ldg(ahat + (pr * (S * 8) + sk) * (int64_t)nA + u);
-        *(uint4*)(sA + sk * STRIP + r * 16) = val;
+  if (!reader) {
+    // The issuer.  Step k: slice i of the A window (row of block w0 - v at
+    // window row V - 1 - k % V) times slice j of Hankel buffer k & 1; the
+    // exact groups into columns 0 .. 255, the combined group's halves into
+    // columns 256 + 128 (k & 1) + 0 / 64.
+    if (lane == 0) {
+      int kis = -1;  // the last step issued
+      for (int k = 0; k < nsteps; ++k) {
+        if (k >= 1 && !mbar_wait(ready, (k - 1) & 1)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int roff = (V - 1) - k % V;
+        const uint64_t dA = sdesc(smem_u32(sA) + 16u * roff, STRIP, 128);
+        const uint64_t dB = sdesc(smem_u32(sH) + (uint32_t)((k & 1) * S * HANKEL), 128, 128);
+        issue_mmas<S, 0>(tmem, dA, dB);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(full_x));
+        if (k >= 2 && !mbar_wait(free_y(k & 1), ((k - 2) >> 1) & 1)) {
+          kis = -2 - k;  // the exact groups of step k are in flight
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t tc = tmem + (uint32_t)((NACC - 1) * T + NCOMB * T * (k & 1));
+        issue_mmas<S, 1>(tc, dA, dB);
+        issue_mmas<S, 2>(tc + T, dA, dB);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(full_y(k & 1)));
+        kis = k;
       }
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncthreads();
+      if (kis != nsteps - 1) {
+        s_fail[2] = 1;
+        // the MMAs in flight (the last commit to each barrier), bounded
+        const int kx = kis >= 0 ? kis : -2 - kis;  // the last step with exact groups issued
+        const int ky = kis >= 0 ? kis : kx - 1;    // the last step with its combined group issued
+        if (kx >= 0) mbar_wait(full_x, kx & 1);
+        if (ky >= 0) mbar_wait(full_y(ky & 1), (ky >> 1) & 1);
+        if (ky >= 1) mbar_wait(full_y((ky - 1) & 1), ((ky - 1) >> 1) & 1);
+      }
     }
-    if (threadIdx.x == 0) {
-      // the exact groups (i + j <= 3) first, committed to barx, then the
-      // combined group to bary: the exact accumulators are read out while
-      // the tensor cores run the rest.  Fully unrolled: every operand offset
-      // and accumulate flag is a constant added to two base descriptors.
+    __syncwarp();
+  } else {
+    for (int k = 0; k < nsteps; ++k) {
+      const int v = v_lo + k;
+      const bool next = k + 1 < nsteps;
+      const bool reload = next && (k + 1) % V == 0;
+      // this row's step: C 2^E units of 2^F, E = alpha + beta - 40 - F <= P
+      const int u = w - v;
+      const int E = (w < nW && u >= 0 && u < nA) ? __ldg(al + u) + __ldg(be + v) - 40 - F : -1000;
+      const int sh = min(63, P - E);
+      const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0;
+      if (!mbar_wait(full_x, k & 1)) s_fail[k & 1] = 1;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int roff = (V - 1) - step % V;  // window row of block w0 - v
-      const uint64_t dA = sdesc(smem_u32(sA) + 16u * roff, STRIP, 128);
-      const uint64_t dB = sdesc(smem_u32(sH) + (uint32_t)((v & 1) * S * HANKEL), 128, 128);
-      issue_mmas<S, 0>(tmem, dA, dB);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barx));
-      issue_mmas<S, 1>(tmem, dA, dB);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bary));
-    }
-    // the next step's operand, built while the tensor cores work (its buffer
-    // was last read by the previous step's MMAs, which have completed)
-    if (v < v_hi) stage_window(v + 1);
-    __syncthreads();
-    if (v < v_hi) build_hankel((v + 1) & 1);
-    // this row's step: C 2^E units of 2^F, E = alpha + beta - 40 - F <= P
-    const int u = w - v;
-    const int E = (w < nW && u >= 0 && u < nA) ? __ldg(al + u) + __ldg(be + v) - 40 - F : -1000;
-    const int sh = min(63, P - E);
-    const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0;
-    if (!mbar_wait(barx, phase)) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      uint32_t r[NACC - 1][16];
-#pragma unroll
-      for (int g = 0; g < NACC - 1; ++g)
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * T + 32 * h + 16 * half), r[g]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        int d[NACC - 1];
+      for (int qc = 0; qc < 4; ++qc) {
+        uint32_t r[NACC - 1][8];
 #pragma unroll
         for (int g = 0; g < NACC - 1; ++g)
-          d[g] = __float_as_int(fmaf(__uint_as_float(r[g][c]), __int_as_float((127 + 7 * g) << 23), 12582912.0f)) -
-                 0x4B400000;
-        const long long C = (long long)d[0] * (1ll << 28) + (long long)d[1] * (1ll << 21) +
-                            (long long)d[2] * (1ll << 14) + (long long)d[3] * 128;
-        acc[16 * half + c] += ((C << P) + rnd) >> sh;
-      }
-    }
-    if (!mbar_wait(bary, phase)) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    {
-      uint32_t r[2][16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((NACC - 1) * T + 32 * h), r[0]);
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((NACC - 1) * T + 32 * h + 16), r[1]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * T + 32 * h + 8 * qc), r[g]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const long long d = __float_as_int(fmaf(__uint_as_float(r[c >> 4][c & 15]),
-                                                __int_as_float((127 + 7 * (NACC - 1)) << 23), 12582912.0f)) -
-                            0x4B400000;
-        acc[c] += ((d << P) + rnd) >> sh;
+        for (int c = 0; c < 8; ++c) {
+          int d[NACC - 1];
+#pragma unroll
+          for (int g = 0; g < NACC - 1; ++g)
+            d[g] = __float_as_int(fmaf(__uint_as_float(r[g][c]), __int_as_float((127 + 7 * g) << 23), 12582912.0f)) -
+                   0x4B400000;
+          const long long C = (long long)d[0] * (1ll << 28) + (long long)d[1] * (1ll << 21) +
+                              (long long)d[2] * (1ll << 14) + (long long)d[3] * 128;
+          acc[8 * qc + c] += ((C << P) + rnd) >> sh;
+        }
       }
-    }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (s_fail) {
-      failed = true;
-      break;
+      if (reload) {
+        // the next chunk's window: every MMA reading the current one is done
+        if (!mbar_wait(full_y(k & 1), (k >> 1) & 1)) s_fail[k & 1] = 1;
+        load_window(v + 1);
+      }
+      if (next) {
+        // step k + 1: its window (reloaded above) and Hankel operand (built
+        // in the previous iteration) in place, step k's exact groups read
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(ready);
+      }
+      if (k + 2 < nsteps) stage_window(v + 2, k & 1);
+      if (!mbar_wait(full_y(k & 1), (k >> 1) & 1)) s_fail[k & 1] = 1;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int qc = 0; qc < 4; ++qc) {
+        uint32_t r[NCOMB][8];
+#pragma unroll
+        for (int kk = 0; kk < NCOMB; ++kk)
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) +
+                       (uint32_t)((NACC - 1) * T + NCOMB * T * (k & 1) + T * kk + 32 * h + 8 * qc),
+                   r[kk]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          long long d = 0;
+#pragma unroll
+          for (int kk = 0; kk < NCOMB; ++kk)
+            d += __float_as_int(fmaf(__uint_as_float(r[kk][c]), __int_as_float((127 + 7 * (NACC - 1)) << 23),
+                                     12582912.0f)) -
+                 0x4B400000;
+          acc[8 * qc + c] += ((d << P) + rnd) >> sh;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(free_y(k & 1));
+      readers_sync();
+      // (a reader past this check may set the next iteration's slot before a
+      // slower one reads this one: separate slots keep the decision uniform)
+      if (s_fail[k & 1]) break;
+      // step k + 2's Hankel operand into buffer k & 1: step k's MMAs are done
+      if (k + 2 < nsteps) build_hankel(k & 1, k & 1);
     }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  const bool failed = s_fail[0] | s_fail[1] | s_fail[2];
   if (failed) {
     if (threadIdx.x == 0) atomicExch(status, 1);
-    mbar_wait(bary, phase ^ 1);  // the MMAs still in flight, bounded
-  } else if (w < nW) {
+  } else if (reader && w < nW) {
     double* o = out + pr * out_pitch;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -475,8 +562,6 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
