@@ -216,8 +216,17 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
  *       N's value) | S (the slot read, bits 2..7) | D (the parent's slot,
  *       8..13) | LEAF (14) | FIRST (15: the last node is its parent's first
  *       child) | UNIFORM (16: one power along a chain) | PID (17..31: table
- *       position of the outgoing edge's power); word 1 = length - 1;
- *       word 2 = first node; word 3 = stream offset.
+ *       position of the outgoing edge's power; 0x7FFF: recomputed, see word
+ *       2); word 1 = length - 1 (bits 0..7), and for a floating-point
+ *       Balanced block of 17 to 22 nodes f = the scheme's split of its run
+ *       (bits 8..15) and the table position of x^f (16..31): the run is
+ *       T(b) + T(a) x^f, its coefficients stored as the runs a and b, each
+ *       from a multiple of 4 elements; word 2 = first node, or for PID 0x7FFF
+ *       (a block or partial block of a large Balanced tree whose edge power
+ *       few ops read) base | m << 15 | (d mod 2^m) << 19: the edge power x^d
+ *       is rebuilt from the table entry at position base (0x7FFF: x) by m
+ *       steps of squaring and, where the bit of d is set, multiplying by x
+ *       (the power program's own steps); word 3 = stream offset.
  *   op_a_node, op_b_node [nops]: node whose coefficient is the op's leaf value
  *       (single-node ops) / initialises the parent's slot when FIRST; -1 = 0.
  *   stream [stream_len]: node whose coefficient sits in each slot of the

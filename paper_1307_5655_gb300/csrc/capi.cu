@@ -220,6 +220,7 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
   o.root_lh = t->ops_root_lh;
   o.root_pid = t->ops_root_pid;
   o.pos_x1 = t->ops_pos_x1;
+  o.ext = t->ops_ext;
   for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t root = t->nnodes - 1;
   switch (dt) {
@@ -699,6 +700,7 @@ int fp_eval_rns(const fp_tree* t, const uint64_t* points, int64_t npts, uint64_t
   o.root_lh = t->ops_root_lh;
   o.root_pid = t->ops_root_pid;
   o.pos_x1 = t->ops_pos_x1;
+  o.ext = t->ops_ext;
   for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t strides[5] = {(int64_t)t->nvars * npts, npts, t->nnodes - 1, (int64_t)t->ops.size(),
                               t->dev.st_rns_pitch};

@@ -139,7 +139,7 @@ int ops_layout(fp_tree* t) {
   std::vector<int64_t> reads(nops, -1);
   for (size_t i = 0; i < nops; ++i) {
     const uint32_t x = t->ops[i].x, kind = x & 3u;
-    const int64_t j0 = t->ops[i].z, j1 = j0 + t->ops[i].y;
+    const int64_t j0 = t->ops[i].z, j1 = j0 + (t->ops[i].y & 255u);
     const bool leaf = (x >> kOpLeaf) & 1u;
     if (kind == kOpPartial) reads[i] = j1;
     else if (kind != kOpBlock && !leaf) reads[i] = j0;
@@ -163,10 +163,63 @@ int ops_layout(fp_tree* t) {
   std::vector<uint8_t> live(np, 0), tmpl(np, 0), needed(np, 0);
   for (size_t i = 0; i < nops; ++i) {
     live[t->ops[i].x >> kOpPid] = 1;
+    if ((t->ops[i].y >> 8) & 255u) live[t->ops[i].y >> 16] = 1;  // x^f of a two-part block
     if ((t->ops[i].x & 3u) == kOpChain)
-      for (int64_t j = t->ops[i].z; j < (int64_t)t->ops[i].z + t->ops[i].y; ++j) live[t->ctrl[j] >> kCtrlPid] = 1;
+      for (int64_t j = t->ops[i].z; j < (int64_t)t->ops[i].z + (t->ops[i].y & 255u); ++j)
+        live[t->ctrl[j] >> kCtrlPid] = 1;
   }
   if (t->root_pid >= 0) live[t->root_pid] = 1;
+  // Balanced trees: edge powers of the block variable that few ops read (the
+  // top levels: one partial block reads x^5003) stay out of the table when
+  // the table is large enough to bound the points resident per SM: the block
+  // or partial block recomputes its edge power from the nearest binary prefix
+  // x^(d >> m) that is kept, or from x itself (in registers), by the power
+  // program's own steps, so the value is the same.  A power is recomputed
+  // while its ops x steps stay within kRecomputeCost (prefixes are decided
+  // first: powers in increasing degree).
+  std::vector<uint8_t> rare(np, 0);
+  std::vector<uint32_t> redge(np, 0);  // the recompute word of a rare power
+  int32_t nlive0 = 0;
+  for (size_t k = 0; k < np; ++k) nlive0 += live[k];
+  if (t->block_scheme == FP_SCHEME_B && nlive0 + nslot >= kRecomputeMinEntries) {
+    const int32_t bv = t->nvars - 1;
+    std::vector<int64_t> uses(np, 0);
+    std::vector<uint8_t> pinned(np, 0);  // read by chains, single nodes, joins or the root
+    for (size_t i = 0; i < nops; ++i) {
+      const uint32_t kind = t->ops[i].x & 3u, pid = t->ops[i].x >> kOpPid;
+      if (kind == kOpBlock || kind == kOpPartial) uses[pid]++;
+      else pinned[pid] = 1;
+      if ((t->ops[i].y >> 8) & 255u) pinned[t->ops[i].y >> 16] = 1;
+      if (kind == kOpChain)
+        for (int64_t j = t->ops[i].z; j < (int64_t)t->ops[i].z + (t->ops[i].y & 255u); ++j)
+          pinned[t->ctrl[j] >> kCtrlPid] = 1;
+    }
+    if (t->root_pid >= 0) pinned[t->root_pid] = 1;
+    std::map<int64_t, size_t> of_deg;  // degree -> power id, block variable (increasing degree)
+    for (size_t k = 0; k < np; ++k)
+      if (t->pow_var[k] == bv) of_deg[t->pow_deg[k]] = k;
+    for (const auto& [d, k] : of_deg) {
+      if (!live[k] || pinned[k] || uses[k] == 0) continue;
+      for (int m = 1; m <= kRecomputeMaxSteps && (d >> m) >= 1; ++m) {
+        const int64_t b = d >> m;
+        uint32_t base;
+        if (b == 1) {
+          base = 0x7FFFu;
+        } else {
+          const auto it = of_deg.find(b);
+          if (it == of_deg.end() || !live[it->second] || rare[it->second]) continue;
+          base = (uint32_t)it->second;  // a power id for now, its position below
+        }
+        if (uses[k] * m <= kRecomputeCost) {
+          rare[k] = 1;
+          redge[k] = base | (uint32_t)m << 15 | (uint32_t)(d & ((1ll << m) - 1)) << 19;
+        }
+        break;  // the nearest kept prefix decides
+      }
+    }
+    for (size_t k = 0; k < np; ++k)
+      if (rare[k]) live[k] = 0;
+  }
   if (t->block_scheme)
     for (int d = 1; d <= kMaxBlock; ++d)
       if (t->pid_pow[d] >= 0) tmpl[t->pid_pow[d]] = 1;
@@ -226,10 +279,19 @@ int ops_layout(fp_tree* t) {
   // op records in this layout
   for (size_t i = 0; i < nops; ++i) {
     uint32_t x = t->ops[i].x;
-    const int64_t j1 = (int64_t)t->ops[i].z + t->ops[i].y;
+    const int64_t j1 = (int64_t)t->ops[i].z + (t->ops[i].y & 255u);
+    if ((t->ops[i].y >> 8) & 255u) t->ops[i].y = (t->ops[i].y & 0xFFFFu) | (uint32_t)pos[t->ops[i].y >> 16] << 16;
     const uint32_t S = reads[i] >= 0 ? (uint32_t)olh[reads[i]] : 0u;
     const uint32_t D = (uint32_t)olh[t->parent[j1]];
-    const uint32_t P = (uint32_t)pos[x >> kOpPid];
+    const uint32_t pid = x >> kOpPid;
+    uint32_t P;
+    if (rare[pid]) {  // recomputed: z carries the base's position, m and the low bits
+      const uint32_t base = redge[pid] & 0x7FFFu;
+      t->ops[i].z = (redge[pid] & ~0x7FFFu) | (base == 0x7FFFu ? 0x7FFFu : (uint32_t)pos[base]);
+      P = kPidRecompute;
+    } else {
+      P = (uint32_t)pos[pid];
+    }
     x &= ~((63u << kOpS) | (63u << kOpD) | (0x7FFFu << kOpPid));
     t->ops[i].x = x | S << kOpS | D << kOpD | P << kOpPid;
   }
@@ -241,6 +303,9 @@ int ops_layout(fp_tree* t) {
   t->ops_root_lh = root_h;
   t->ops_root_pid = t->root_pid >= 0 ? pos[t->root_pid] : -1;
   t->ops_pos_x1 = t->pid_x1 >= 0 && live[t->pid_x1] ? pos[t->pid_x1] : -1;
+  t->ops_ext = 0;
+  for (size_t i = 0; i < nops; ++i)
+    if (((t->ops[i].y >> 8) & 255u) || (t->ops[i].x >> kOpPid) == kPidRecompute) t->ops_ext = 1;
   // template powers exist only for trees with blocks (E, B): without, their
   // positions may have been reused by temporaries, so none is reported
   for (int d = 0; d <= kMaxBlock; ++d)
@@ -410,8 +475,20 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
     const int bv = nvars - 1;
     const bool blocks = scheme == FP_SCHEME_E || scheme == FP_SCHEME_B;
     // residues are exact, so their kernels run a block as one loop over its
-    // run (any length); the floating-point kernels use compiled templates
-    const int64_t max_block = coeff_type == FP_MODP ? kMaxExactBlock : kMaxBlock;
+    // run (any length); the floating-point kernels use compiled templates of
+    // at most kMaxBlock nodes, and a longer run (up to kMaxTwoPartBlock) as its
+    // two parts under the scheme's split, joined with x^f from the table
+    const bool exact_blocks = coeff_type == FP_MODP;
+    const int64_t max_block = exact_blocks ? kMaxExactBlock : kMaxTwoPartBlock;
+    // (blocks of 13 to 16 nodes already amortise an op: two such parts
+    // measured slower, so only the Balanced scheme takes longer runs, and
+    // only up to kMaxTwoPartBlock nodes, i.e. parts of at most 11)
+    auto split_power_ok = [&](int64_t s) {  // a run of s nodes can form one op
+      if (exact_blocks || s <= kMaxBlock) return true;
+      if (scheme != FP_SCHEME_B || s > kMaxTwoPartBlock) return false;
+      const int64_t f = split_count(scheme, nullptr, 0, s - 1);
+      return f >= 1 && f <= kMaxBlock && s - f <= kMaxBlock && pid.count({bv, (int32_t)f}) > 0;
+    };
     // nodes j0..r have consecutive exponents of x_bv and equal exponents of the others
     auto dense_run = [&](int64_t j0, int64_t r) {
       const int32_t* er = &t->node_e[r * nvars];
@@ -432,7 +509,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
       std::vector<uint8_t> qual(N, 0), in_block(N, 0);
       for (int64_t r = 0; r + 1 < N; ++r) {
         const int64_t s = size[r];
-        qual[r] = s >= 2 && s <= max_block && r - s + 1 < (1ll << 32) && dense_run(r - s + 1, r);
+        qual[r] = s >= 2 && s <= max_block && r - s + 1 < (1ll << 32) && split_power_ok(s) && dense_run(r - s + 1, r);
       }
       // subtrees inside a maximal qualifying subtree (nodes in index order:
       // a subtree is the contiguous range ending at its root)
@@ -449,8 +526,8 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
         while (pos >= 0 && t->parent[pos] == r && s + size[pos] <= max_block) {
           s += size[pos];
           pos -= size[pos];
-          if (dense_run(r - s + 1, r)) best = s;
-          else break;
+          if (!dense_run(r - s + 1, r)) break;
+          if (split_power_ok(s)) best = s;
         }
         s = best;
         if (s < 2) continue;
@@ -476,15 +553,25 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
         for (int64_t j = j0; j < j1; ++j) uni = uni && pid_of(j) == pid_of(j0);
         x |= (uni ? 1u : 0u) << kOpUniform;
       }
+      // a floating-point block longer than kMaxBlock: the split f of its run,
+      // the power x^f, and its coefficients as two aligned runs (a, then b)
+      const int64_t len = j1 - j0 + 1;
+      const bool two_part = (kind == kOpBlock || kind == kOpPartial) && !exact_blocks && len > kMaxBlock;
+      const int64_t f = two_part ? split_count(scheme, nullptr, 0, len - 1) : 0;
       uint32_t off = 0;
       if (kind != kOpNode) {
         while (t->stream.size() % kStreamAlign) t->stream.push_back(-1);
         off = (uint32_t)t->stream.size();
-        for (int64_t j = j0; j <= j1; ++j) t->stream.push_back(j);
+        for (int64_t j = j0; j <= j1; ++j) {
+          if (two_part && j == j1 - f + 1)
+            while ((t->stream.size() - off) % kStreamAlign) t->stream.push_back(-1);
+          t->stream.push_back(j);
+        }
       }
       uint4 w;
       w.x = x;
-      w.y = (uint32_t)(j1 - j0);
+      w.y = (uint32_t)(len - 1);
+      if (two_part) w.y |= (uint32_t)f << 8 | pid.at({bv, (int32_t)f}) << 16;
       w.z = (uint32_t)j0;
       w.w = off;
       t->ops.push_back(w);

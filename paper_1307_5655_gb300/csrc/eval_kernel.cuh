@@ -20,6 +20,7 @@
 //   children's sum and then multiplies; the result is the same polynomial).
 //   IV64 keeps the paper's order literally (see the interval policy).
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cstring>
@@ -611,7 +612,13 @@ struct OpArgs {
   int root_lh, root_pid;      // root slot, position of the root's power (-1: none)
   int pos_x1;                 // position of x_b (b: the blocks' variable) among the walk's powers (-1: none)
   int pid_pow[kMaxBlock + 1];  // position of x^d for the block templates (-1: absent)
+  int ext;                     // Balanced tree with two-part blocks or recomputed edge powers
 };
+
+// The kernels of a Balanced tree whose schedule has two-part blocks or
+// recomputed edge powers (OpArgs::ext) are a template of their own: the code
+// for them slows the plain Balanced kernel down even where it never runs.
+constexpr int kSchemeBExt = 0x100 | FP_SCHEME_B;
 
 template <int SCHEME>
 __host__ __device__ constexpr int scheme_split(int n) {
@@ -658,16 +665,36 @@ __device__ __forceinline__ typename A::val block_eval(const typename A::coef (&c
   }
 }
 
+// coefficients st[off + 4q .. off + 4q + 3] (off is a multiple of 4)
+template <class C>
+__device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]) {
+  if constexpr (sizeof(C) == 8) {
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(st + off) + 2 * q;
+    const ulonglong2 u0 = __ldg(v), u1 = __ldg(v + 1);
+    memcpy(&c[0], &u0.x, 8); memcpy(&c[1], &u0.y, 8); memcpy(&c[2], &u1.x, 8); memcpy(&c[3], &u1.y, 8);
+  } else {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(st + off) + q);
+    memcpy(&c[0], &u.x, 4); memcpy(&c[1], &u.y, 4); memcpy(&c[2], &u.z, 4); memcpy(&c[3], &u.w, 4);
+  }
+}
+
 // The value of the block's last node N is its coefficient; for a partial
 // block it is N's slot (slot[p]).  Types with A::kSlotAtEnd evaluate the run
 // with 0 for N and add the slot afterwards (the slot's load then overlaps the
-// block's arithmetic; one add more), the others start from the slot.
+// block's arithmetic; one add more), the others start from the slot.  Each
+// length loads its own ceil(L / 4) coefficient vectors of the op's run.
 template <class A, int SCHEME, int PPT>
-__device__ __forceinline__ void block_dispatch(int len, bool partial, const typename A::coef (&c)[kMaxBlock],
+__device__ __forceinline__ void block_dispatch(int len, bool partial, const typename A::coef* st, int64_t off,
                                                const typename A::pw (&xp)[PPT][kMaxBlock + 1],
                                                const typename A::val (&slot)[PPT], typename A::val (&v)[PPT]) {
+  typename A::coef c[kMaxBlock];
 #define FP_BLOCK_CASE(L)                                                                      \
   case L:                                                                                     \
+    _Pragma("unroll") for (int q = 0; q < (L + 3) / 4; ++q) {                                 \
+      typename A::coef c4[4];                                                                 \
+      load4(st, off, q, c4);                                                                  \
+      _Pragma("unroll") for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];                     \
+    }                                                                                         \
     _Pragma("unroll") for (int p = 0; p < PPT; ++p) {                                         \
       if constexpr (A::kSlotAtEnd) {                                                          \
         const typename A::val base = A::from_coef(partial ? typename A::coef(0) : c[L - 1]);  \
@@ -680,7 +707,7 @@ __device__ __forceinline__ void block_dispatch(int len, bool partial, const type
     }                                                                                         \
     break;
   switch (len) {
-    FP_BLOCK_CASE(2) FP_BLOCK_CASE(3) FP_BLOCK_CASE(4) FP_BLOCK_CASE(5) FP_BLOCK_CASE(6)
+    FP_BLOCK_CASE(1) FP_BLOCK_CASE(2) FP_BLOCK_CASE(3) FP_BLOCK_CASE(4) FP_BLOCK_CASE(5) FP_BLOCK_CASE(6)
     FP_BLOCK_CASE(7) FP_BLOCK_CASE(8) FP_BLOCK_CASE(9) FP_BLOCK_CASE(10) FP_BLOCK_CASE(11)
     FP_BLOCK_CASE(12) FP_BLOCK_CASE(13) FP_BLOCK_CASE(14) FP_BLOCK_CASE(15) FP_BLOCK_CASE(16)
     default: break;
@@ -700,19 +727,6 @@ __device__ __forceinline__ void load_rec(const OpRec<C>* r, uint4& h, C& a, C& b
     const uint2 q = __ldg(reinterpret_cast<const uint2*>(r) + 2);
     memcpy(&a, &q.x, 4);
     memcpy(&b, &q.y, 4);
-  }
-}
-
-// coefficients st[off + 4q .. off + 4q + 3] (off is a multiple of 4)
-template <class C>
-__device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]) {
-  if constexpr (sizeof(C) == 8) {
-    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(st + off) + 2 * q;
-    const ulonglong2 u0 = __ldg(v), u1 = __ldg(v + 1);
-    memcpy(&c[0], &u0.x, 8); memcpy(&c[1], &u0.y, 8); memcpy(&c[2], &u1.x, 8); memcpy(&c[3], &u1.y, 8);
-  } else {
-    const uint4 u = __ldg(reinterpret_cast<const uint4*>(st + off) + q);
-    memcpy(&c[0], &u.x, 4); memcpy(&c[1], &u.y, 4); memcpy(&c[2], &u.z, 4); memcpy(&c[3], &u.w, 4);
   }
 }
 
@@ -767,7 +781,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     const int S = (int)((h.x >> kOpS) & 63u), D = (int)((h.x >> kOpD) & 63u);
     const bool leaf = (h.x >> kOpLeaf) & 1u, first = (h.x >> kOpFirst) & 1u;
     const int pid = (int)(h.x >> kOpPid);
-    const int len = (int)h.y + 1;
+    const int len = (int)(h.y & 255u) + 1;
     const int64_t off = (int64_t)h.w;
     V v[PPT];
     if (kind == kOpNode) {
@@ -824,15 +838,6 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
       for (int p = 0; p < PPT; ++p) v[p] = A::mad(v[p], xp[p][1], partial ? acc[(S * PPT + p) * TPB + tid] : cl);
     } else {
       if constexpr (SCHEME != 0) {
-        C c[kMaxBlock];
-#pragma unroll
-        for (int q = 0; q < kMaxBlock / 4; ++q) {
-          C c4[4];
-          if (4 * q < len) load4(st, off, q, c4);
-          else c4[0] = c4[1] = c4[2] = c4[3] = C(0);
-#pragma unroll
-          for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];
-        }
         // a partial block's last node N starts from its slot (c_N plus N's
         // earlier children)
         const bool partial = kind == kOpPartial;
@@ -841,15 +846,67 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
 #pragma unroll
           for (int p = 0; p < PPT; ++p) slot[p] = acc[(S * PPT + p) * TPB + tid];
         }
-        block_dispatch<A, SCHEME, PPT>(len, partial, c, xp, slot, v);
+        // Balanced trees: a run longer than kMaxBlock (f > 0) is T(b) +
+        // T(a) x^f, b its f lowest nodes (ending at the op's last node), a
+        // the others; each part is a run of at most kMaxBlock nodes stored
+        // from an aligned offset, evaluated by the same templates (one loop,
+        // one copy of the code).  Other schemes have single-part blocks only.
+        if constexpr (SCHEME != kSchemeBExt) {
+          block_dispatch<A, SCHEME, PPT>(len, partial, st, off, xp, slot, v);
+        } else {
+        const int f = (int)((h.y >> 8) & 255u);
+        V va[PPT];
+#pragma unroll 1
+        for (int part = f > 0 ? 0 : 1; part < 2; ++part) {
+          const bool lower = part == 1;
+          const int plen = lower ? (f > 0 ? f : len) : len - f;
+          const int64_t poff = lower && f > 0 ? off + ((len - f + kStreamAlign - 1) & ~(kStreamAlign - 1)) : off;
+          V w[PPT];
+          block_dispatch<A, SCHEME, PPT>(plen, lower && partial, st, poff, xp, slot, w);
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) {
+            if (lower) v[p] = w[p];
+            else va[p] = w[p];
+          }
+        }
+        if (f > 0) {
+          const int cp = (int)(h.y >> 16);
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) v[p] = A::mad(va[p], pw[(cp * PPT + p) * TPB + tid], v[p]);
+        }
+        }
       }
     }
-    // the outgoing edge of the op's last node
+    // the outgoing edge of the op's last node; its power from the table, or
+    // (kPidRecompute: a block of a Balanced tree whose power few ops read)
+    // recomputed from a kept prefix x^(d >> m), or x, by the power program's
+    // steps: square, then times x where the bit of d is set
+    if (SCHEME != kSchemeBExt || pid != (int)kPidRecompute) {
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      V* dst = &acc[(D * PPT + p) * TPB + tid];
-      const V init = first ? A::from_coef(b) : *dst;
-      *dst = A::mad(v[p], pw[(pid * PPT + p) * TPB + tid], init);
+      for (int p = 0; p < PPT; ++p) {
+        V* dst = &acc[(D * PPT + p) * TPB + tid];
+        const V init = first ? A::from_coef(b) : *dst;
+        *dst = A::mad(v[p], pw[(pid * PPT + p) * TPB + tid], init);
+      }
+    } else if constexpr (SCHEME == kSchemeBExt) {
+      const int base = (int)(h.z & 0x7FFFu), m = (int)((h.z >> 15) & 15u);
+      const uint32_t bits = h.z >> 19;
+      W xe[PPT];
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) xe[p] = base == 0x7FFF ? xp[p][1] : pw[(base * PPT + p) * TPB + tid];
+      for (int i = m - 1; i >= 0; --i) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+          xe[p] = A::square(xe[p]);
+          if ((bits >> i) & 1u) xe[p] = A::mulx(xe[p], xp[p][1]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        V* dst = &acc[(D * PPT + p) * TPB + tid];
+        const V init = first ? A::from_coef(b) : *dst;
+        *dst = A::mad(v[p], xe[p], init);
+      }
     }
   }
 
@@ -955,11 +1012,41 @@ inline int sm_count() {
   return cached[dev];
 }
 
-// Small grids balance badly over the SMs (a grid of 3.4 blocks per SM runs
-// as long as its SMs with 4): one point per thread and fewer than 16 blocks
-// of kTPB threads per SM takes narrower blocks (64, or 32 under 4 per SM), so
-// the remainder is a smaller fraction of each SM's share.  Results do not
-// depend on the block width.
+// registers per thread of a kernel (cached per instantiation)
+template <class A, int PPT, int SCHEME, int TPB>
+int ops_kernel_regs() {
+  static int regs = 0;
+  if (!regs) {
+    cudaFuncAttributes fa;
+    regs = cudaFuncGetAttributes(&fa, eval_ops_kernel<A, PPT, SCHEME, TPB>) == cudaSuccess && fa.numRegs > 0
+               ? fa.numRegs
+               : 255;
+    cudaGetLastError();
+  }
+  return regs;
+}
+
+// Points resident per SM with blocks of tpb threads: shared memory (228 KB
+// per SM, 1 KB of it reserved per block), registers (64 K per SM, allocated
+// per warp in units of 256), at most 32 blocks and 2048 threads per SM.
+inline int64_t ops_resident_points(size_t bytes_per_point, int tpb, int ppt, int regs) {
+  const size_t blk = bytes_per_point * (size_t)tpb * ppt;
+  if (blk > kSmemMax) return 0;
+  const int64_t by_smem = (int64_t)((228 * 1024) / (blk + 1024));
+  const int64_t warp_regs = ((int64_t)regs * 32 + 255) / 256 * 256;
+  const int64_t by_regs = 65536 / (warp_regs * (tpb / 32));
+  const int64_t nb = std::min<int64_t>(std::min<int64_t>(by_smem, by_regs), std::min<int64_t>(32, 2048 / tpb));
+  return nb * tpb * ppt;
+}
+
+// Block width.  Small grids balance badly over the SMs (a grid of 3.4 blocks
+// per SM runs as long as its SMs with 4): one point per thread and fewer than
+// 16 blocks of kTPB threads per SM takes narrower blocks (64, or 32 under 4
+// per SM), so the remainder is a smaller fraction of each SM's share.  Large
+// grids take 64-thread blocks where more points stay resident per SM (the
+// per-point table bounds the blocks per SM: a 47 KB block of 128 threads x 2
+// points leaves four per SM, a 23.5 KB one of 64 threads nine).  Results do
+// not depend on the block width.
 template <class A, int PPT, int SCHEME>
 cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
   if constexpr (PPT == 1) {
@@ -967,6 +1054,12 @@ cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) 
     const int64_t sms = sm_count();
     if (blocks < 4 * sms) return launch_eval_ops_tpb<A, PPT, SCHEME, 32>(a, o, s);
     if (blocks < 16 * sms) return launch_eval_ops_tpb<A, PPT, SCHEME, 64>(a, o, s);
+  }
+  if constexpr (PPT <= 2) {
+    const size_t per_point = sizeof(typename A::pw) * (size_t)o.entries;
+    if (ops_resident_points(per_point, 64, PPT, ops_kernel_regs<A, PPT, SCHEME, 64>()) >
+        ops_resident_points(per_point, kTPB, PPT, ops_kernel_regs<A, PPT, SCHEME, kTPB>()))
+      return launch_eval_ops_tpb<A, PPT, SCHEME, 64>(a, o, s);
   }
   return launch_eval_ops_tpb<A, PPT, SCHEME, kTPB>(a, o, s);
 }
@@ -979,7 +1072,8 @@ cudaError_t launch_eval_fused(const EvalArgs& a, const OpArgs& o, int scheme, cu
   if (variant == 1 && !ops_ok) return cudaErrorInvalidValue;
   if (variant != 2 && ops_ok) {
     if (scheme == FP_SCHEME_E) return launch_eval_ops<A, PPT_OPS, FP_SCHEME_E>(a, o, s);
-    if (scheme == FP_SCHEME_B) return launch_eval_ops<A, PPT_OPS, FP_SCHEME_B>(a, o, s);
+    if (scheme == FP_SCHEME_B)
+      return o.ext ? launch_eval_ops<A, PPT_OPS, kSchemeBExt>(a, o, s) : launch_eval_ops<A, PPT_OPS, FP_SCHEME_B>(a, o, s);
     return launch_eval_ops<A, PPT_OPS, 0>(a, o, s);
   }
   return launch_eval_smem<A, PPT_NODE>(a, s);

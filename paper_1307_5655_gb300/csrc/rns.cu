@@ -216,6 +216,7 @@ int launch_eval_rns(const EvalArgs& a, const OpArgs& o, int scheme, int k, const
     if (!configured[dev]) {
       cudaError_t e = raise_smem(rns_ops_kernel<1, FP_SCHEME_E>);
       if (e == cudaSuccess) e = raise_smem(rns_ops_kernel<1, FP_SCHEME_B>);
+      if (e == cudaSuccess) e = raise_smem(rns_ops_kernel<1, kSchemeBExt>);
       if (e == cudaSuccess) e = raise_smem(rns_ops_kernel<1, 0>);
       if (e == cudaSuccess) e = raise_smem(rns_node_kernel<1, true>);
       if (e == cudaSuccess) e = raise_smem(rns_node_kernel<1, false>);
@@ -235,6 +236,7 @@ int launch_eval_rns(const EvalArgs& a, const OpArgs& o, int scheme, int k, const
   const size_t fly = sizeof(uint64_t) * (size_t)(a.nslot + a.nvars) * kTPB;
   if (o.recs && ops_smem <= kTableSmemCap) {
     if (scheme == FP_SCHEME_E) rns_ops_kernel<1, FP_SCHEME_E><<<grid, kTPB, ops_smem, st>>>(a, o, s);
+    else if (scheme == FP_SCHEME_B && o.ext) rns_ops_kernel<1, kSchemeBExt><<<grid, kTPB, ops_smem, st>>>(a, o, s);
     else if (scheme == FP_SCHEME_B) rns_ops_kernel<1, FP_SCHEME_B><<<grid, kTPB, ops_smem, st>>>(a, o, s);
     else rns_ops_kernel<1, 0><<<grid, kTPB, ops_smem, st>>>(a, o, s);
   } else if (table <= kTableSmemCap) {

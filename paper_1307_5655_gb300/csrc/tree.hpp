@@ -41,13 +41,31 @@ constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 //      bits 2..7 S, 8..13 D, 14 LEAF (first node of the op is a leaf),
 //      15 FIRST (last node is its parent's first child), 16 UNIFORM (all
 //      powers inside a chain are the same), 17..31 PID of the outgoing edge
-//   y: len - 1      z: first node j0      w: offset of the op's coefficients
+//   y: bits 0..7 len - 1; for a block or partial block of more than
+//      kMaxBlock nodes, bits 8..15 f = the scheme's split of the run and
+//      bits 16..31 the table position of x^f: the run is T(b) + T(a) x^f,
+//      b its f lowest nodes, and its coefficients are stored as two runs
+//      (a, then b), each from a multiple of 4 elements
+//   z: first node j0      w: offset of the op's coefficients
 //   a: leaf coefficient of a single-node op   b: parent coefficient if FIRST
 // The coefficients of chains and blocks are stored per op in a stream, each
 // op's run starting at a multiple of 4 elements (aligned vector loads).
 constexpr uint32_t kOpNode = 0, kOpChain = 1, kOpBlock = 2, kOpPartial = 3;
 constexpr uint32_t kOpS = 2, kOpD = 8, kOpLeaf = 14, kOpFirst = 15, kOpUniform = 16, kOpPid = 17;
 constexpr int kMaxChain = 64, kMaxBlock = 16, kStreamAlign = 4;
+// a floating-point block of kMaxBlock < len <= kMaxSplitBlock nodes runs as
+// its two parts T(run) = T(b) + T(a) x^f, each at most kMaxBlock nodes
+constexpr int kMaxSplitBlock = 2 * kMaxBlock;
+constexpr int kMaxTwoPartBlock = 22;  // the longest run the compiler forms into two parts
+// PID of a block or partial block of a Balanced tree whose edge power is not
+// in the table: the
+// op recomputes x_b^d from a kept power x_b^(d >> m) (or x_b itself), its
+// record's z = base position (bits 0..14; 0x7FFF: x_b) | m << 15 (4 bits) |
+// (d mod 2^m) << 19, with the power program's steps (square, times x_b)
+constexpr uint32_t kPidRecompute = 0x7FFFu;
+constexpr int kRecomputeMinEntries = 20;  // only tables of at least this many entries per point shrink
+constexpr int kRecomputeCost = 16;        // ops x steps per point a recomputed power may cost
+constexpr int kRecomputeMaxSteps = 13;
 constexpr int kMaxExactBlock = 64;  // blocks of mod-p trees (evaluated by a loop, not a template)
 
 template <class C>
@@ -127,6 +145,7 @@ struct fp_tree {
   int ops_nlive = 0, ops_nslot = 1, ops_entries = 1;
   int ops_root_lh = 0, ops_root_pid = -1;
   int ops_pos_x1 = -1;  // position of x_b when the walk reads it
+  int ops_ext = 0;      // two-part blocks or recomputed edge powers (Balanced)
   int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_b^d for the block templates (-1: absent)
 
   // residue number system (fp_compile_rns): coefficients modulo rns_k primes,

@@ -8,7 +8,10 @@ definition sum c x^e mod p of the oracle at every point.  A wrong slot, a
 wrong power, a dropped or doubled coefficient (e.g. c_N counted both by a
 partial block and by the first child's initial value) changes the value.
 The block templates are replayed from Def. 1.2 directly: the value of a
-dense run is T(b) + T(a) x^f with b its f lowest terms."""
+dense run is T(b) + T(a) x^f with b its f lowest terms.  A floating-point
+block of 17 to 32 nodes is stored as its two parts a and b under the top
+split, joined with x^f from the table: the replay checks f, the stored runs
+and that power."""
 import math
 
 import numpy as np
@@ -81,10 +84,14 @@ def _replay(t, coeffs, x, counts=None):
         return tab[pos]
 
     for rec_, a_node, b_node in zip(sc["op_words"], sc["op_a_node"], sc["op_b_node"]):
-        w0, ln, j0, off = (int(v) for v in rec_)
+        w0, w1, j0, off = (int(v) for v in rec_)
         kind, S, D = w0 & 3, (w0 >> 2) & 63, (w0 >> 8) & 63
         leaf, first, uniform, pid = (w0 >> 14) & 1, (w0 >> 15) & 1, (w0 >> 16) & 1, w0 >> 17
-        ln += 1
+        ln, fsplit, fpos = (w1 & 255) + 1, (w1 >> 8) & 255, w1 >> 16
+        recompute = pid == 0x7FFF  # the edge power is rebuilt from a kept prefix
+        if recompute:  # word 2 is the recompute word; the first node is the stream's
+            assert kind >= 2 and sc["block_scheme"] in (2, 3)
+            ez, j0 = j0, int(sc["stream"][off])
         j1 = j0 + ln - 1
         if counts is not None:
             counts[kind] += 1
@@ -94,8 +101,18 @@ def _replay(t, coeffs, x, counts=None):
             if leaf:
                 assert a_node == j0
         else:
-            st = [int(s) for s in sc["stream"][off:off + ln]]
-            assert st == list(range(j0, j1 + 1)) and off % 4 == 0
+            assert off % 4 == 0
+            if fsplit:  # two parts: a (ln - f nodes), then b from the next multiple of 4
+                assert kind >= 2 and 16 < ln <= 32 and fsplit == _split(sc["block_scheme"], ln - 1)
+                assert ln - fsplit <= 16 and fsplit <= 16
+                offb = off + (ln - fsplit + 3) // 4 * 4
+                st = [int(s) for s in sc["stream"][off:off + ln - fsplit]] + \
+                    [int(s) for s in sc["stream"][offb:offb + fsplit]]
+                assert all(int(s) == -1 for s in sc["stream"][off + ln - fsplit:offb])
+                power(fpos, fsplit, len(x) - 1)  # x^f of the join, kept in the table
+            else:
+                st = [int(s) for s in sc["stream"][off:off + ln]]
+            assert st == list(range(j0, j1 + 1))
             cs = [node_c[j] for j in st]
             if kind == 1:
                 v = cs[0] if leaf else tab[slot(S)]
@@ -109,7 +126,8 @@ def _replay(t, coeffs, x, counts=None):
                 if uniform:
                     assert len(pids) == 1
             else:
-                # mod-p trees run blocks as a loop: up to 64 nodes (templates: 16)
+                # mod-p trees run blocks as a loop: up to 64 nodes (templates:
+                # 16, or 32 as two parts)
                 assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 64
                 run = ex["node_e"][j0:j1 + 1]
                 assert np.array_equal(run[:, -1], np.arange(run[0, -1], run[0, -1] - ln, -1))
@@ -119,7 +137,20 @@ def _replay(t, coeffs, x, counts=None):
                 v = _run_value(sc["block_scheme"], cs, xpow)
         q = int(ex["parent"][j1])
         # the op's outgoing edge is the edge of its last node
-        xd = power(pid, int(ex["pd"][j1]), int(ex["pd_var"][j1]))
+        deg, var = int(ex["pd"][j1]), int(ex["pd_var"][j1])
+        if recompute:  # x^(d >> m) (kept, or x), then square / times x per bit
+            assert var == len(x) - 1
+            base, m, bits = ez & 0x7FFF, (ez >> 15) & 15, ez >> 19
+            assert bits < (1 << m) and bits == deg % (1 << m)
+            xd = x1 if base == 0x7FFF else power(base, deg >> m, var)
+            assert base != 0x7FFF or deg >> m == 1
+            for i in range(m - 1, -1, -1):
+                xd = xd * xd % P
+                if (bits >> i) & 1:
+                    xd = xd * x1 % P
+            assert xd == pow(x1, deg, P)
+        else:
+            xd = power(pid, deg, var)
         if first:
             init = node_c[b_node] if b_node >= 0 else 0
             if b_node >= 0:
@@ -161,11 +192,19 @@ def test_large_univariate_schedules_use_partial_blocks():
         assert counts[3] > 0 and counts[2] > 0
         # a partial block absorbs the small children: far fewer ops than nodes
         assert sum(counts) * 6 < 10007, counts
-    # the floating-point trees keep blocks of at most 16 nodes
-    e, c, _ = W.univariate_case(3000, 1, 4243)
+    # the floating-point trees keep blocks of at most 22 nodes, those over 16
+    # as two parts under the top split; 10007 terms under B: runs of ~20
+    e, c, _ = W.univariate_case(10007, 1, 4243)
     sc = fpl.fp_compile_host(e, c, "B").schedule()
-    lens = sc["op_words"][:, 1][(sc["op_words"][:, 0] & 3) >= 2] + 1
-    assert lens.max() <= 16
+    w1 = sc["op_words"][:, 1][(sc["op_words"][:, 0] & 3) >= 2].astype(np.int64)
+    lens, fs = (w1 & 255) + 1, (w1 >> 8) & 255
+    assert lens.max() <= 22 and (fs[lens > 16] > 0).all() and (fs[lens <= 16] == 0).all()
+    assert lens.mean() > 16
+    # 3000 terms: runs of ~23 stay blocks of ~12 (two such parts gain nothing)
+    e, c, _ = W.univariate_case(3000, 1, 4244)
+    sc = fpl.fp_compile_host(e, c, "B").schedule()
+    w1 = sc["op_words"][:, 1][(sc["op_words"][:, 0] & 3) >= 2].astype(np.int64)
+    assert ((w1 & 255) + 1 <= 16).all()
 
 
 def test_sparse_and_hybrid_schedules():
@@ -233,7 +272,7 @@ def _random_terms(r, nvars):
 def test_random_schedules_replay_for_both_coefficient_types(seed):
     """Fuzz: random sparse multivariate term sets under random schemes
     (including random split tables), for the mod-p trees (blocks up to 64
-    nodes) and the floating-point trees (up to 16), replayed mod p."""
+    nodes) and the floating-point trees (up to 32), replayed mod p."""
     r = W.rng(9000 + seed)
     nvars = int(r.integers(1, 4))
     e = _random_terms(r, nvars)
@@ -258,5 +297,31 @@ def test_random_schedules_replay_for_both_coefficient_types(seed):
         if not modp:
             sc = t.schedule()
             blk = (sc["op_words"][:, 0] & 3) >= 2
-            assert (sc["op_words"][:, 1][blk] + 1 <= 16).all()
+            assert ((sc["op_words"][:, 1][blk].astype(np.int64) & 255) + 1 <= 32).all()
         t.free()
+
+
+@pytest.mark.parametrize("k", [40, 100, 1000, 3000, 10007])
+@pytest.mark.parametrize("scheme", ["E", "B"])
+def test_floating_point_schedules_with_two_part_blocks(k, scheme):
+    """The floating-point trees' schedules (under B, blocks of 17..32 nodes
+    stored as their two parts) replayed mod p with residues in the coefficients' places
+    equal the plain definition; two-part blocks and partial blocks occur."""
+    e, cf, _ = W.univariate_case(k, 1, 6100 + k)
+    res = W.residues(k, 6200 + k)
+    t = fpl.fp_compile_host(e, cf, scheme)
+    sc = t.schedule()
+    kinds = sc["op_words"][:, 0] & 3
+    w1 = sc["op_words"][:, 1].astype(np.int64)
+    two_part = (kinds >= 2) & (((w1 >> 8) & 255) > 0)
+    if scheme == "B" and k == 10007:  # runs of ~20 under the top splits
+        assert two_part.any()
+    if scheme == "B" and k == 10007:  # the table keeps the powers most ops read
+        assert ((sc["op_words"][:, 0] >> 17) == 0x7FFF).any() and sc["entries"] <= 16
+    if scheme == "E":  # Estrin keeps blocks of at most 16
+        assert not two_part.any() and ((w1[kinds >= 2] & 255) + 1 <= 16).all()
+    x = W.points_modp(1, 2, 6300 + k)
+    ref = O.eval_modp(e, res, x)
+    for p in range(2):
+        assert _replay(t, res, [int(x[0, p])]) == int(ref[p]), (scheme, k, p)
+    t.free()
