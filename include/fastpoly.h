@@ -239,10 +239,16 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
  *   block_pow [17]: table position of x_b^d read by the block templates
  *       after the program (-1: absent); b = nvars - 1, the innermost
  *       variable, whose groups are univariate polynomials under the scheme.
- *   layout [7]: nlive (the walk's powers sit at positions [0, nlive)),
+ *   layout [8]: nlive (the walk's powers sit at positions [0, nlive)),
  *       nslot (slot s sits at position nlive + s), table entries per point,
  *       block scheme (FP_SCHEME_E / FP_SCHEME_B when blocks are used, else 0),
- *       root is a leaf, root slot, position of the root's power (-1: none).
+ *       root is a leaf, root slot, position of the root's power (-1: none),
+ *       split: the first op of the root's later children (0: none) -- ops
+ *       [0, split) evaluate the root's first child's subtree (nodes 0 .. its
+ *       root) and its edge into the root's slot, ops [split, nops) the other
+ *       children, so small grids run the two ranges in two warps that start
+ *       from separate tables (the second from a zero root slot) and add the
+ *       root slots.
  * Any array pointer may be NULL.  FP_E_BAD_VALUE for a NULL tree. */
 int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_t* op_a_node,
                      int64_t* op_b_node, int64_t* stream_len, int64_t* stream, int32_t* nprog,

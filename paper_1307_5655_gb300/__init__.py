@@ -143,13 +143,13 @@ class Tree:
         prog = np.zeros((nprog.value, 2), dtype=np.uint32)
         cp = np.zeros(max(n - 1, 0), dtype=np.uint32)
         bp = np.zeros(17, dtype=np.int32)
-        lay = np.zeros(7, dtype=np.int32)
+        lay = np.zeros(8, dtype=np.int32)
         _check(_lib.fp_tree_schedule(self._h, None, _ptr(words), _ptr(a), _ptr(b), None, _ptr(st), None, _ptr(prog),
                                      _ptr(cp), _ptr(bp), _ptr(lay)), "fp_tree_schedule")
         return {"op_words": words, "op_a_node": a, "op_b_node": b, "stream": st, "prog": prog, "chain_pid": cp,
                 "block_pow": bp, "nlive": int(lay[0]), "nslot": int(lay[1]), "entries": int(lay[2]),
                 "block_scheme": int(lay[3]), "root_leaf": int(lay[4]), "root_lh": int(lay[5]),
-                "root_pid": int(lay[6])}
+                "root_pid": int(lay[6]), "split": int(lay[7])}
 
 
 def _compile(fn, exps, coeffs, scheme, ftab, modp):

@@ -29,7 +29,7 @@ int upload(const std::vector<T>& h, T** d) {
 void release(fp_tree* t) {
   DeviceSchedule& d = t->dev;
   void* ptrs[] = {d.ctrl, d.pow_prog, d.pow_dv, d.ca_f64, d.cb_f64, d.ca_f32, d.cb_f32, d.ca_u64, d.cb_u64,
-                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64, d.ops_prog, d.ops_chain_pid,
+                  d.ops_f64, d.ops_f32, d.ops_u64, d.st_f64, d.st_f32, d.st_u64, d.ops_prog, d.ops_chain_pid, d.ops_defer,
                   d.ca_rns, d.cb_rns, d.ops_rns, d.st_rns, d.root_rns};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -61,6 +61,7 @@ int upload_schedule(fp_tree* t) {
   if (rc == FP_OK) rc = upload(t->pow_prog, &d.pow_prog);
   if (rc == FP_OK) rc = upload(t->ops_prog, &d.ops_prog);
   if (rc == FP_OK) rc = upload(t->ops_chain_pid, &d.ops_chain_pid);
+  if (rc == FP_OK) rc = upload(t->ops_defer, &d.ops_defer);
   if (rc != FP_OK) return rc;
   std::vector<uint2> dv(t->pow_prog.size());
   for (size_t k = 0; k < dv.size(); ++k) dv[k] = make_uint2((unsigned)t->pow_var[k], (unsigned)t->pow_deg[k]);
@@ -213,6 +214,7 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
   o.nops = (int64_t)t->ops.size();
   o.prog = t->dev.ops_prog;
   o.chain_pid = t->dev.ops_chain_pid;
+  o.defer_edges = t->dev.ops_defer;
   o.nprog = (int)t->ops_prog.size();
   o.nlive = t->ops_nlive;
   o.nslot = t->ops_nslot;
@@ -221,6 +223,8 @@ int fill_eval_args(const fp_tree* t, fp_dtype dt, const void* points, int64_t np
   o.root_pid = t->ops_root_pid;
   o.pos_x1 = t->ops_pos_x1;
   o.ext = t->ops_ext;
+  o.split = t->ops_split;
+  o.ndefer = t->ops_ndefer;
   for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t root = t->nnodes - 1;
   switch (dt) {
@@ -577,6 +581,7 @@ int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_
     layout[4] = t->root_leaf;
     layout[5] = t->ops_root_lh;
     layout[6] = t->ops_root_pid;
+    layout[7] = (int32_t)t->ops_split;
   }
   return FP_OK;
 }
@@ -693,6 +698,7 @@ int fp_eval_rns(const fp_tree* t, const uint64_t* points, int64_t npts, uint64_t
   o.nops = (int64_t)t->ops.size();
   o.prog = t->dev.ops_prog;
   o.chain_pid = t->dev.ops_chain_pid;
+  o.defer_edges = t->dev.ops_defer;
   o.nprog = (int)t->ops_prog.size();
   o.nlive = t->ops_nlive;
   o.nslot = t->ops_nslot;
@@ -701,6 +707,8 @@ int fp_eval_rns(const fp_tree* t, const uint64_t* points, int64_t npts, uint64_t
   o.root_pid = t->ops_root_pid;
   o.pos_x1 = t->ops_pos_x1;
   o.ext = t->ops_ext;
+  o.split = t->ops_split;
+  o.ndefer = t->ops_ndefer;
   for (int d = 0; d <= kMaxBlock; ++d) o.pid_pow[d] = t->ops_pid_pow[d];
   const int64_t strides[5] = {(int64_t)t->nvars * npts, npts, t->nnodes - 1, (int64_t)t->ops.size(),
                               t->dev.st_rns_pitch};

@@ -158,6 +158,41 @@ int ops_layout(fp_tree* t) {
     if (fed[r]) nslot = std::max(nslot, finalize(r) + 1);
   if (nslot - 1 > FP_MAX_LAZY_HEIGHT) return FP_E_TOO_LARGE;  // 6-bit slot fields
 
+  // The split of the op list for small grids: the root's first child (the
+  // upper part a of the top split p = a x^f + b) heads a subtree of nodes
+  // 0 .. ra, and ops [0, s) cover exactly those nodes; ops [s, nops) add the
+  // root's later children into its slot.  The two ranges can run in two
+  // warps (the second starting from a zero slot) whose slots are then added.
+  // Kept when each range has at least a quarter of the nodes.
+  t->ops_split = 0;
+  if (N > 2) {
+    int64_t ra = -1;
+    for (int64_t j = 0; j + 1 < N && ra < 0; ++j)
+      if (t->parent[j] == N - 1) ra = j;
+    std::vector<int64_t> sz(N, 1);
+    for (int64_t j = 0; j + 1 < N; ++j) sz[t->parent[j]] += sz[j];
+    if (ra >= 0 && ra - sz[ra] + 1 == 0 && 4 * (ra + 1) >= N && 4 * (N - 1 - ra) >= N)
+      for (size_t i = 1; i < nops; ++i) {
+        const int64_t prev_j1 = (int64_t)t->ops[i - 1].z + (t->ops[i - 1].y & 255u);
+        if (prev_j1 == ra && (int64_t)t->ops[i].z == ra + 1) {
+          t->ops_split = (int64_t)i;
+          break;
+        }
+      }
+  }
+  // past the split, the edges into the root's slot are marked (w bit 31):
+  // the second warp keeps their values and applies them after the first
+  // warp's part, in walk order, so the split's result is the walk's own
+  t->ops_ndefer = 0;
+  if (t->ops_split > 0)
+    for (size_t i = (size_t)t->ops_split; i < nops; ++i) {
+      const int64_t j1 = (int64_t)t->ops[i].z + (t->ops[i].y & 255u);
+      if (t->parent[j1] == N - 1) {
+        t->ops[i].w |= 0x80000000u;
+        ++t->ops_ndefer;
+      }
+    }
+
   // powers the walk reads, and the block templates' powers
   const size_t np = t->pow_prog.size();
   std::vector<uint8_t> live(np, 0), tmpl(np, 0), needed(np, 0);
@@ -295,6 +330,9 @@ int ops_layout(fp_tree* t) {
     x &= ~((63u << kOpS) | (63u << kOpD) | (0x7FFFu << kOpPid));
     t->ops[i].x = x | S << kOpS | D << kOpD | P << kOpPid;
   }
+  t->ops_defer.clear();
+  for (size_t i = 0; i < nops; ++i)
+    if (t->ops[i].w >> 31) t->ops_defer.push_back(make_uint2(t->ops[i].x >> kOpPid, t->ops[i].z));
   t->ops_chain_pid.assign(N > 0 ? N - 1 : 0, 0);
   for (int64_t j = 0; j + 1 < N; ++j) {
     const int32_t p = pos[t->ctrl[j] >> kCtrlPid];
@@ -561,7 +599,7 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
       uint32_t off = 0;
       if (kind != kOpNode) {
         while (t->stream.size() % kStreamAlign) t->stream.push_back(-1);
-        off = (uint32_t)t->stream.size();
+        off = (uint32_t)t->stream.size();  // below 2^31 (FP_MAX_TERMS): w's bit 31 is a flag
         for (int64_t j = j0; j <= j1; ++j) {
           if (two_part && j == j1 - f + 1)
             while ((t->stream.size() - off) % kStreamAlign) t->stream.push_back(-1);

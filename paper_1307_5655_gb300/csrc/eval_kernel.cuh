@@ -21,6 +21,7 @@
 //   IV64 keeps the paper's order literally (see the interval policy).
 #pragma once
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cstring>
@@ -613,6 +614,9 @@ struct OpArgs {
   int pos_x1;                 // position of x_b (b: the blocks' variable) among the walk's powers (-1: none)
   int pid_pow[kMaxBlock + 1];  // position of x^d for the block templates (-1: absent)
   int ext;                     // Balanced tree with two-part blocks or recomputed edge powers
+  int64_t split;               // first op of the root's later children (0: none)
+  int ndefer;                  // ops from split on whose edge goes into the root's slot
+  const uint2* defer_edges;    // [ndefer] their {PID, z} in walk order
 };
 
 // The kernels of a Balanced tree whose schedule has two-part blocks or
@@ -732,7 +736,32 @@ __device__ __forceinline__ void load_rec(const OpRec<C>* r, uint4& h, C& a, C& b
 
 // TPB: threads per block (the stride of the per-point table); kTPB unless the
 // launch chose narrower blocks for a small grid
-template <class A, int PPT, int SCHEME, int TPB = kTPB>
+// The edge power x^d of an op marked kPidRecompute, rebuilt from its record's
+// z word: the table entry at its base position (0x7FFF: x itself), then m
+// steps of squaring and, where the bit of d is set, multiplying by x -- the
+// power program's own steps, so the value is the table's would-be entry.
+template <class A>
+__device__ __forceinline__ typename A::pw rebuild_power(uint32_t z, const typename A::pw* col, int stride,
+                                                        typename A::pw x) {
+  const int base = (int)(z & 0x7FFFu), m = (int)((z >> 15) & 15u);
+  const uint32_t bits = z >> 19;
+  typename A::pw y = base == 0x7FFF ? x : col[base * stride];
+  for (int i = m - 1; i >= 0; --i) {
+    y = A::square(y);
+    if ((bits >> i) & 1u) y = A::mulx(y, x);
+  }
+  return y;
+}
+
+// SPLIT (one point per thread, TPB = 64): the block's two warps evaluate the
+// same 32 points, warp 0 the ops [0, o.split) (the root's first child's
+// subtree, ending with its edge into the root's slot) and warp 1 the others,
+// keeping the values of its edges into the root's slot (marked in w) in its
+// own table entries past o.entries; after warp 0 is done warp 1 applies them,
+// in walk order, to warp 0's root slot -- the walk's own operations in its own
+// order, so the result is that of one warp.  Twice the warps for a grid too
+// small to fill the SMs' schedulers evenly.
+template <class A, int PPT, int SCHEME, int TPB = kTPB, bool SPLIT = false>
 __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int64_t base, unsigned char* smem_raw) {
   using V = typename A::val;
   using W = typename A::pw;
@@ -741,13 +770,16 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
   W* pw = reinterpret_cast<W*>(smem_raw);                        // [entries][PPT][TPB]
   V* acc = reinterpret_cast<V*>(smem_raw) + (size_t)o.nlive * PPT * TPB;  // slots above the walk's powers
   const int tid = threadIdx.x;
+  static_assert(!SPLIT || (PPT == 1 && TPB == 64), "the split runs one point per thread in two warps");
+  const int col = SPLIT ? (tid & 31) : tid;  // the thread's point within the block's points
+  const int half = SPLIT ? (tid >> 5) : 0;
 
   for (int k = 0; k < o.nprog; ++k) {
     const uint2 e = __ldg(o.prog + k);
     const uint32_t op = e.x & 3u, a1 = (e.x >> 2) & 0x7FFFu, a2 = e.x >> 17, dst = e.y;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-      const int64_t idx = base + p * TPB + tid;
+      const int64_t idx = base + p * TPB + col;
       W r;
       if (op == kPowLoad) r = idx < g.npts ? A::load_point(g.points, (int)a1, idx, g.npts) : A::dummy_point();
       else if (op == kPowSq) r = A::square(pw[(a1 * PPT + p) * TPB + tid]);
@@ -773,7 +805,14 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
 
   const OpRec<C>* recs = reinterpret_cast<const OpRec<C>*>(o.recs);
   const C* st = reinterpret_cast<const C*>(o.stream);
-  for (int64_t i = 0; i < o.nops; ++i) {
+  int64_t i_begin = 0, i_end = o.nops;
+  V* defer = reinterpret_cast<V*>(smem_raw) + (size_t)o.entries * TPB;  // SPLIT: kept root edges
+  int nd = 0;
+  if constexpr (SPLIT) {
+    if (half == 0) i_end = o.split;
+    else i_begin = o.split;
+  }
+  for (int64_t i = i_begin; i < i_end; ++i) {
     uint4 h;
     C a, b;
     load_rec(recs + i, h, a, b);
@@ -782,7 +821,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     const bool leaf = (h.x >> kOpLeaf) & 1u, first = (h.x >> kOpFirst) & 1u;
     const int pid = (int)(h.x >> kOpPid);
     const int len = (int)(h.y & 255u) + 1;
-    const int64_t off = (int64_t)h.w;
+    const int64_t off = (int64_t)(h.w & 0x7FFFFFFFu);
     V v[PPT];
     if (kind == kOpNode) {
 #pragma unroll
@@ -881,6 +920,13 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     // (kPidRecompute: a block of a Balanced tree whose power few ops read)
     // recomputed from a kept prefix x^(d >> m), or x, by the power program's
     // steps: square, then times x where the bit of d is set
+    if constexpr (SPLIT) {
+      if (half == 1 && (h.w >> 31)) {  // an edge into the root's slot: applied after warp 0
+        defer[nd * TPB + tid] = v[0];
+        ++nd;
+        continue;
+      }
+    }
     if (SCHEME != kSchemeBExt || pid != (int)kPidRecompute) {
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
@@ -889,18 +935,9 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
         *dst = A::mad(v[p], pw[(pid * PPT + p) * TPB + tid], init);
       }
     } else if constexpr (SCHEME == kSchemeBExt) {
-      const int base = (int)(h.z & 0x7FFFu), m = (int)((h.z >> 15) & 15u);
-      const uint32_t bits = h.z >> 19;
       W xe[PPT];
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) xe[p] = base == 0x7FFF ? xp[p][1] : pw[(base * PPT + p) * TPB + tid];
-      for (int i = m - 1; i >= 0; --i) {
-#pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-          xe[p] = A::square(xe[p]);
-          if ((bits >> i) & 1u) xe[p] = A::mulx(xe[p], xp[p][1]);
-        }
-      }
+      for (int p = 0; p < PPT; ++p) xe[p] = rebuild_power<A>(h.z, pw + p * TPB + tid, PPT * TPB, xp[p][1]);
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         V* dst = &acc[(D * PPT + p) * TPB + tid];
@@ -910,6 +947,23 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
     }
   }
 
+  if constexpr (SPLIT) {
+    __syncthreads();
+    if (half == 1) {
+      const int64_t idx = base + col;
+      V r = acc[o.root_lh * TPB + tid - 32];  // the root's slot after warp 0's part
+      for (int k = 0; k < o.ndefer; ++k) {
+        const uint2 e = __ldg(o.defer_edges + k);
+        W xe;
+        if (SCHEME != kSchemeBExt || e.x != kPidRecompute) xe = pw[e.x * TPB + tid];
+        else xe = rebuild_power<A>(e.y, pw + tid, TPB, xp[0][1]);
+        r = A::mad(defer[k * TPB + tid], xe, r);
+      }
+      if (o.root_pid >= 0) r = A::apply_root_power(r, pw[o.root_pid * TPB + tid]);
+      if (idx < g.npts) A::store(g.out, idx, g.npts, r);
+    }
+    return;
+  }
   const C rc = A::coef_from_bits(g.root_c);
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
@@ -920,10 +974,10 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
   }
 }
 
-template <class A, int PPT, int SCHEME, int TPB = kTPB>
+template <class A, int PPT, int SCHEME, int TPB = kTPB, bool SPLIT = false>
 __global__ void __launch_bounds__(TPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ops_tile<A, PPT, SCHEME, TPB>(g, o, (int64_t)blockIdx.x * (TPB * PPT), smem_raw);
+  ops_tile<A, PPT, SCHEME, TPB, SPLIT>(g, o, (int64_t)blockIdx.x * (SPLIT ? 32 : TPB * PPT), smem_raw);
 }
 
 // Launch helpers (defined per type in eval_<type>.cu).  variant: 0 = choose,
@@ -996,6 +1050,27 @@ cudaError_t launch_eval_ops_tpb(const EvalArgs& a, const OpArgs& o, cudaStream_t
   return cudaGetLastError();
 }
 
+// the split kernel: blocks of two warps over 32 points each
+template <class A, int SCHEME>
+cudaError_t launch_eval_ops_split(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
+  const size_t smem = sizeof(typename A::pw) * (size_t)(o.entries + o.ndefer) * 64;
+  if (smem > kSmemMax) return cudaErrorInvalidValue;
+  static int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, 1, SCHEME, 64, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  const int64_t blocks = (a.npts + 31) / 32;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  eval_ops_kernel<A, 1, SCHEME, 64, true><<<(unsigned)blocks, 64, smem, s>>>(a, o);
+  return cudaGetLastError();
+}
+
 // multiprocessors of the current device (cached per device)
 inline int sm_count() {
   static int cached[64] = {0};
@@ -1049,6 +1124,17 @@ inline int64_t ops_resident_points(size_t bytes_per_point, int tpb, int ppt, int
 // not depend on the block width.
 template <class A, int PPT, int SCHEME>
 cudaError_t launch_eval_ops(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
+  if constexpr (PPT == 1 && SCHEME != 0) {
+    // A small grid takes as long as the schedulers (4 per SM) with one warp
+    // more than the others: w warps per scheduler cost ceil(w) / w of the
+    // balanced time, the split's 2w half-warps ceil(2w) / 2w.  A tree with a
+    // split takes it where that gains more than 5 %.
+    if (o.split > 0) {
+      const double w = (double)((a.npts + 31) / 32) / (4.0 * sm_count());
+      if (w > 0 && w < 16 && (std::ceil(w) / w) > 1.05 * (std::ceil(2 * w) / (2 * w)))
+        return launch_eval_ops_split<A, SCHEME>(a, o, s);
+    }
+  }
   if constexpr (PPT == 1) {
     const int64_t blocks = (a.npts + kTPB - 1) / kTPB;
     const int64_t sms = sm_count();

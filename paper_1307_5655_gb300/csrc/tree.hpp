@@ -46,7 +46,9 @@ constexpr uint32_t kPowLoad = 0, kPowSq = 1, kPowMulX = 2;
 //      bits 16..31 the table position of x^f: the run is T(b) + T(a) x^f,
 //      b its f lowest nodes, and its coefficients are stored as two runs
 //      (a, then b), each from a multiple of 4 elements
-//   z: first node j0      w: offset of the op's coefficients
+//   z: first node j0      w: offset of the op's coefficients (bits 0..30);
+//      bit 31: the op lies past the split and its edge goes into the root's
+//      slot (see ops_layout)
 //   a: leaf coefficient of a single-node op   b: parent coefficient if FIRST
 // The coefficients of chains and blocks are stored per op in a stream, each
 // op's run starting at a multiple of 4 elements (aligned vector loads).
@@ -93,6 +95,7 @@ struct DeviceSchedule {
   uint64_t* st_u64 = nullptr;
   uint2* ops_prog = nullptr;         // power program of the grouped-op kernel
   uint32_t* ops_chain_pid = nullptr;  // [nsteps]
+  uint2* ops_defer = nullptr;         // [ops_ndefer] edges into the root past the split
   // residues (fp_compile_rns), one slice per prime
   uint64_t* ca_rns = nullptr;        // [k][nsteps]
   uint64_t* cb_rns = nullptr;        // [k][nsteps]
@@ -146,6 +149,9 @@ struct fp_tree {
   int ops_root_lh = 0, ops_root_pid = -1;
   int ops_pos_x1 = -1;  // position of x_b when the walk reads it
   int ops_ext = 0;      // two-part blocks or recomputed edge powers (Balanced)
+  int64_t ops_split = 0;  // first op of the root's later children (0: no split; see ops_layout)
+  int ops_ndefer = 0;     // ops from ops_split on whose edge goes into the root's slot
+  std::vector<uint2> ops_defer;  // those ops' {PID, z} in walk order (their edge powers)
   int ops_pid_pow[fp::kMaxBlock + 1] = {};  // position of x_b^d for the block templates (-1: absent)
 
   // residue number system (fp_compile_rns): coefficients modulo rns_k primes,

@@ -83,83 +83,108 @@ def _replay(t, coeffs, x, counts=None):
         assert tab[pos] == pow(int(x[var]), deg, P), (pos, deg, var)
         return tab[pos]
 
-    for rec_, a_node, b_node in zip(sc["op_words"], sc["op_a_node"], sc["op_b_node"]):
-        w0, w1, j0, off = (int(v) for v in rec_)
-        kind, S, D = w0 & 3, (w0 >> 2) & 63, (w0 >> 8) & 63
-        leaf, first, uniform, pid = (w0 >> 14) & 1, (w0 >> 15) & 1, (w0 >> 16) & 1, w0 >> 17
-        ln, fsplit, fpos = (w1 & 255) + 1, (w1 >> 8) & 255, w1 >> 16
-        recompute = pid == 0x7FFF  # the edge power is rebuilt from a kept prefix
-        if recompute:  # word 2 is the recompute word; the first node is the stream's
-            assert kind >= 2 and sc["block_scheme"] in (2, 3)
-            ez, j0 = j0, int(sc["stream"][off])
-        j1 = j0 + ln - 1
-        if counts is not None:
-            counts[kind] += 1
-        if kind == 0:
-            assert ln == 1
-            v = node_c[a_node] if leaf else tab[slot(S)]
-            if leaf:
-                assert a_node == j0
-        else:
-            assert off % 4 == 0
-            if fsplit:  # two parts: a (ln - f nodes), then b from the next multiple of 4
-                assert kind >= 2 and 16 < ln <= 32 and fsplit == _split(sc["block_scheme"], ln - 1)
-                assert ln - fsplit <= 16 and fsplit <= 16
-                offb = off + (ln - fsplit + 3) // 4 * 4
-                st = [int(s) for s in sc["stream"][off:off + ln - fsplit]] + \
-                    [int(s) for s in sc["stream"][offb:offb + fsplit]]
-                assert all(int(s) == -1 for s in sc["stream"][off + ln - fsplit:offb])
-                power(fpos, fsplit, len(x) - 1)  # x^f of the join, kept in the table
+    ops = list(zip(sc["op_words"], sc["op_a_node"], sc["op_b_node"]))
+
+    def run_ops(tab, lo, hi, defer=None):
+        for i_op, (rec_, a_node, b_node) in enumerate(ops[lo:hi], start=lo):
+            w0, w1, j0, w3 = (int(v) for v in rec_)
+            off, root_edge = w3 & 0x7FFFFFFF, w3 >> 31
+            kind, S, D = w0 & 3, (w0 >> 2) & 63, (w0 >> 8) & 63
+            leaf, first, uniform, pid = (w0 >> 14) & 1, (w0 >> 15) & 1, (w0 >> 16) & 1, w0 >> 17
+            ln, fsplit, fpos = (w1 & 255) + 1, (w1 >> 8) & 255, w1 >> 16
+            recompute = pid == 0x7FFF  # the edge power is rebuilt from a kept prefix
+            if recompute:  # word 2 is the recompute word; the first node is the stream's
+                assert kind >= 2 and sc["block_scheme"] in (2, 3)
+                ez, j0 = j0, int(sc["stream"][off])
+            j1 = j0 + ln - 1
+            if counts is not None:
+                counts[kind] += 1
+            if kind == 0:
+                assert ln == 1
+                v = node_c[a_node] if leaf else tab[slot(S)]
+                if leaf:
+                    assert a_node == j0
             else:
-                st = [int(s) for s in sc["stream"][off:off + ln]]
-            assert st == list(range(j0, j1 + 1))
-            cs = [node_c[j] for j in st]
-            if kind == 1:
-                v = cs[0] if leaf else tab[slot(S)]
-                pids = set()
-                for i in range(1, ln):
-                    j = j0 + i - 1
-                    assert int(ex["parent"][j]) == j + 1
-                    pc = int(sc["chain_pid"][j])
-                    pids.add(pc)
-                    v = (v * power(pc, int(ex["pd"][j]), int(ex["pd_var"][j])) + cs[i]) % P
-                if uniform:
-                    assert len(pids) == 1
+                assert off % 4 == 0
+                if fsplit:  # two parts: a (ln - f nodes), then b from the next multiple of 4
+                    assert kind >= 2 and 16 < ln <= 32 and fsplit == _split(sc["block_scheme"], ln - 1)
+                    assert ln - fsplit <= 16 and fsplit <= 16
+                    offb = off + (ln - fsplit + 3) // 4 * 4
+                    st = [int(s) for s in sc["stream"][off:off + ln - fsplit]] + \
+                        [int(s) for s in sc["stream"][offb:offb + fsplit]]
+                    assert all(int(s) == -1 for s in sc["stream"][off + ln - fsplit:offb])
+                    power(fpos, fsplit, len(x) - 1)  # x^f of the join, kept in the table
+                else:
+                    st = [int(s) for s in sc["stream"][off:off + ln]]
+                assert st == list(range(j0, j1 + 1))
+                cs = [node_c[j] for j in st]
+                if kind == 1:
+                    v = cs[0] if leaf else tab[slot(S)]
+                    pids = set()
+                    for i in range(1, ln):
+                        j = j0 + i - 1
+                        assert int(ex["parent"][j]) == j + 1
+                        pc = int(sc["chain_pid"][j])
+                        pids.add(pc)
+                        v = (v * power(pc, int(ex["pd"][j]), int(ex["pd_var"][j])) + cs[i]) % P
+                    if uniform:
+                        assert len(pids) == 1
+                else:
+                    # mod-p trees run blocks as a loop: up to 64 nodes (templates:
+                    # 16, or 32 as two parts)
+                    assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 64
+                    run = ex["node_e"][j0:j1 + 1]
+                    assert np.array_equal(run[:, -1], np.arange(run[0, -1], run[0, -1] - ln, -1))
+                    assert (run[:, :-1] == run[-1, :-1]).all()
+                    if kind == 3:  # N's slot (c_N and its earlier children) stands for c_N
+                        cs = cs[:-1] + [tab[slot(S)]]
+                    v = _run_value(sc["block_scheme"], cs, xpow)
+            q = int(ex["parent"][j1])
+            # past the split, exactly the edges into the root are marked
+            assert root_edge == (sc["split"] > 0 and i_op >= sc["split"] and q == n - 1)
+            # the op's outgoing edge is the edge of its last node
+            deg, var = int(ex["pd"][j1]), int(ex["pd_var"][j1])
+            if recompute:  # x^(d >> m) (kept, or x), then square / times x per bit
+                assert var == len(x) - 1
+                base, m, bits = ez & 0x7FFF, (ez >> 15) & 15, ez >> 19
+                assert bits < (1 << m) and bits == deg % (1 << m)
+                xd = x1 if base == 0x7FFF else power(base, deg >> m, var)
+                assert base != 0x7FFF or deg >> m == 1
+                for i in range(m - 1, -1, -1):
+                    xd = xd * xd % P
+                    if (bits >> i) & 1:
+                        xd = xd * x1 % P
+                assert xd == pow(x1, deg, P)
             else:
-                # mod-p trees run blocks as a loop: up to 64 nodes (templates:
-                # 16, or 32 as two parts)
-                assert sc["block_scheme"] in (2, 3) and 2 <= ln <= 64
-                run = ex["node_e"][j0:j1 + 1]
-                assert np.array_equal(run[:, -1], np.arange(run[0, -1], run[0, -1] - ln, -1))
-                assert (run[:, :-1] == run[-1, :-1]).all()
-                if kind == 3:  # N's slot (c_N and its earlier children) stands for c_N
-                    cs = cs[:-1] + [tab[slot(S)]]
-                v = _run_value(sc["block_scheme"], cs, xpow)
-        q = int(ex["parent"][j1])
-        # the op's outgoing edge is the edge of its last node
-        deg, var = int(ex["pd"][j1]), int(ex["pd_var"][j1])
-        if recompute:  # x^(d >> m) (kept, or x), then square / times x per bit
-            assert var == len(x) - 1
-            base, m, bits = ez & 0x7FFF, (ez >> 15) & 15, ez >> 19
-            assert bits < (1 << m) and bits == deg % (1 << m)
-            xd = x1 if base == 0x7FFF else power(base, deg >> m, var)
-            assert base != 0x7FFF or deg >> m == 1
-            for i in range(m - 1, -1, -1):
-                xd = xd * xd % P
-                if (bits >> i) & 1:
-                    xd = xd * x1 % P
-            assert xd == pow(x1, deg, P)
-        else:
-            xd = power(pid, deg, var)
-        if first:
-            init = node_c[b_node] if b_node >= 0 else 0
-            if b_node >= 0:
-                assert b_node == q
-        else:
-            init = tab[slot(D)]
-        tab[slot(D)] = (v * xd + init) % P
+                xd = power(pid, deg, var)
+            if first:
+                init = node_c[b_node] if b_node >= 0 else 0
+                if b_node >= 0:
+                    assert b_node == q
+            else:
+                init = tab[slot(D)]
+            if defer is not None and root_edge:  # kept, applied after the first part
+                defer.append((v, xd))
+                continue
+            tab[slot(D)] = (v * xd + init) % P
     root = n - 1
+    split = sc["split"]
+    tab0 = list(tab)  # after the power program: the split's halves start here
+    run_ops(tab, 0, len(ops))
     r = node_c[root] if sc["root_leaf"] else tab[slot(sc["root_lh"])]
+    if split:
+        # the small-grid split: ops [0, split) and [split, nops) on separate
+        # tables; the second keeps its edges into the root (marked) and
+        # applies them, in order, to the first's root slot: the walk's value
+        assert 0 < split < len(ops) and not sc["root_leaf"]
+        ta, tb = list(tab0), list(tab0)
+        run_ops(ta, 0, split)
+        kept = []
+        run_ops(tb, split, len(ops), kept)
+        r2 = ta[slot(sc["root_lh"])]
+        for v, xd in kept:
+            r2 = (v * xd + r2) % P
+        assert r2 == r and len(kept) > 0
     if sc["root_pid"] >= 0:
         r = r * power(sc["root_pid"], int(ex["pd"][root]), 0) % P
     return r
@@ -304,9 +329,11 @@ def test_random_schedules_replay_for_both_coefficient_types(seed):
 @pytest.mark.parametrize("k", [40, 100, 1000, 3000, 10007])
 @pytest.mark.parametrize("scheme", ["E", "B"])
 def test_floating_point_schedules_with_two_part_blocks(k, scheme):
-    """The floating-point trees' schedules (under B, blocks of 17..32 nodes
-    stored as their two parts) replayed mod p with residues in the coefficients' places
-    equal the plain definition; two-part blocks and partial blocks occur."""
+    """The floating-point trees' schedules (under B, blocks of 17..22 nodes
+    stored as their two parts) replayed mod p with residues in the
+    coefficients' places equal the plain definition (and so do the two
+    halves of the small-grid split, added); two-part blocks occur, and the
+    trees whose first top part holds a quarter of the nodes have a split."""
     e, cf, _ = W.univariate_case(k, 1, 6100 + k)
     res = W.residues(k, 6200 + k)
     t = fpl.fp_compile_host(e, cf, scheme)
@@ -320,6 +347,8 @@ def test_floating_point_schedules_with_two_part_blocks(k, scheme):
         assert ((sc["op_words"][:, 0] >> 17) == 0x7FFF).any() and sc["entries"] <= 16
     if scheme == "E":  # Estrin keeps blocks of at most 16
         assert not two_part.any() and ((w1[kinds >= 2] & 255) + 1 <= 16).all()
+    if k in (1000, 3000):  # top parts of 488 / 952 (E), 500 / 1500 (B) nodes
+        assert sc["split"] > 0
     x = W.points_modp(1, 2, 6300 + k)
     ref = O.eval_modp(e, res, x)
     for p in range(2):
