@@ -49,8 +49,9 @@ __global__ void __launch_bounds__(kTPB) eval_batch_kernel(const BatchJob* __rest
       const OpArgs o = jobs[lo].o;
       const int scheme = jobs[lo].scheme;
       if (scheme == FP_SCHEME_E) ops_tile<A, PPT, FP_SCHEME_E>(g, o, base, smem_raw);
-      else if (scheme == FP_SCHEME_B && o.ext) ops_tile<A, PPT, kSchemeBExt>(g, o, base, smem_raw);
-      else if (scheme == FP_SCHEME_B) ops_tile<A, PPT, FP_SCHEME_B>(g, o, base, smem_raw);
+      // Balanced: the extended path, which also runs plain Balanced schedules
+      // (one instantiation less in this kernel, which serves every scheme)
+      else if (scheme == FP_SCHEME_B) ops_tile<A, PPT, kSchemeBExt>(g, o, base, smem_raw);
       else ops_tile<A, PPT, 0>(g, o, base, smem_raw);
     } else if (mode == kModeNodeTable) {
       node_tile<A, PPT, true>(g, base, smem_raw);

@@ -685,20 +685,25 @@ __device__ __forceinline__ void load4(const C* st, int64_t off, int q, C (&c)[4]
 // The value of the block's last node N is its coefficient; for a partial
 // block it is N's slot (slot[p]).  Types with A::kSlotAtEnd evaluate the run
 // with 0 for N and add the slot afterwards (the slot's load then overlaps the
-// block's arithmetic; one add more), the others start from the slot.  Each
-// length loads its own ceil(L / 4) coefficient vectors of the op's run.
+// block's arithmetic; one add more), the others start from the slot.  The
+// op's run is loaded before the dispatch, in 4-element vectors (loading per
+// length inside each case raised the register use of the kernels that serve
+// every scheme -- batch, resident -- into spills).
 template <class A, int SCHEME, int PPT>
 __device__ __forceinline__ void block_dispatch(int len, bool partial, const typename A::coef* st, int64_t off,
                                                const typename A::pw (&xp)[PPT][kMaxBlock + 1],
                                                const typename A::val (&slot)[PPT], typename A::val (&v)[PPT]) {
   typename A::coef c[kMaxBlock];
+#pragma unroll
+  for (int q = 0; q < kMaxBlock / 4; ++q) {
+    typename A::coef c4[4];
+    if (4 * q < len) load4(st, off, q, c4);
+    else c4[0] = c4[1] = c4[2] = c4[3] = typename A::coef(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];
+  }
 #define FP_BLOCK_CASE(L)                                                                      \
   case L:                                                                                     \
-    _Pragma("unroll") for (int q = 0; q < (L + 3) / 4; ++q) {                                 \
-      typename A::coef c4[4];                                                                 \
-      load4(st, off, q, c4);                                                                  \
-      _Pragma("unroll") for (int r = 0; r < 4; ++r) c[4 * q + r] = c4[r];                     \
-    }                                                                                         \
     _Pragma("unroll") for (int p = 0; p < PPT; ++p) {                                         \
       if constexpr (A::kSlotAtEnd) {                                                          \
         const typename A::val base = A::from_coef(partial ? typename A::coef(0) : c[L - 1]);  \

@@ -162,8 +162,9 @@ __global__ void __launch_bounds__(kTPB) resident_kernel(ResQueue* q, const ResJo
         if (mode == kResModeOps) {
           const OpArgs o = s_desc.o;
           if (scheme == FP_SCHEME_E) ops_tile<A, PPT, FP_SCHEME_E>(g, o, base, smem_raw);
-          else if (scheme == FP_SCHEME_B && o.ext) ops_tile<A, PPT, kSchemeBExt>(g, o, base, smem_raw);
-          else if (scheme == FP_SCHEME_B) ops_tile<A, PPT, FP_SCHEME_B>(g, o, base, smem_raw);
+          // Balanced: the extended path, which also runs plain Balanced schedules
+          // (one instantiation less in this kernel, which serves every scheme)
+          else if (scheme == FP_SCHEME_B) ops_tile<A, PPT, kSchemeBExt>(g, o, base, smem_raw);
           else ops_tile<A, PPT, 0>(g, o, base, smem_raw);
         } else if (mode == kResModeNodeTable) {
           node_tile<A, PPT, true>(g, base, smem_raw);
