@@ -63,7 +63,7 @@ namespace fp {
 namespace tc {
 
 constexpr int T = 64;                // coefficients per block: N and K of one step
-constexpr int V = 16;                // steps per load of the A window
+constexpr int V = 32;                // steps per load of the A window
 constexpr int MROWS = 128;           // output blocks per tile (MMA M, TMEM lanes)
 constexpr int WROWS = MROWS + V;     // rows of the A window in shared memory
 constexpr int STRIP = WROWS * 16;    // bytes of one (slice, 8-column chunk) strip of A
