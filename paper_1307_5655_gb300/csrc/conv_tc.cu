@@ -315,23 +315,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 // its thread while the tensor cores' queue is full, so a thread that issued
 // and also read out would leave the tensor cores idle during its readout.
 //
-// Steps k = 0 .. v_hi - v_lo (v = v_lo + k).  Barriers:
+// Steps k = 0 .. v_hi - v_lo (v = v_lo + k).  The readers read a step's
+// exact and combined groups together (one rounding shift per coefficient);
+// the issuer queues step k + 1's combined group (its buffer alternates) ahead
+// of its exact groups, so the tensor cores run it during step k's readout.
+// Barriers (b = parity of the step they concern):
 //   full_x     step k's exact groups are in TMEM (commit; phase k)
-//   full_y(b)  step k's combined group, b = k & 1 (commit; phase k >> 1)
-//   ready      step k's operands are in shared memory and step k - 1's exact
-//              groups are read out (the readers; phase k - 1; step 0 is
-//              covered by the prologue's __syncthreads)
-//   free_y(b)  step k's combined group is read out (the readers; phase k >> 1)
-// A step is issued only after the readers passed the previous phase of each
-// barrier it waits on, so no wait is ever more than one phase behind and the
-// parity of the awaited phase identifies it.
+//   full_y(b)  step k's combined group (commit; phase k >> 1)
+//   ops(b)     step k's operands are in shared memory (the readers; the
+//              (k >> 1)-th phase of ops(k & 1) for k >= 1 -- step 0 is
+//              covered by the prologue's __syncthreads): signalled after
+//              step k - 2's readout, when its Hankel operand is built, or
+//              after step k - 1's when the A window is reloaded for step k
+//   free(b)    step k is read out (the readers; phase k >> 1): step k + 1's
+//              exact groups and step k + 2's combined group may overwrite
+// Each barrier's next phase needs an MMA that is issued only after its
+// waiter passed the current one, so no wait is ever more than one phase
+// behind and the parity of the awaited phase identifies it.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     k_conv_tc(const uint4* __restrict__ ahat, const int* __restrict__ alpha, int nA, const uint4* __restrict__ rhat,
               const int* __restrict__ beta, int nV, int nW, int rl, int mtiles, double* out, int64_t out_pitch,
               int mode, const double* init, int64_t init_pitch, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[6];
+  __shared__ __align__(8) uint64_t bar[7];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail[3];  // a reader's wait of iteration k gave up (slot k & 1); the issuer's (slot 2)
   unsigned char* sA = smem;                                // A window: S x 8 strips
@@ -361,17 +368,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = 0;
 
-  const uint32_t full_x = smem_u32(&bar[0]), ready = smem_u32(&bar[3]);
+  const uint32_t full_x = smem_u32(&bar[0]);
   auto full_y = [&](int b) { return smem_u32(&bar[1 + b]); };
-  auto free_y = [&](int b) { return smem_u32(&bar[4 + b]); };
+  auto ops = [&](int b) { return smem_u32(&bar[3 + b]); };
+  auto freed = [&](int b) { return smem_u32(&bar[5 + b]); };
+  // the phase of ops(k & 1) that step k's operands complete (k >= 1)
+  auto ops_phase = [](int k) { return ((k - 2 + (k & 1)) >> 1) & 1; };
+  // step k's A window is loaded after step k - 1's readout (every V steps)
+  auto reload = [](int k) { return k > 0 && k % V == 0; };
   if (threadIdx.x == 0) {
     s_fail[0] = s_fail[1] = s_fail[2] = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_x), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_y(0)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_y(1)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ready), "r"(READERS));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(free_y(0)), "r"(READERS));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(free_y(1)), "r"(READERS));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full_y(b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ops(b)), "r"(READERS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(freed(b)), "r"(READERS));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -430,38 +442,37 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base;
+  if (reader && nsteps > 1) mbar_arrive(ops(1));  // step 1's operands (its Hankel, window 0)
 
   if (!reader) {
     // The issuer.  Step k: slice i of the A window (row of block w0 - v at
     // window row V - 1 - k % V) times slice j of Hankel buffer k & 1; the
-    // exact groups into columns 0 .. 255, the combined group's halves into
-    // columns 256 + 128 (k & 1) + 0 / 64.
+    // combined group's halves into columns 256 + 128 (k & 1) + 0 / 64 (after
+    // step k - 2's readout), then the exact groups into columns 0 .. 255
+    // (after step k - 1's).
     if (lane == 0) {
-      int kis = -1;  // the last step issued
+      int kx = -1, ky = -1;  // the last steps whose exact / combined groups were issued
       for (int k = 0; k < nsteps; ++k) {
-        if (k >= 1 && !mbar_wait(ready, (k - 1) & 1)) break;
+        if (k >= 1 && !mbar_wait(ops(k & 1), ops_phase(k))) break;
+        if (k >= 2 && !mbar_wait(freed(k & 1), ((k - 2) >> 1) & 1)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const int roff = (V - 1) - k % V;
         const uint64_t dA = sdesc(smem_u32(sA) + 16u * roff, STRIP, 128);
         const uint64_t dB = sdesc(smem_u32(sH) + (uint32_t)((k & 1) * S * HANKEL), 128, 128);
-        issue_mmas<S, 0>(tmem, dA, dB);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(full_x));
-        if (k >= 2 && !mbar_wait(free_y(k & 1), ((k - 2) >> 1) & 1)) {
-          kis = -2 - k;  // the exact groups of step k are in flight
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t tc = tmem + (uint32_t)((NACC - 1) * T + NCOMB * T * (k & 1));
         issue_mmas<S, 1>(tc, dA, dB);
         issue_mmas<S, 2>(tc + T, dA, dB);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(full_y(k & 1)));
-        kis = k;
+        ky = k;
+        if (k >= 1 && !mbar_wait(freed((k - 1) & 1), ((k - 1) >> 1) & 1)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        issue_mmas<S, 0>(tmem, dA, dB);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(full_x));
+        kx = k;
       }
-      if (kis != nsteps - 1) {
+      if (kx != nsteps - 1) {
         s_fail[2] = 1;
         // the MMAs in flight (the last commit to each barrier), bounded
-        const int kx = kis >= 0 ? kis : -2 - kis;  // the last step with exact groups issued
-        const int ky = kis >= 0 ? kis : kx - 1;    // the last step with its combined group issued
         if (kx >= 0) mbar_wait(full_x, kx & 1);
         if (ky >= 0) mbar_wait(full_y(ky & 1), (ky >> 1) & 1);
         if (ky >= 1) mbar_wait(full_y((ky - 1) & 1), ((ky - 1) >> 1) & 1);
@@ -471,21 +482,25 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     for (int k = 0; k < nsteps; ++k) {
       const int v = v_lo + k;
-      const bool next = k + 1 < nsteps;
-      const bool reload = next && (k + 1) % V == 0;
-      // this row's step: C 2^E units of 2^F, E = alpha + beta - 40 - F <= P
+      // this row's step: (C + D) 2^E units of 2^F, E = alpha + beta - 40 - F <= P
       const int u = w - v;
       const int E = (w < nW && u >= 0 && u < nA) ? __ldg(al + u) + __ldg(be + v) - 40 - F : -1000;
       const int sh = min(63, P - E);
       const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0;
+      if (!mbar_wait(full_y(k & 1), (k >> 1) & 1)) s_fail[k & 1] = 1;
       if (!mbar_wait(full_x, k & 1)) s_fail[k & 1] = 1;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int qc = 0; qc < 4; ++qc) {
-        uint32_t r[NACC - 1][8];
+        uint32_t r[NACC - 1 + NCOMB][8];
 #pragma unroll
         for (int g = 0; g < NACC - 1; ++g)
           tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * T + 32 * h + 8 * qc), r[g]);
+#pragma unroll
+        for (int kk = 0; kk < NCOMB; ++kk)
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) +
+                       (uint32_t)((NACC - 1) * T + NCOMB * T * (k & 1) + T * kk + 32 * h + 8 * qc),
+                   r[NACC - 1 + kk]);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -494,54 +509,36 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int g = 0; g < NACC - 1; ++g)
             d[g] = __float_as_int(fmaf(__uint_as_float(r[g][c]), __int_as_float((127 + 7 * g) << 23), 12582912.0f)) -
                    0x4B400000;
+          int dc = 0;
+#pragma unroll
+          for (int kk = 0; kk < NCOMB; ++kk)
+            dc += __float_as_int(fmaf(__uint_as_float(r[NACC - 1 + kk][c]),
+                                      __int_as_float((127 + 7 * (NACC - 1)) << 23), 12582912.0f)) -
+                  0x4B400000;
           const long long C = (long long)d[0] * (1ll << 28) + (long long)d[1] * (1ll << 21) +
-                              (long long)d[2] * (1ll << 14) + (long long)d[3] * 128;
+                              (long long)d[2] * (1ll << 14) + (long long)d[3] * 128 + dc;
           acc[8 * qc + c] += ((C << P) + rnd) >> sh;
         }
       }
-      if (reload) {
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(freed(k & 1));
+      if (k + 1 < nsteps && reload(k + 1)) {
         // the next chunk's window: every MMA reading the current one is done
-        if (!mbar_wait(full_y(k & 1), (k >> 1) & 1)) s_fail[k & 1] = 1;
         load_window(v + 1);
-      }
-      if (next) {
-        // step k + 1: its window (reloaded above) and Hankel operand (built
-        // in the previous iteration) in place, step k's exact groups read
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        mbar_arrive(ready);
+        mbar_arrive(ops((k + 1) & 1));
       }
       if (k + 2 < nsteps) stage_window(v + 2, k & 1);
-      if (!mbar_wait(full_y(k & 1), (k >> 1) & 1)) s_fail[k & 1] = 1;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll
-      for (int qc = 0; qc < 4; ++qc) {
-        uint32_t r[NCOMB][8];
-#pragma unroll
-        for (int kk = 0; kk < NCOMB; ++kk)
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) +
-                       (uint32_t)((NACC - 1) * T + NCOMB * T * (k & 1) + T * kk + 32 * h + 8 * qc),
-                   r[kk]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          long long d = 0;
-#pragma unroll
-          for (int kk = 0; kk < NCOMB; ++kk)
-            d += __float_as_int(fmaf(__uint_as_float(r[kk][c]), __int_as_float((127 + 7 * (NACC - 1)) << 23),
-                                     12582912.0f)) -
-                 0x4B400000;
-          acc[8 * qc + c] += ((d << P) + rnd) >> sh;
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      mbar_arrive(free_y(k & 1));
       readers_sync();
       // (a reader past this check may set the next iteration's slot before a
       // slower one reads this one: separate slots keep the decision uniform)
       if (s_fail[k & 1]) break;
-      // step k + 2's Hankel operand into buffer k & 1: step k's MMAs are done
-      if (k + 2 < nsteps) build_hankel(k & 1, k & 1);
+      if (k + 2 < nsteps) {
+        // step k + 2's Hankel operand into buffer k & 1: step k's MMAs are done
+        build_hankel(k & 1, k & 1);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (!reload(k + 2)) mbar_arrive(ops(k & 1));
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
