@@ -37,11 +37,11 @@
 // each into its integer with one FMA against 1.5 2^23 (exact for |D| < 2^22),
 // and forms C = D_0 2^28 + D_1 2^21 + D_2 2^14 + D_3 2^7 (|C| < 2^47) and
 // D_4 (the two combined accumulators' integers, each rounded to the unit):
-// the step contributes (C + D_4) 2^(alpha_{w-v} + beta_v - 40).  TMEM holds
-// the four exact accumulators once and the combined pair twice (512
-// columns), so all of step v + 1 is issued as soon as step v's exact groups
-// are read out, and the tensor cores run it while step v's combined group is
-// read out and the Hankel operand of step v + 2 is built.  Each output row
+// the step contributes (C + D_4) 2^(alpha_{w-v} + beta_v - 40), rounded to
+// the row's unit once.  TMEM holds the four exact accumulators once and the
+// combined pair twice (512 columns): step v + 1's combined group is queued
+// before step v is read out, and the tensor cores run it during that
+// readout; its exact groups follow once step v is read.  Each output row
 // keeps a 64-bit fixed-point accumulator with unit 2^F_w, F_w = max over the
 // row's steps of alpha + beta - 40 - (15 - hr), hr the bits of the row's step
 // count: every contribution stays below 2^(62 - hr) units and their sum
