@@ -426,6 +426,8 @@ def run_profile_case(args):
     # k > 0: dense univariate with k terms at 2^24 points; k = 0: trivariate
     # total degree 40 (12341 terms) at 2^22 points
     nv, npts = (1, NPTS) if k > 0 else (3, 1 << 22)
+    if args.profile_points > 0:
+        npts = args.profile_points
     x = W.points_f64(nv, npts, SEED + 1)
     if k > 0:
         e, c, _ = W.univariate_case(k, 1, SEED + k)
@@ -1304,6 +1306,8 @@ def main():
     ap.add_argument("--profile-dtype", default="f64")
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "ops", "node"])
     ap.add_argument("--profile-ppt", type=int, default=0, help="points per thread (0: automatic)")
+    ap.add_argument("--profile-points", type=int, default=0,
+                    help="points of the profile case (0: 2^24 univariate, 2^22 trivariate)")
     ap.add_argument("--compose-dtypes", default="modp,f64", help="value types of --workload compose")
     ap.add_argument("--compose-schemes", default="E,B", help="schemes of --workload compose")
     ap.add_argument("--gpus", type=int, default=1)
