@@ -112,3 +112,49 @@ def test_residues_balanced_with_recomputed_powers():
     for j, p in enumerate(small, start=len(big)):
         assert fpl.limbs_to_int(got_limbs[j]) == X.int_value(e.tolist(), coeffs, (p,)), j
     t.free()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_small_grid_split_is_bit_identical(seed):
+    """The small-grid split (one point per thread, the root's two parts in two
+    warps, the second's root edges applied after the first's) against the
+    same tree at two points per thread (never split): FP64, FP32C and MODP
+    results equal bit for bit, over random univariate and multivariate trees
+    under E, B and random split tables (7 of the 12 trees have a split, and
+    the grids of 2000-40000 points take it); plus each against the oracle's
+    bar."""
+    r = W.rng(7100 + seed)
+    nvars = int(r.integers(1, 4))
+    if nvars == 1:
+        k = int(r.integers(60, 3000))
+        e = W.dense_univariate_exps(k)
+    else:
+        e = W.total_degree_exps(nvars, int(r.integers(6, 16 if nvars == 2 else 10)))
+    k = len(e)
+    scheme = ["E", "B", "CUSTOM"][int(r.integers(0, 3))]
+    ftab = None
+    if scheme == "CUSTOM":
+        nmax = int(e.max()) + 1
+        ftab = np.zeros(nmax + 1, dtype=np.int32)
+        for n in range(1, nmax + 1):
+            ftab[n] = max(1, n // 2 if r.random() < 0.5 else 2 ** int(np.log2(n)))
+    npts = int(r.integers(2000, 40000))
+    c = W.uniform_f64(k, 7200 + seed)
+    x = W.uniform_f64(nvars * npts, 7300 + seed).reshape(nvars, npts)
+    t = fpl.fp_compile(e, c, scheme, ftab)
+    res = W.residues(k, 7400 + seed)
+    tm = fpl.fp_compile(e, res, scheme, ftab, modp=True)
+    xm = W.points_modp(nvars, npts, 7500 + seed)
+    for dt, tree, pts in (("f64", t, x), ("f32c", t, x), ("modp", tm, xm)):
+        d = device_points(dt, pts)
+        one = fpl.fp_eval_ex(tree, dt, d, kernel="ops", ppt=1).cpu().numpy()
+        two = fpl.fp_eval_ex(tree, dt, d, kernel="ops", ppt=2).cpu().numpy()
+        assert np.array_equal(one.view(np.uint8), two.view(np.uint8)), (dt, scheme, nvars, k, npts)
+        if dt == "f64":
+            check_f64(e, c, pts, one)
+        elif dt == "f32c":
+            check_f32c(e, c, pts, one)
+        else:
+            check_modp(e, res, pts, one.view(np.uint64))
+    t.free()
+    tm.free()
