@@ -724,6 +724,49 @@ __device__ __forceinline__ void block_dispatch(int len, bool partial, const type
 #undef FP_BLOCK_CASE
 }
 
+// A Balanced run of L = 17 .. 22 nodes as its two parts in one straight
+// piece of code: a, the upper ceil(L / 2) nodes, and b, the lower floor(L / 2)
+// (ending at the op's last node), then T(b) + T(a) x^f -- the operations of
+// the two-part loop below, in its order, without its second dispatch and part
+// moves, and with the two parts' chains independent for the scheduler.
+template <class A, int SCHEME, int PPT, int L>
+__device__ __forceinline__ void two_part_case(bool partial, const typename A::coef* st, int64_t off,
+                                              const typename A::pw (&xp)[PPT][kMaxBlock + 1],
+                                              const typename A::val (&slot)[PPT], const typename A::pw (&xf)[PPT],
+                                              typename A::val (&v)[PPT]) {
+  using C = typename A::coef;
+  using V = typename A::val;
+  constexpr int LB = L / 2, LA = L - LB;
+  const int64_t offb = off + ((LA + kStreamAlign - 1) & ~(kStreamAlign - 1));
+  C ca[kMaxBlock], cb[kMaxBlock];
+#pragma unroll
+  for (int q = 0; q < (LA + 3) / 4; ++q) {
+    C c4[4];
+    load4(st, off, q, c4);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) ca[4 * q + r] = c4[r];
+  }
+#pragma unroll
+  for (int q = 0; q < (LB + 3) / 4; ++q) {
+    C c4[4];
+    load4(st, offb, q, c4);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) cb[4 * q + r] = c4[r];
+  }
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const V va = block_eval<A, SCHEME, 0, LA - 1, true>(ca, xp[p], A::from_coef(ca[LA - 1]));
+    V vb;
+    if constexpr (A::kSlotAtEnd) {
+      vb = block_eval<A, SCHEME, 0, LB - 1, true>(cb, xp[p], A::from_coef(partial ? C(0) : cb[LB - 1]));
+      if (partial) vb = A::add(vb, slot[p]);
+    } else {
+      vb = block_eval<A, SCHEME, 0, LB - 1, true>(cb, xp[p], partial ? slot[p] : A::from_coef(cb[LB - 1]));
+    }
+    v[p] = A::mad(va, xf[p], vb);
+  }
+}
+
 // 128-bit loads of an op record and of coefficient runs (read-only path)
 template <class C>
 __device__ __forceinline__ void load_rec(const OpRec<C>* r, uint4& h, C& a, C& b) {
@@ -899,6 +942,19 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
           block_dispatch<A, SCHEME, PPT>(len, partial, st, off, xp, slot, v);
         } else {
         const int f = (int)((h.y >> 8) & 255u);
+        if (f > 0 && f == len / 2 && len >= 17 && len <= 22) {
+          W xf[PPT];
+#pragma unroll
+          for (int p = 0; p < PPT; ++p) xf[p] = pw[((int)(h.y >> 16) * PPT + p) * TPB + tid];
+          switch (len) {
+            case 17: two_part_case<A, SCHEME, PPT, 17>(partial, st, off, xp, slot, xf, v); break;
+            case 18: two_part_case<A, SCHEME, PPT, 18>(partial, st, off, xp, slot, xf, v); break;
+            case 19: two_part_case<A, SCHEME, PPT, 19>(partial, st, off, xp, slot, xf, v); break;
+            case 20: two_part_case<A, SCHEME, PPT, 20>(partial, st, off, xp, slot, xf, v); break;
+            case 21: two_part_case<A, SCHEME, PPT, 21>(partial, st, off, xp, slot, xf, v); break;
+            default: two_part_case<A, SCHEME, PPT, 22>(partial, st, off, xp, slot, xf, v); break;
+          }
+        } else {
         V va[PPT];
 #pragma unroll 1
         for (int part = f > 0 ? 0 : 1; part < 2; ++part) {
@@ -917,6 +973,7 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
           const int cp = (int)(h.y >> 16);
 #pragma unroll
           for (int p = 0; p < PPT; ++p) v[p] = A::mad(va[p], pw[(cp * PPT + p) * TPB + tid], v[p]);
+        }
         }
         }
       }
