@@ -1,5 +1,5 @@
 """Balanced trees whose grouped schedules use the extended kernels: runs of 17
-to 24 nodes evaluated as two parts joined with x^f, and edge powers that few
+to 22 nodes evaluated as two parts joined with x^f, and edge powers that few
 ops read recomputed from a kept binary prefix instead of read from the
 per-point table.  Every value type that runs the grouped schedule -- FP64,
 FP32C, MODP and residues -- through fp_eval, the batch launch and the
