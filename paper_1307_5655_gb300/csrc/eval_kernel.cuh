@@ -1036,8 +1036,20 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
   }
 }
 
+// Minimum resident blocks per SM given to ptxas (0: none, its own register
+// choice).  Left to itself ptxas holds the FP32C Estrin kernel at two points
+// per thread to 56 registers, for a residency that its power table (>= 16
+// entries, >= 32 KB per 128-thread block, at >= 3000 terms) never allows; a
+// bound of one block lets it take 96, 7 % faster at 10007 terms (2^24 points)
+// with the same 5 blocks per SM.  Every other instantiation measured level or
+// slower with the bound (FP32C H and B, and MODP, at 1, 2 and 4 points).
+template <class A, int PPT, int SCHEME>
+constexpr int ops_min_blocks() {
+  return (std::is_same<A, F32C>::value && SCHEME == FP_SCHEME_E && PPT == 2) ? 1 : 0;
+}
+
 template <class A, int PPT, int SCHEME, int TPB = kTPB, bool SPLIT = false>
-__global__ void __launch_bounds__(TPB) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
+__global__ void __launch_bounds__(TPB, (ops_min_blocks<A, PPT, SCHEME>())) eval_ops_kernel(const EvalArgs g, const OpArgs o) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ops_tile<A, PPT, SCHEME, TPB, SPLIT>(g, o, (int64_t)blockIdx.x * (SPLIT ? 32 : TPB * PPT), smem_raw);
 }
