@@ -68,14 +68,14 @@ namespace {
 
 template <class A, int PPT>
 cudaError_t launch_batch_t(const BatchJob* d_jobs, int njobs, int64_t nblocks, size_t smem, cudaStream_t st) {
-  static int configured_dev = -1;
+  static std::atomic<int> configured_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_dev != dev) {
+  if (configured_dev.load(std::memory_order_relaxed) != dev) {
     cudaError_t e = cudaFuncSetAttribute(eval_batch_kernel<A, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemMax);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
+    configured_dev.store(dev, std::memory_order_relaxed);
   }
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;

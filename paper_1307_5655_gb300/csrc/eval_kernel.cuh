@@ -21,6 +21,7 @@
 //   IV64 keeps the paper's order literally (see the interval policy).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -1080,15 +1081,17 @@ cudaError_t launch_eval_smem(const EvalArgs& a, cudaStream_t s) {
   const bool table = eval_smem<A, PPT>(a, true) <= kTableSmemCap;
   const size_t smem = eval_smem<A, PPT>(a, table);
   if (smem > kSmemMax) return cudaErrorInvalidValue;
-  static int configured_dev = -1;  // raise the dynamic shared-memory cap once per device
+  // raise the dynamic shared-memory cap once per device (atomic: the server's
+  // worker and the caller's threads may launch concurrently; a repeat is harmless)
+  static std::atomic<int> configured_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_dev != dev) {
+  if (configured_dev.load(std::memory_order_relaxed) != dev) {
     cudaError_t e = cudaFuncSetAttribute(eval_kernel<A, PPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(eval_kernel<A, PPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
+    configured_dev.store(dev, std::memory_order_relaxed);
   }
   const int64_t per_block = (int64_t)kTPB * PPT;
   const int64_t blocks = (a.npts + per_block - 1) / per_block;
@@ -1108,13 +1111,13 @@ template <class A, int PPT, int SCHEME, int TPB>
 cudaError_t launch_eval_ops_tpb(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
   const size_t smem = ops_smem<A, PPT>(o) / kTPB * TPB;
   if (smem > kSmemMax) return cudaErrorInvalidValue;
-  static int configured_dev = -1;
+  static std::atomic<int> configured_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_dev != dev) {
+  if (configured_dev.load(std::memory_order_relaxed) != dev) {
     cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, PPT, SCHEME, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
+    configured_dev.store(dev, std::memory_order_relaxed);
   }
   const int64_t per_block = (int64_t)TPB * PPT;
   const int64_t blocks = (a.npts + per_block - 1) / per_block;
@@ -1129,14 +1132,14 @@ template <class A, int SCHEME>
 cudaError_t launch_eval_ops_split(const EvalArgs& a, const OpArgs& o, cudaStream_t s) {
   const size_t smem = sizeof(typename A::pw) * (size_t)(o.entries + o.ndefer) * 64;
   if (smem > kSmemMax) return cudaErrorInvalidValue;
-  static int configured_dev = -1;
+  static std::atomic<int> configured_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_dev != dev) {
+  if (configured_dev.load(std::memory_order_relaxed) != dev) {
     cudaError_t e = cudaFuncSetAttribute(eval_ops_kernel<A, 1, SCHEME, 64, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
+    configured_dev.store(dev, std::memory_order_relaxed);
   }
   const int64_t blocks = (a.npts + 31) / 32;
   if (blocks <= 0) return cudaSuccess;
@@ -1147,32 +1150,36 @@ cudaError_t launch_eval_ops_split(const EvalArgs& a, const OpArgs& o, cudaStream
 
 // multiprocessors of the current device (cached per device)
 inline int sm_count() {
-  static int cached[64] = {0};
+  static std::atomic<int> cached[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 152; }
-  if (!cached[dev]) {
+  int c = cached[dev].load(std::memory_order_relaxed);
+  if (!c) {
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
       cudaGetLastError();
       n = 152;
     }
-    cached[dev] = n;
+    cached[dev].store(n, std::memory_order_relaxed);
+    c = n;
   }
-  return cached[dev];
+  return c;
 }
 
 // registers per thread of a kernel (cached per instantiation)
 template <class A, int PPT, int SCHEME, int TPB>
 int ops_kernel_regs() {
-  static int regs = 0;
-  if (!regs) {
+  static std::atomic<int> regs{0};
+  int r = regs.load(std::memory_order_relaxed);
+  if (!r) {
     cudaFuncAttributes fa;
-    regs = cudaFuncGetAttributes(&fa, eval_ops_kernel<A, PPT, SCHEME, TPB>) == cudaSuccess && fa.numRegs > 0
-               ? fa.numRegs
-               : 255;
+    r = cudaFuncGetAttributes(&fa, eval_ops_kernel<A, PPT, SCHEME, TPB>) == cudaSuccess && fa.numRegs > 0
+            ? fa.numRegs
+            : 255;
     cudaGetLastError();
+    regs.store(r, std::memory_order_relaxed);
   }
-  return regs;
+  return r;
 }
 
 // Points resident per SM with blocks of tpb threads: shared memory (228 KB
