@@ -226,7 +226,9 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
  *       few ops read) base | m << 15 | (d mod 2^m) << 19: the edge power x^d
  *       is rebuilt from the table entry at position base (0x7FFF: x) by m
  *       steps of squaring and, where the bit of d is set, multiplying by x
- *       (the power program's own steps); word 3 = stream offset.
+ *       (the power program's own steps); word 3 = stream offset (bits
+ *       0..30) | ROOT_EDGE (31: an op past the split, see layout, whose edge
+ *       goes into the root's slot).
  *   op_a_node, op_b_node [nops]: node whose coefficient is the op's leaf value
  *       (single-node ops) / initialises the parent's slot when FIRST; -1 = 0.
  *   stream [stream_len]: node whose coefficient sits in each slot of the
@@ -246,9 +248,11 @@ int fp_tree_export(const fp_tree* t, int32_t* node_exps, int64_t* term_of_node, 
  *       split: the first op of the root's later children (0: none) -- ops
  *       [0, split) evaluate the root's first child's subtree (nodes 0 .. its
  *       root) and its edge into the root's slot, ops [split, nops) the other
- *       children, so small grids run the two ranges in two warps that start
- *       from separate tables (the second from a zero root slot) and add the
- *       root slots.
+ *       children, so small grids run the two ranges in two warps with tables
+ *       of their own; the second keeps the values of its ROOT_EDGE ops and,
+ *       after the first is done, applies them in walk order to the first's
+ *       root slot (the walk's own operations in its order: the result is
+ *       bit-identical to one warp's).
  * Any array pointer may be NULL.  FP_E_BAD_VALUE for a NULL tree. */
 int fp_tree_schedule(const fp_tree* t, int64_t* nops, uint32_t* op_words, int64_t* op_a_node,
                      int64_t* op_b_node, int64_t* stream_len, int64_t* stream, int32_t* nprog,
