@@ -162,8 +162,9 @@ int ops_layout(fp_tree* t) {
   // upper part a of the top split p = a x^f + b) heads a subtree of nodes
   // 0 .. ra, and ops [0, s) cover exactly those nodes; ops [s, nops) add the
   // root's later children into its slot.  The two ranges can run in two
-  // warps (the second starting from a zero slot) whose slots are then added.
-  // Kept when each range has at least a quarter of the nodes.
+  // warps, the second applying its edges into the root's slot (marked below)
+  // to the first's root slot afterwards, in walk order.  Kept when each range
+  // has at least a quarter of the nodes.
   t->ops_split = 0;
   if (N > 2) {
     int64_t ra = -1;
