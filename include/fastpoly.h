@@ -456,7 +456,7 @@ int fp_compose_workspace(const fp_tree* p, fp_dtype dtype, int per_pair_coeffs, 
  * from one region of FP_NOALLOC_SCRATCH_BYTES that every GPU loading the
  * library holds until the process exits; nothing is allocated or freed.
  *   - The first call on a device looks up that region's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).
  *   - All calls share the region and it keeps the last call's contents, so
  *     calls that overlap on the GPU (other streams, other threads) race:
  *     serialise them.
