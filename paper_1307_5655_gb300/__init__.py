@@ -191,17 +191,76 @@ def _torch_dtype(dtype):
     return {"f64": torch.float64, "f32c": torch.float32, "iv64": torch.float64, "modp": torch.int64}[dtype]
 
 
+def _elem_types(dtype):
+    """Element types accepted for a value type's points and results (torch
+    dtypes; residues as int64 or uint64 bit patterns)."""
+    import torch
+    if dtype == "modp":
+        return (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    return {"f64": (torch.float64,), "f32c": (torch.float32,), "iv64": (torch.float64,)}[dtype]
+
+
+def _point_elems(dtype, nvars, npts):
+    """Elements of a points array in the layout of fp_eval."""
+    return nvars * npts * (2 if dtype == "iv64" else 1)
+
+
+def _check_extent(what, name, etype, numel, types, need):
+    if etype not in types:
+        raise ValueError("%s: %s has element type %s, expected %s" % (what, name, etype, " or ".join(map(str, types))))
+    if numel < need:
+        raise ValueError("%s: %s holds %d elements, the call touches %d" % (what, name, numel, need))
+
+
+def _check_device(what, name, a, types, need, device=None):
+    """Refuse, before the C call, a device buffer that would send a kernel
+    outside its memory: not a contiguous CUDA tensor, another element type,
+    fewer elements than the call touches, or another device than `device`."""
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("%s: %s must be a contiguous CUDA tensor" % (what, name))
+    _check_extent(what, name, a.dtype, a.numel(), types, need)
+    if device is not None and a.device != device:
+        raise ValueError("%s: %s is on %s, the points on %s" % (what, name, a.device, device))
+
+
+def _check_eval_io(what, tree, dtype, points, npts, out):
+    """points and out in the layouts of fp_eval for this tree, value type and
+    number of points."""
+    types = _elem_types(dtype)
+    _check_device(what, "points", points, types, _point_elems(dtype, tree.nvars, npts))
+    _check_device(what, "out", out, types, int(np.prod(out_shape(dtype, npts))), points.device)
+
+
+def _check_host_io(what, tree, dtype, points, npts, out):
+    """The same for host buffers (numpy arrays or CPU tensors), which the
+    library copies from and to."""
+    import torch
+    np_types = {"f64": (np.float64,), "f32c": (np.float32,), "iv64": (np.float64,),
+                "modp": (np.uint64, np.int64)}[dtype]
+    for name, a, need in (("points", points, _point_elems(dtype, tree.nvars, npts)),
+                          ("out", out, int(np.prod(out_shape(dtype, npts))))):
+        if isinstance(a, np.ndarray):
+            if not a.flags.c_contiguous:
+                raise ValueError("%s: %s must be a C-contiguous array" % (what, name))
+            _check_extent(what, name, a.dtype.type, a.size, np_types, need)
+        elif isinstance(a, torch.Tensor) and not a.is_cuda and a.is_contiguous():
+            _check_extent(what, name, a.dtype, a.numel(), _elem_types(dtype), need)
+        else:
+            raise ValueError("%s: %s must be a contiguous host array or CPU tensor" % (what, name))
+
+
 def fp_eval(tree, dtype, points, npts=None, out=None, stream=None):
     """Evaluate on the GPU.  points: CUDA tensor in the layout of fp_eval
     (f64 [nvars, npts] float64; f32c [nvars, npts] float32; iv64
     [nvars, 2, npts] float64; modp [nvars, npts] uint64).  Returns out."""
     import torch
-    if not points.is_cuda or not points.is_contiguous():
-        raise ValueError("points must be a contiguous CUDA tensor")
+    _check_device("fp_eval", "points", points, _elem_types(dtype), 0)
     if npts is None:
         npts = points.shape[-1]
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    _check_eval_io("fp_eval", tree, dtype, points, npts, out)
     _check(_lib.fp_eval(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream)), "fp_eval")
     return out
 
@@ -217,12 +276,12 @@ def fp_eval_ex(tree, dtype, points, kernel="auto", npts=None, out=None, stream=N
     """fp_eval with an explicit kernel choice ('auto', 'ops', 'node') and
     points per thread (0: automatic)."""
     import torch
-    if not points.is_cuda or not points.is_contiguous():
-        raise ValueError("points must be a contiguous CUDA tensor")
+    _check_device("fp_eval_ex", "points", points, _elem_types(dtype), 0)
     if npts is None:
         npts = points.shape[-1]
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    _check_eval_io("fp_eval_ex", tree, dtype, points, npts, out)
     cfg = LaunchCfg(KERNELS[kernel], ppt)
     _check(_lib.fp_eval_ex(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
                            ctypes.byref(cfg)), "fp_eval_ex")
@@ -265,11 +324,14 @@ def fp_eval_rns(tree, points, out=None, stream=None):
     """p(x) mod each prime: points device [k][nvars][npts] (int64 containers of
     uint64 residues), out [k][npts]."""
     import torch
-    if not points.is_cuda or not points.is_contiguous():
-        raise ValueError("points must be a contiguous CUDA tensor")
+    types = _elem_types("modp")
+    _check_device("fp_eval_rns", "points", points, types, 0)
     npts = points.shape[-1]
+    k = getattr(tree, "rns_k", 1)
     if out is None:
-        out = torch.empty((tree.rns_k, npts), dtype=torch.int64, device=points.device)
+        out = torch.empty((k, npts), dtype=torch.int64, device=points.device)
+    _check_device("fp_eval_rns", "points", points, types, k * tree.nvars * npts)
+    _check_device("fp_eval_rns", "out", out, types, k * npts, points.device)
     _check(_lib.fp_eval_rns(tree.handle, _ptr(points), npts, _ptr(out), _stream_handle(stream)), "fp_eval_rns")
     return out
 
@@ -278,9 +340,14 @@ def fp_crt(residues, out=None, stream=None):
     """Integers from residues [k][npts] (device): limbs [npts][k], least
     significant first, two's complement of the value in (-Q/2, Q/2]."""
     import torch
+    types = _elem_types("modp")
+    _check_device("fp_crt", "residues", residues, types, 0)
+    if residues.dim() != 2:
+        raise ValueError("fp_crt: residues must be [k][npts]")
     k, npts = residues.shape
     if out is None:
         out = torch.empty((npts, k), dtype=torch.int64, device=residues.device)
+    _check_device("fp_crt", "out", out, types, npts * k, residues.device)
     _check(_lib.fp_crt(k, _ptr(residues), npts, _ptr(out), _stream_handle(stream)), "fp_crt")
     return out
 
@@ -316,9 +383,13 @@ def fp_tune_scheme(exps, coeffs, dtype, points, out=None, stream=None, modp=Fals
         e = e.reshape(-1, 1)
     nterms, nvars = e.shape
     c = np.ascontiguousarray(coeffs, dtype=np.uint64 if modp else np.float64)
+    types = _elem_types(dtype)
+    _check_device("fp_tune_scheme", "points", points, types, 0)
     npts = points.shape[-1]
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    _check_device("fp_tune_scheme", "points", points, types, _point_elems(dtype, nvars, npts))
+    _check_device("fp_tune_scheme", "out", out, types, int(np.prod(out_shape(dtype, npts))), points.device)
     h = ctypes.c_void_p()
     k0 = ctypes.c_int64()
     _check(_lib.fp_tune_scheme(nvars, nterms, _ptr(e), _ptr(c), DTYPES["modp"] if modp else DTYPES["f64"],
@@ -331,9 +402,11 @@ def fp_tune(tree, dtype, points, out=None, stream=None):
     """Autotune the launch configuration of this tree and value type on these
     points (synchronous); returns (kernel name, points per thread)."""
     import torch
+    _check_device("fp_tune", "points", points, _elem_types(dtype), 0)
     npts = points.shape[-1]
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
+    _check_eval_io("fp_tune", tree, dtype, points, npts, out)
     cfg = LaunchCfg()
     _check(_lib.fp_tune(tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out), _stream_handle(stream),
                         ctypes.byref(cfg)), "fp_tune")
@@ -347,6 +420,7 @@ def fp_eval_host(tree, dtype, points, stream=None):
     npts = pts.shape[-1]
     npdt = {"f64": np.float64, "f32c": np.float32, "iv64": np.float64, "modp": np.uint64}[dtype]
     out = np.empty(out_shape(dtype, npts), dtype=npdt)
+    _check_host_io("fp_eval_host", tree, dtype, pts, npts, out)
     _check(_lib.fp_eval_host(tree.handle, DTYPES[dtype], _ptr(pts), npts, _ptr(out), _stream_handle(stream)),
            "fp_eval_host")
     return out
@@ -355,9 +429,13 @@ def fp_eval_host(tree, dtype, points, stream=None):
 def fp_eval_plain_f64(coeffs_by_degree, points, out=None, stream=None):
     """Baseline: one thread per point, Horner over dense FP64 coefficients."""
     import torch
+    f64 = _elem_types("f64")
+    _check_device("fp_eval_plain_f64", "points", points, f64, 0)
+    _check_device("fp_eval_plain_f64", "coefficients", coeffs_by_degree, f64, 0, points.device)
     npts = points.shape[-1]
     if out is None:
         out = torch.empty(npts, dtype=torch.float64, device=points.device)
+    _check_device("fp_eval_plain_f64", "out", out, f64, npts, points.device)
     _check(_lib.fp_eval_plain_f64(_ptr(coeffs_by_degree), coeffs_by_degree.numel(), _ptr(points), npts, _ptr(out),
                                   _stream_handle(stream)), "fp_eval_plain_f64")
     return out
@@ -461,16 +539,23 @@ _lib.fp_batch_free.restype = None
 _lib.fp_batch_free.argtypes = [_P]
 
 
-def _jobs_array(jobs):
+def _check_job(what, tree, dtype, points, out):
+    """A job (tree, points, out) in the layouts of fp_eval."""
+    _check_device(what, "points", points, _elem_types(dtype), 0)
+    _check_eval_io(what, tree, dtype, points, points.shape[-1], out)
+
+
+def _jobs_array(jobs, dtype, what):
     arr = (_Job * max(1, len(jobs)))()
     for i, (tree, pts, out) in enumerate(jobs):
+        _check_job(what, tree, dtype, pts, out)
         arr[i] = _Job(tree.handle, pts.data_ptr(), pts.shape[-1], out.data_ptr())
     return arr
 
 
 def fp_eval_batch(dtype, jobs, stream=None):
     """jobs: list of (tree, points, out) with CUDA tensors in fp_eval layouts."""
-    arr = _jobs_array(jobs)
+    arr = _jobs_array(jobs, dtype, "fp_eval_batch")
     _check(_lib.fp_eval_batch(DTYPES[dtype], ctypes.cast(arr, ctypes.c_void_p), len(jobs), _stream_handle(stream)),
            "fp_eval_batch")
 
@@ -481,7 +566,7 @@ class Batch:
 
     def __init__(self, dtype, jobs):
         self._keep = list(jobs)
-        arr = _jobs_array(jobs)
+        arr = _jobs_array(jobs, dtype, "Batch")
         h = ctypes.c_void_p()
         _check(_lib.fp_batch_create(DTYPES[dtype], ctypes.cast(arr, ctypes.c_void_p), len(jobs), ctypes.byref(h)),
                "fp_batch_create")
@@ -541,6 +626,7 @@ class Server:
     def submit(self, tree, dtype, points, out):
         t = ctypes.c_int64()
         npts = points.shape[-1]
+        _check_host_io("Server.submit", tree, dtype, points, npts, out)
         with self._lock:
             _check(_lib.fp_server_submit(self._h, tree.handle, DTYPES[dtype], _ptr(points), npts, _ptr(out),
                                          ctypes.byref(t)), "fp_server_submit")
@@ -597,8 +683,7 @@ class Resident:
 
     def submit(self, tree, points, out):
         """points, out: CUDA tensors in fp_eval layouts.  Returns the ticket."""
-        if not points.is_cuda or not out.is_cuda or not points.is_contiguous() or not out.is_contiguous():
-            raise ValueError("points and out must be contiguous CUDA tensors")
+        _check_job("Resident.submit", tree, self.dtype, points, out)
         job = _Job(tree.handle, points.data_ptr(), points.shape[-1], out.data_ptr())
         t = ctypes.c_int64()
         _check(_lib.fp_resident_submit(self._h, ctypes.byref(job), ctypes.byref(t)), "fp_resident_submit")
