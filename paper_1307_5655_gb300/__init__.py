@@ -205,6 +205,11 @@ def _point_elems(dtype, nvars, npts):
     return nvars * npts * (2 if dtype == "iv64" else 1)
 
 
+def _out_elems(dtype, npts):
+    """Elements of a result array in the layout of fp_eval (out_shape)."""
+    return npts * (2 if dtype in ("f32c", "iv64") else 1)
+
+
 def _check_extent(what, name, etype, numel, types, need):
     if etype not in types:
         raise ValueError("%s: %s has element type %s, expected %s" % (what, name, etype, " or ".join(map(str, types))))
@@ -229,7 +234,7 @@ def _check_eval_io(what, tree, dtype, points, npts, out):
     number of points."""
     types = _elem_types(dtype)
     _check_device(what, "points", points, types, _point_elems(dtype, tree.nvars, npts))
-    _check_device(what, "out", out, types, int(np.prod(out_shape(dtype, npts))), points.device)
+    _check_device(what, "out", out, types, _out_elems(dtype, npts), points.device)
 
 
 def _check_host_io(what, tree, dtype, points, npts, out):
@@ -239,7 +244,7 @@ def _check_host_io(what, tree, dtype, points, npts, out):
     np_types = {"f64": (np.float64,), "f32c": (np.float32,), "iv64": (np.float64,),
                 "modp": (np.uint64, np.int64)}[dtype]
     for name, a, need in (("points", points, _point_elems(dtype, tree.nvars, npts)),
-                          ("out", out, int(np.prod(out_shape(dtype, npts))))):
+                          ("out", out, _out_elems(dtype, npts))):
         if isinstance(a, np.ndarray):
             if not a.flags.c_contiguous:
                 raise ValueError("%s: %s must be a C-contiguous array" % (what, name))
@@ -389,7 +394,7 @@ def fp_tune_scheme(exps, coeffs, dtype, points, out=None, stream=None, modp=Fals
     if out is None:
         out = torch.empty(out_shape(dtype, npts), dtype=_torch_dtype(dtype), device=points.device)
     _check_device("fp_tune_scheme", "points", points, types, _point_elems(dtype, nvars, npts))
-    _check_device("fp_tune_scheme", "out", out, types, int(np.prod(out_shape(dtype, npts))), points.device)
+    _check_device("fp_tune_scheme", "out", out, types, _out_elems(dtype, npts), points.device)
     h = ctypes.c_void_p()
     k0 = ctypes.c_int64()
     _check(_lib.fp_tune_scheme(nvars, nterms, _ptr(e), _ptr(c), DTYPES["modp"] if modp else DTYPES["f64"],
