@@ -382,12 +382,7 @@ def run_ours(args):
                              "depend on the scheme (%.1f s wall)" % wall,
                    "single_thread": {"value": cpu_oracle_rate_single() / 1e9, "unit": UNIT, "cores": 1,
                                      "sample": "2^13 points per (k, value type), in this process"}}
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "eval_f64_traffic.txt")
-        if os.path.exists(tf):
-            for line in open(tf):
-                if line.startswith("bytes_per_launch_k10007_2^24:"):
-                    traffic = float(line.split(":")[1])
+        traffic = f64_traffic_per_launch()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -413,6 +408,17 @@ def run_ours(args):
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def f64_traffic_per_launch():
+    """DRAM bytes (read + written) per launch of the FP64 kernel at 10007
+    terms and 2^24 points, from its ncu capture in profiles/, or None."""
+    tf = os.path.join(ROOT, "profiles", "eval_f64_traffic.txt")
+    if os.path.exists(tf):
+        for line in open(tf):
+            if line.startswith("bytes_per_launch_k10007_2^24:"):
+                return float(line.split(":")[1])
+    return None
 
 
 def run_profile_case(args):

@@ -1,7 +1,8 @@
 """The roofline arithmetic of bench.py's composition line (compose_work), on
 CPU, against operation counts worked out by hand for trees small enough to
 follow: a transform of length n is (n/2) log2 n radix-2 butterflies, plus n
-twiddle multiplications when it takes the four-step form (n > 4096)."""
+twiddle multiplications when it takes the four-step form (n > 4096); and
+the DRAM traffic figure the benchmark line reports for its FP64 kernel."""
 import paper_1307_5655_gb300 as fpl
 import workloads as W
 
@@ -43,3 +44,13 @@ def test_one_four_step_product():
     bfly, mul = bench.compose_work(t, 3000, True)
     assert bfly == 3 * 4096 * 13 - 2 * 4096
     assert mul == 3001 + 3 * 8192 + 8192 + 2 * 4096
+
+
+def test_f64_traffic_figure_is_a_whole_launch():
+    """The committed capture of the FP64 kernel at 10007 terms and 2^24 points
+    gives bytes per launch comparable with that launch's point I/O (2^24
+    points of 8 bytes in, 8 bytes out): reads at least the points, writes at
+    most the results, so between half and 1.1 times the I/O in total."""
+    t = bench.f64_traffic_per_launch()
+    io = bench.NPTS * 16
+    assert t is not None and 0.5 * io <= t <= 1.1 * io, (t, io)
