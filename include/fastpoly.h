@@ -34,7 +34,8 @@ typedef enum {
   FP_E_NOMEM = -5,       /* host or device allocation failed */
   FP_E_TOO_LARGE = -6,   /* a size beyond the documented limits */
   FP_E_CUDA = -7,        /* a CUDA call or kernel launch failed */
-  FP_E_TIMEOUT = -8      /* a bounded device-side wait gave up */
+  FP_E_TIMEOUT = -8,     /* a bounded device-side wait gave up */
+  FP_E_INTERNAL = -9     /* a compiled schedule failed the library's own bounds check (a library fault) */
 } fp_status;
 
 /* Function schemes f (Sec. 1.1, Def. 1.2, and the balanced scheme of Sec. 1.2).
@@ -89,7 +90,10 @@ typedef struct fp_tree fp_tree;
  *   scheme       see fp_scheme; f_table/f_table_len only for FP_SCHEME_CUSTOM.
  *   out          receives the new tree.
  * Errors: FP_E_BAD_VALUE, FP_E_DUP_TERM, FP_E_BAD_SCHEME, FP_E_TOO_LARGE
- * (nvars, nterms, or lazy height above the limits), FP_E_NOMEM, FP_E_CUDA.
+ * (nvars, nterms, or lazy height above the limits), FP_E_NOMEM, FP_E_CUDA,
+ * FP_E_INTERNAL (every schedule is checked against the bounds of the arrays
+ * and tables the kernels index before it is uploaded; a failure is a fault of
+ * the library's compiler, reported instead of running the kernels on it).
  * Synchronous: returns after the schedule is resident on the device.
  */
 int fp_compile(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,

@@ -758,6 +758,7 @@ const char* fp_strerror(int status) {
     case FP_E_TOO_LARGE: return "size beyond the supported limits";
     case FP_E_CUDA: return "CUDA error";
     case FP_E_TIMEOUT: return "device wait timed out";
+    case FP_E_INTERNAL: return "internal schedule check failed";
   }
   return "unknown status";
 }

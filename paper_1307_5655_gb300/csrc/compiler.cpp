@@ -355,6 +355,107 @@ int ops_layout(fp_tree* t) {
 
 }  // namespace
 
+// Every index the kernels take from a schedule, checked against the array or
+// table it indexes before the schedule is uploaded: a schedule that fails is
+// a fault of this compiler, reported as FP_E_INTERNAL instead of sending a
+// kernel outside its buffers.  Node-by-node kernel: slots 0..max_lh, powers
+// [0, npow), program operands earlier in the program (dependency order).
+// Grouped-op kernel: slots below nslot (positions nlive + S < entries),
+// powers below entries (or rebuilt, Balanced blocks only), the coefficient
+// stream read in aligned 4-element vectors within its device padding, edge
+// powers of chains for nodes 0 .. nnodes - 2, and the split's marked edges.
+int validate_schedule(const fp_tree* t) {
+  const int64_t N = t->nnodes;
+  if (N <= 0) return FP_OK;
+  const int64_t npow = (int64_t)t->pow_prog.size();
+  const int L = t->max_lh;
+  if ((int64_t)t->ctrl.size() != N - 1 || (int64_t)t->pow_var.size() != npow ||
+      (int64_t)t->pow_deg.size() != npow)
+    return FP_E_INTERNAL;
+  for (int64_t k = 0; k < npow; ++k) {
+    const uint32_t w = t->pow_prog[k], op = w & 3u, a1 = (w >> 2) & 0x7FFFu, a2 = w >> 17;
+    if (op == kPowLoad) {
+      if ((int)a1 >= t->nvars) return FP_E_INTERNAL;
+    } else if (op == kPowSq) {
+      if ((int64_t)a1 >= k) return FP_E_INTERNAL;
+    } else if (op == kPowMulX) {
+      if ((int64_t)a1 >= k || (int64_t)a2 >= k) return FP_E_INTERNAL;
+    } else {
+      return FP_E_INTERNAL;
+    }
+    if (t->pow_var[k] < 0 || t->pow_var[k] >= t->nvars) return FP_E_INTERNAL;
+  }
+  for (int64_t j = 0; j + 1 < N; ++j) {
+    const uint32_t c = t->ctrl[j];
+    if ((int)((c >> kCtrlS) & 63u) > L || (int)((c >> kCtrlD) & 63u) > L || (int64_t)(c >> kCtrlPid) >= npow)
+      return FP_E_INTERNAL;
+  }
+  if (t->root_lh < 0 || t->root_lh > L || t->root_pid >= npow) return FP_E_INTERNAL;
+
+  const int64_t nops = (int64_t)t->ops.size(), ns = (int64_t)t->stream.size();
+  const int E = t->ops_entries, nslot = t->ops_nslot;
+  if (t->ops_nlive < 0 || nslot < 1 || t->ops_nlive + nslot > E) return FP_E_INTERNAL;
+  if ((int64_t)t->ops_chain_pid.size() != N - 1) return FP_E_INTERNAL;
+  for (const uint32_t p : t->ops_chain_pid)
+    if ((int64_t)p >= E) return FP_E_INTERNAL;
+  auto r4 = [](int64_t n) { return (n + kStreamAlign - 1) / kStreamAlign * kStreamAlign; };
+  int64_t marked = 0;
+  for (int64_t i = 0; i < nops; ++i) {
+    const uint4 h = t->ops[i];
+    const uint32_t kind = h.x & 3u, S = (h.x >> kOpS) & 63u, D = (h.x >> kOpD) & 63u, pid = h.x >> kOpPid;
+    const int64_t len = (int64_t)(h.y & 255u) + 1, f = (h.y >> 8) & 255u, off = h.w & 0x7FFFFFFFu;
+    const bool block = kind == kOpBlock || kind == kOpPartial;
+    if ((int)S >= nslot || (int)D >= nslot) return FP_E_INTERNAL;
+    if (pid == kPidRecompute) {  // z is the rebuild word: base | m << 15 | bits << 19
+      const uint32_t base = h.z & 0x7FFFu;
+      if (!t->ops_ext || !block || (base != 0x7FFFu && (int)base >= E) || t->ops_pid_pow[1] < 0)
+        return FP_E_INTERNAL;
+    } else {  // z is the first node; the op's nodes are non-root nodes
+      if ((int)pid >= E || (int64_t)h.z + len > N - 1) return FP_E_INTERNAL;
+    }
+    if (kind != kOpNode) {
+      if (off % kStreamAlign) return FP_E_INTERNAL;
+      int64_t end = off + r4(len);
+      if (f > 0) {  // a two-part run: a from off, b from the next aligned offset
+        if (!t->ops_ext || !block || f >= len || (int)(h.y >> 16) >= E) return FP_E_INTERNAL;
+        end = off + r4(len - f) + r4(f);
+      }
+      if (end > ns + kStreamAlign) return FP_E_INTERNAL;  // the device stream's padding
+    }
+    if (h.w >> 31) {
+      if (t->ops_split <= 0 || i < t->ops_split) return FP_E_INTERNAL;
+      ++marked;
+    }
+  }
+  if (t->ops_split < 0 || (nops > 0 && t->ops_split >= nops) || marked != t->ops_ndefer ||
+      (int64_t)t->ops_defer.size() != marked)
+    return FP_E_INTERNAL;
+  for (const uint2& e : t->ops_defer) {
+    if (e.x == kPidRecompute) {
+      if (!t->ops_ext || ((e.y & 0x7FFFu) != 0x7FFFu && (int)(e.y & 0x7FFFu) >= E)) return FP_E_INTERNAL;
+    } else if ((int)e.x >= E) {
+      return FP_E_INTERNAL;
+    }
+  }
+  if (t->ops_root_lh < 0 || t->ops_root_lh >= nslot || t->ops_root_pid >= E) return FP_E_INTERNAL;
+  for (int d = 0; d <= kMaxBlock; ++d)
+    if (t->ops_pid_pow[d] >= E) return FP_E_INTERNAL;
+  for (const uint2& e : t->ops_prog) {
+    const uint32_t op = e.x & 3u, a1 = (e.x >> 2) & 0x7FFFu, a2 = e.x >> 17;
+    if ((int64_t)e.y >= E) return FP_E_INTERNAL;
+    if (op == kPowLoad) {
+      if ((int)a1 >= t->nvars) return FP_E_INTERNAL;
+    } else if (op == kPowSq) {
+      if ((int)a1 >= E) return FP_E_INTERNAL;
+    } else if (op == kPowMulX) {
+      if ((int)a1 >= E || (int)a2 >= E) return FP_E_INTERNAL;
+    } else {
+      return FP_E_INTERNAL;
+    }
+  }
+  return FP_OK;
+}
+
 int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
                  fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
                  int64_t f_table_len, fp_tree* t) {
@@ -648,7 +749,8 @@ int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coe
   t->root_leaf = has_child[N - 1] ? 0 : 1;
   t->root_lh = t->lh[N - 1];
   t->root_pid = t->pd[N - 1] > 0 ? pid.at({0, t->pd[N - 1]}) : -1;
-  return ops_layout(t);
+  const int rc = ops_layout(t);
+  return rc == FP_OK ? validate_schedule(t) : rc;
 }
 
 }  // namespace fp
