@@ -47,7 +47,7 @@ def test_binding_constants_match_header():
     dtypes = _enum("FP_")
     for name, code in fpl.DTYPES.items():
         assert dtypes["FP_" + name.upper()] == code, name
-    assert dtypes["FP_OK"] == 0 and dtypes["FP_E_TIMEOUT"] == -8
+    assert dtypes["FP_OK"] == 0 and dtypes["FP_E_TIMEOUT"] == -8 and dtypes["FP_E_INTERNAL"] == -9
 
 
 def _compare(exps, coeffs, scheme, ftab=None):
@@ -214,7 +214,7 @@ def test_argument_checks_before_any_cuda_call():
     rates = np.zeros(2)
     assert lib.fp_measure_rates(None, 2, None) == -1
     assert lib.fp_measure_rates(rates.ctypes.data_as(ctypes.c_void_p), -1, None) == -1
-    msgs = [lib.fp_strerror(c) for c in range(0, -9, -1)]
+    msgs = [lib.fp_strerror(c) for c in range(0, -10, -1)]
     assert msgs[0] == b"ok" and len(set(msgs)) == len(msgs) and all(msgs)
     assert lib.fp_strerror(-99) == b"unknown status"
 
