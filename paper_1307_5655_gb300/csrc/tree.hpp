@@ -175,4 +175,8 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
 int compile_host(int nvars, int64_t nterms, const int32_t* exps, const void* coeffs,
                  fp_dtype coeff_type, fp_scheme scheme, const int32_t* f_table,
                  int64_t f_table_len, fp_tree* t);
+
+// Bounds check of a compiled schedule against the arrays and tables the
+// kernels index: FP_OK, or FP_E_INTERNAL (compile_host ends with it).
+int validate_schedule(const fp_tree* t);
 }  // namespace fp
