@@ -936,9 +936,12 @@ __device__ __forceinline__ void ops_tile(const EvalArgs& g, const OpArgs& o, int
         }
         // Balanced trees: a run longer than kMaxBlock (f > 0) is T(b) +
         // T(a) x^f, b its f lowest nodes (ending at the op's last node), a
-        // the others; each part is a run of at most kMaxBlock nodes stored
-        // from an aligned offset, evaluated by the same templates (one loop,
-        // one copy of the code).  Other schemes have single-part blocks only.
+        // the others, each stored from an aligned offset.  When f is the
+        // run's middle (the Balanced split, 17 to 22 nodes) one straight-line
+        // case evaluates both parts and the join; otherwise the loop below
+        // runs the parts through the same templates (f = 0: an ordinary block
+        // of at most kMaxBlock nodes, its one part).  Other schemes have
+        // single-part blocks only.
         if constexpr (SCHEME != kSchemeBExt) {
           block_dispatch<A, SCHEME, PPT>(len, partial, st, off, xp, slot, v);
         } else {
